@@ -1,0 +1,147 @@
+/*
+ * Oracle: a plain, slow, serial LSD radix sort of unsigned integer keys.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load this library. The GPU sort library shares no code,
+ * header, table or helper with it, and neither calls the other.
+ *
+ * What it computes (the plain definition): the ascending order of the input
+ * keys; with payloads, the STABLE ascending order (equal keys keep their input
+ * order and every payload moves with its key); for a segmented sort, the same
+ * on each [offsets[i], offsets[i+1]) independently. Radix sort reaches exactly
+ * this result, which is unique, so any correct sort agrees with it bit for bit.
+ *
+ * How: the paper's serial radix sort SR4 (Section "SR4, PR2, PR4, BTN and OET
+ * under MBSP", Eq. Ts): rounds of count-sort, one per r-ary digit, least
+ * significant digit first (the CLRS RADIX-SORT/COUNTING-SORT pair the paper
+ * cites). Each round
+ *   1. allocates and zeroes a count array of r counters,
+ *   2. reads the input once, counting each key's digit,
+ *   3. turns the counts into exclusive prefix sums (first output slot per digit),
+ *   4. reads the input a second time, in ascending index order, writing each key
+ *      (and its payload) to the next free slot of its digit -- one output write.
+ * Reading the input twice and writing once is the paper's 3N main-memory words
+ * per round. The rounds ping-pong between the array and a scratch copy; after an
+ * odd number of rounds the result is copied back.
+ *
+ * Digit p of key k is (k >> (p*b)) & (2^b - 1); when b does not divide the key
+ * width the last digit is narrower (e.g. 11, 11, 10 bits for b = 11 on 32-bit
+ * keys). Readings where the paper is silent: LSD order, unsigned keys, forward
+ * output loop with exclusive prefix (CLRS loops backwards with inclusive counts;
+ * both are stable and give the same array).
+ */
+#include "oracle.h"
+
+#include <stdlib.h>
+#include <string.h>
+
+static uint64_t get_key(const void *a, int64_t i, int key_bytes) {
+  if (key_bytes == 4) return ((const uint32_t *)a)[i];
+  return ((const uint64_t *)a)[i];
+}
+
+static void put_key(void *a, int64_t i, uint64_t k, int key_bytes) {
+  if (key_bytes == 4)
+    ((uint32_t *)a)[i] = (uint32_t)k;
+  else
+    ((uint64_t *)a)[i] = k;
+}
+
+static void copy_val(void *dst, int64_t j, const void *src, int64_t i, int val_bytes) {
+  if (val_bytes == 4)
+    ((uint32_t *)dst)[j] = ((const uint32_t *)src)[i];
+  else if (val_bytes == 8)
+    ((uint64_t *)dst)[j] = ((const uint64_t *)src)[i];
+}
+
+int oracle_count_sort_round(const void *keys_in, void *keys_out, const void *vals_in,
+                            void *vals_out, int64_t n, int key_bits, int val_bits, int shift,
+                            int digit_bits) {
+  if (n < 0 || (key_bits != 32 && key_bits != 64) ||
+      (val_bits != 0 && val_bits != 32 && val_bits != 64) || digit_bits < 1 ||
+      digit_bits > 24 || shift < 0 || shift + digit_bits > key_bits)
+    return 1;
+  const int kb = key_bits / 8, vb = val_bits / 8;
+  const int64_t r = (int64_t)1 << digit_bits;
+  const uint64_t mask = (uint64_t)r - 1;
+
+  /* 1. count array of r counters, zeroed */
+  int64_t *count = (int64_t *)calloc((size_t)r, sizeof(int64_t));
+  if (!count) return 2;
+
+  /* 2. first read of the input: count digits */
+  for (int64_t i = 0; i < n; ++i) count[(get_key(keys_in, i, kb) >> shift) & mask]++;
+
+  /* 3. exclusive prefix sums: count[d] becomes the first output slot of digit d */
+  int64_t sum = 0;
+  for (int64_t d = 0; d < r; ++d) {
+    int64_t c = count[d];
+    count[d] = sum;
+    sum += c;
+  }
+
+  /* 4. second read, ascending index order: stable placement, one output write */
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t k = get_key(keys_in, i, kb);
+    int64_t pos = count[(k >> shift) & mask]++;
+    put_key(keys_out, pos, k, kb);
+    if (vb) copy_val(vals_out, pos, vals_in, i, vb);
+  }
+  free(count);
+  return 0;
+}
+
+int oracle_num_passes(int key_bits, int radix_bits) {
+  return (key_bits + radix_bits - 1) / radix_bits;
+}
+
+int oracle_radix_sort(void *keys, void *vals, int64_t n, int key_bits, int val_bits,
+                      int radix_bits) {
+  if (n < 0 || (key_bits != 32 && key_bits != 64) ||
+      (val_bits != 0 && val_bits != 32 && val_bits != 64) || radix_bits < 1 || radix_bits > 24 ||
+      (n > 0 && !keys) || (n > 0 && val_bits && !vals))
+    return 1;
+  if (n <= 1) return 0;
+  const int kb = key_bits / 8, vb = val_bits / 8;
+  void *kscratch = malloc((size_t)n * kb);
+  void *vscratch = vb ? malloc((size_t)n * vb) : NULL;
+  if (!kscratch || (vb && !vscratch)) {
+    free(kscratch);
+    free(vscratch);
+    return 2;
+  }
+  void *kin = keys, *kout = kscratch, *vin = vals, *vout = vscratch;
+  const int passes = oracle_num_passes(key_bits, radix_bits);
+  int rc = 0;
+  for (int p = 0; p < passes && rc == 0; ++p) {
+    int shift = p * radix_bits;
+    int bits = key_bits - shift < radix_bits ? key_bits - shift : radix_bits;
+    rc = oracle_count_sort_round(kin, kout, vin, vout, n, key_bits, val_bits, shift, bits);
+    void *t = kin; kin = kout; kout = t;   /* swap in/out */
+    t = vin; vin = vout; vout = t;
+  }
+  if (rc == 0 && kin != keys) { /* odd number of rounds: copy the result back */
+    memcpy(keys, kin, (size_t)n * kb);
+    if (vb) memcpy(vals, vin, (size_t)n * vb);
+  }
+  free(kscratch);
+  free(vscratch);
+  return rc;
+}
+
+int oracle_segmented_sort(void *keys, void *vals, const int64_t *offsets, int64_t num_segments,
+                          int key_bits, int val_bits, int radix_bits) {
+  if (num_segments < 0 || (num_segments > 0 && !offsets)) return 1;
+  if (key_bits != 32 && key_bits != 64) return 1;
+  if (num_segments > 0 && offsets[0] != 0) return 1;
+  for (int64_t s = 0; s < num_segments; ++s)
+    if (offsets[s + 1] < offsets[s]) return 1;
+  const int kb = key_bits / 8, vb = val_bits / 8;
+  for (int64_t s = 0; s < num_segments; ++s) {
+    int64_t lo = offsets[s], len = offsets[s + 1] - offsets[s];
+    int rc = oracle_radix_sort((char *)keys + lo * kb, vb ? (char *)vals + lo * vb : NULL, len,
+                               key_bits, val_bits, radix_bits);
+    if (rc) return rc;
+  }
+  return 0;
+}

@@ -1,0 +1,40 @@
+/*
+ * Oracle for the LSD radix sort (serial C). TEST INFRASTRUCTURE ONLY: only the
+ * tests, the smoke check and the benchmark's CPU-baseline leg may load it; the
+ * GPU library shares nothing with it.
+ *
+ * All calls return 0 on success, 1 on bad arguments, 2 when malloc fails.
+ * Keys are unsigned, key_bits 32 or 64; payload width val_bits 0 (none), 32 or 64.
+ */
+#ifndef ORACLE_H
+#define ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* One count-sort round (SR4, "first the counting process ... then the output"):
+ * stable distribution of keys_in[0..n) by digit (k >> shift) & (2^digit_bits - 1)
+ * into keys_out; payloads follow. Input and output must not overlap. */
+int oracle_count_sort_round(const void *keys_in, void *keys_out, const void *vals_in,
+                            void *vals_out, int64_t n, int key_bits, int val_bits, int shift,
+                            int digit_bits);
+
+/* ceil(key_bits / radix_bits): the "32 / lg r" rounds of Eq. Ts. */
+int oracle_num_passes(int key_bits, int radix_bits);
+
+/* In-place LSD radix sort with radix 2^radix_bits (1..24), least significant
+ * digit first; stable on equal keys when payloads are present. */
+int oracle_radix_sort(void *keys, void *vals, int64_t n, int key_bits, int val_bits,
+                      int radix_bits);
+
+/* Each [offsets[s], offsets[s+1]) sorted independently (offsets: num_segments+1
+ * entries, offsets[0] = 0, non-decreasing). */
+int oracle_segmented_sort(void *keys, void *vals, const int64_t *offsets, int64_t num_segments,
+                          int key_bits, int val_bits, int radix_bits);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
