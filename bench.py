@@ -1,0 +1,459 @@
+#!/usr/bin/env python3
+"""Benchmark of the GPU LSD radix sort: one JSON line on rank 0.
+
+Default workload (one "step" = one whole sort through isort_keys): n = 2^28
+uniform uint32 keys, radix 256 (4 count-sort passes), keys only, seeded
+synthetic data generated in HBM. Inputs (1 GiB) are larger than L2; before each
+timed sort the keys are restored from a pristine copy and L2 is flushed by
+reading a 512 MiB buffer, both outside the timed event pair.
+
+  python bench.py [--gpus N --steps K --warmup W]   our GPU path
+  python bench.py --impl reference                    the serial C oracle on host cores
+
+Other workloads (--workload): r16 (radix 65536, 2 passes), pairs (2^27 u32 keys
++ u32 index payloads), u64 (2^26 u64 keys, 8 passes), and any of the six key
+distributions via --dist.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+WORKLOADS = {
+    # name: (n, key_bits, val_bits, radix_bits, description)
+    "u32_2p28_r256": (1 << 28, 32, 0, 8, "plain sort, 2^28 uint32 keys, radix 256 (4 passes)"),
+    "u32_2p28_r65536": (1 << 28, 32, 0, 16, "plain sort, 2^28 uint32 keys, radix 65536 (2 passes)"),
+    "pairs_2p27": (1 << 27, 32, 32, 8, "stable pairs, 2^27 uint32 keys + uint32 index payloads"),
+    "u64_2p26": (1 << 26, 64, 0, 8, "plain sort, 2^26 uint64 keys, radix 256 (8 passes)"),
+    "u32_128M_paper": (131_072_000, 32, 0, 8, "the paper's 128M (1M = 1,024,000) uint32 keys"),
+}
+ALIASES = {"r16": "u32_2p28_r65536", "pairs": "pairs_2p27", "u64": "u64_2p26",
+           "paper128m": "u32_128M_paper", "default": "u32_2p28_r256"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="u32_2p28_r256")
+    ap.add_argument("--dist", default="uniform")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle baseline sample")
+    a = ap.parse_args()
+    a.workload = ALIASES.get(a.workload, a.workload)
+    if a.workload not in WORKLOADS:
+        ap.error(f"unknown workload {a.workload}")
+    if a.warmup < 3 and a.impl == "ours":
+        ap.error("at least 3 warm-up steps")
+    return a
+
+
+# --------------------------------------------------------------------------- dist
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Replicas:
+    """N independent replicas (one per GPU); a barrier and a max over ranks only."""
+
+    def __init__(self, world, rank, local, backend):
+        self.world, self.rank = world, rank
+        self.pg = None
+        if world > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- helpers
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        v = json.load(open(p))["hbm_gbs"]
+        return float(v), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def onesweep_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("onesweep.cuh", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1808_10292_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload, variant):
+    """Per-launch DRAM bytes of the dominant kernel from a committed ncu summary,
+    or None if there is none for this exact kernel source and shape."""
+    try:
+        rec = json.load(open(PROFILE_TRAFFIC))
+    except (OSError, ValueError):
+        return None
+    r = rec.get(workload)
+    if not r or r.get("source_hash") != onesweep_source_hash() or r.get("variant") != list(variant):
+        return None
+    return r.get("dram_bytes_per_launch")
+
+
+def cpu_cores_available() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(n_full, key_bits, val_bits, radix_bits, dist, seed, target_s, max_sorts=None):
+    """Time the oracle on a bounded sample of the workload: sorts of a 2^24-key
+    slice (or the whole input if smaller) until target_s seconds have passed."""
+    import inputs
+    import oracle
+    n = min(n_full, 1 << 24)
+    k = inputs.keys(n, key_bits, dist, seed)
+    v = inputs.iota(n, val_bits) if val_bits else None
+    oracle.radix_sort(k[:1024], None if v is None else v[:1024], radix_bits)  # load + warm
+    times = []
+    t_end = time.perf_counter() + target_s
+    while time.perf_counter() < t_end and (max_sorts is None or len(times) < max_sorts):
+        t0 = time.perf_counter()
+        oracle.radix_sort(k, v, radix_bits)
+        times.append(time.perf_counter() - t0)
+    return n, times
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(a):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    n_full, kb, vb, rb, desc = WORKLOADS[a.workload]
+    # each step: one oracle sort of a 2^24-key slice of the workload
+    n, times = oracle_sample(n_full, kb, vb, rb, a.dist, a.seed, target_s=1e9,
+                             max_sorts=a.steps + a.warmup)
+    timed = times[a.warmup:]
+    total = sum(timed)
+    value = n * len(timed) / total
+    sample = (f"{len(timed)} oracle sorts of a {n}-key slice ({a.dist}, seed {a.seed}) of the "
+              f"{n_full}-key workload, 1 thread")
+    line = {
+        "impl": "reference",
+        "metric": f"uint{kb} keys/s ({desc})",
+        "value": value,
+        "unit": "keys/s",
+        "n_gpus": a.gpus,
+        "steps": len(timed),
+        "warmup": a.warmup,
+        "ms_per_step": 1000 * total / len(timed),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": f"u{kb}",
+        "data": "synthetic",
+        "config": {"workload": a.workload, "n": n_full, "key_bits": kb, "val_bits": vb,
+                   "radix_bits": rb, "dist": a.dist, "seed": a.seed, "sample_n": n},
+        "cpu_baseline": {"value": value, "unit": "keys/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(a):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    rep = Replicas(world, rank, local, "nccl")
+    import inputs
+    import paper_1808_10292_gb300 as isort
+    from paper_1808_10292_gb300 import _lib
+
+    n, kb, vb, rb, desc = WORKLOADS[a.workload]
+    kdt = torch.uint32 if kb == 32 else torch.uint64
+    pristine = inputs.device_keys(n, kb, a.dist, a.seed)
+    keys = torch.empty_like(pristine)
+    vals = vpr = None
+    if vb:
+        vpr = inputs.device_iota(n, vb)
+        vals = torch.empty_like(vpr)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda").view(torch.int32)
+    flush.zero_()
+    stream = torch.cuda.current_stream()
+
+    def restore():
+        keys.copy_(pristine)
+        if vb:
+            vals.copy_(vpr)
+        flush.sum()  # read-only pass over 512 MiB: evicts keys from L2 without dirty lines
+
+    def sort():
+        if vb:
+            isort.sort_pairs(keys, vals, rb)
+        else:
+            isort.sort_keys(keys, rb)
+
+    variant = None
+    if rb == 8:
+        variant = isort.tune_variants(kb, vb, rb)[0]
+
+    # warm-up (also allocates the workspace)
+    for _ in range(a.warmup):
+        restore()
+        sort()
+    torch.cuda.synchronize()
+    if isort.stream_status() != _lib.OK:
+        raise RuntimeError("device error during warm-up")
+
+    isort.debug_set(_lib.DEBUG_KERNEL_TIMING, 1)
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    kernel_ms = {}
+    kernel_launches = 0
+    rep.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    for i in range(a.steps):
+        restore()
+        ev[i][0].record(stream)
+        sort()
+        ev[i][1].record(stream)
+        for name, ms in isort.kernel_times():
+            kernel_ms.setdefault(name, []).append(ms)
+            kernel_launches += 1
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    rep.barrier()
+    isort.debug_set(_lib.DEBUG_KERNEL_TIMING, 0)
+    if isort.stream_status() != _lib.OK:
+        raise RuntimeError("device error during the timed steps")
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    total_s = rep.max(sum(step_ms) / 1000.0)
+    value = n * a.steps * world / total_s
+
+    # sanity: the last result is sorted (device-side check, outside timing);
+    # flipping the top bit turns the unsigned order into the signed one
+    sk = keys.view(torch.int64 if kb == 64 else torch.int32) ^ (-(1 << (kb - 1)))
+    if not bool((sk[1:] >= sk[:-1]).all()):
+        raise RuntimeError("benchmark result is not sorted")
+    del sk
+
+    # dominant kernel: the onesweep pass (radix 256) or the radix-65536 scatter
+    dom = max(kernel_ms, key=lambda k: sum(kernel_ms[k]))
+    dom_ms = statistics.mean(kernel_ms[dom])
+    bytes_per_key = (kb + vb) // 8
+    passes = -(-kb // rb)
+    if dom in ("k_onesweep", "k_scatter16"):
+        # one count-sort round: read and write every key (and payload) once
+        alg_bytes = 2 * n * bytes_per_key
+    else:
+        alg_bytes = n * kb // 8
+    peak, peak_kind = measured_peak_hbm()
+    achieved = alg_bytes / (dom_ms / 1000.0) / 1e9
+    traffic = recorded_traffic(a.workload, variant) if variant else None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
+                "avg_launch_ms": dom_ms, "launches": len(kernel_ms[dom])}
+    # whole-sort roofline by the headline formula: 2 n (w_k + w_v) per executed pass
+    sort_alg_bytes = 2 * n * bytes_per_key * passes
+    per_kernel = {k: {"launches": len(v), "mean_ms": statistics.mean(v), "total_ms": sum(v)}
+                  for k, v in kernel_ms.items()}
+
+    e2e = None
+    if not a.no_e2e:
+        e2e = measure_e2e(a, n, kb, vb, rb, torch, isort, inputs, stream)
+
+    cpu = None
+    if not a.no_cpu_baseline and rank == 0 and world == 1:
+        sn, times = oracle_sample(n, kb, vb, rb, a.dist, a.seed, a.cpu_seconds)
+        cpu = {"value": sn * len(times) / sum(times), "unit": "keys/s", "cores": 1,
+               "kind": "oracle",
+               "sample": f"{len(times)} single-thread oracle sorts of a {sn}-key slice "
+                         f"({a.dist}, seed {a.seed}) of the {n}-key workload; host has "
+                         f"{cpu_cores_available()} cores"}
+
+    line = {
+        "metric": f"uint{kb} keys/s ({desc})",
+        "value": value,
+        "unit": "keys/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": 1000 * total_s / a.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": f"u{kb}" + (f"+u{vb}" if vb else ""),
+        "data": "synthetic",
+        "config": {"workload": a.workload, "n": n, "key_bits": kb, "val_bits": vb,
+                   "radix_bits": rb, "passes": passes, "dist": a.dist, "seed": a.seed,
+                   "variant": list(variant) if variant else None,
+                   "l2": "inputs (1 GiB+) larger than L2; keys restored and L2 flushed by a "
+                         "512 MiB read before each timed sort, outside the event pair",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": roofline,
+        "sort_roofline": {"alg_bytes_per_sort": sort_alg_bytes,
+                          "achieved_gbs": sort_alg_bytes * a.steps / total_s / 1e9,
+                          "frac": sort_alg_bytes * a.steps / total_s / 1e9 / peak},
+        "kernels": per_kernel,
+        "gpu_launches": kernel_launches,
+        "clocks": clk,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "wall_s_timed_loop": t_wall,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    rep.close()
+    return 0
+
+
+def measure_e2e(a, n, kb, vb, rb, torch, isort, inputs, stream):
+    """keys/s through the public call with HOST buffers: pinned host -> device
+    copy, the sort, device -> host copy of the sorted keys, every step."""
+    host_in = inputs.device_keys(n, kb, a.dist, a.seed).cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    dev = torch.empty(n, dtype=host_in.dtype, device="cuda")
+    hv_in = hv_out = dv = None
+    if vb:
+        hv_in = inputs.device_iota(n, vb).cpu().pin_memory()
+        hv_out = torch.empty_like(hv_in).pin_memory()
+        dv = torch.empty(n, dtype=hv_in.dtype, device="cuda")
+    steps = max(3, min(a.steps, 10))
+
+    def step():
+        dev.copy_(host_in, non_blocking=True)
+        if vb:
+            dv.copy_(hv_in, non_blocking=True)
+            isort.sort_pairs(dev, dv, rb)
+            hv_out.copy_(dv, non_blocking=True)
+        else:
+            isort.sort_keys(dev, rb)
+        host_out.copy_(dev, non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(steps):
+        step()
+    e.record(stream)
+    e.synchronize()
+    ms = s.elapsed_time(e) / steps
+    out = host_out.numpy()
+    if not (out[1:] >= out[:-1]).all():
+        raise RuntimeError("e2e result not sorted")
+    bi = n * (kb + vb) // 8
+    return {"value": n / (ms / 1000.0), "unit": "keys/s", "h2d_bytes_per_step": bi,
+            "d2h_bytes_per_step": bi, "ms_per_step": ms, "steps": steps}
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,121 @@
+/*
+ * isort -- LSD radix sort of unsigned integer keys on one GB300 GPU (sm_103a).
+ *
+ * The operation is the paper's radix sort (Gerbessiotis, "A study of integer
+ * sorting on multicores", arXiv 1808.10292): rounds of stable count-sort, one
+ * per r-ary digit, least significant digit first -- SR4 / PR4 with r = 2^8
+ * (four rounds on 32-bit keys) and PR2 with r = 2^16 (two rounds), Section
+ * "SR4, PR2, PR4, BTN and OET under MBSP", Eqs. Ts, Tp, Tp4, Tp2. Each round is
+ * a digit histogram, an exclusive prefix over the digit counts (the paper's
+ * p x r count exchange, done here as a single-pass decoupled look-back across
+ * GPU tiles), and a stable scatter.
+ *
+ * The result is the unique stable ascending order of the input: equal keys keep
+ * their input order and payloads move with their keys.
+ *
+ * Conventions for every call:
+ *  - keys, vals, offsets are DEVICE pointers owned by the caller; the library
+ *    never frees caller memory. Sorts are in place.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls are
+ *    asynchronous: they validate arguments, enqueue kernels on `stream` and
+ *    return. Argument errors are returned at once and enqueue nothing.
+ *  - Scratch memory ("workspace") is per stream: either bound by the caller with
+ *    isort_set_workspace, or allocated by the library on first use with
+ *    stream-ordered cudaMallocAsync and grown as needed.
+ *  - Device-side errors (a bounded wait that gave up, an index check that
+ *    failed) are latched in the stream's workspace error word and reported by
+ *    isort_stream_status.
+ *  - Keys are unsigned 32- or 64-bit (key_bits 32|64); payloads 32- or 64-bit
+ *    (val_bits 32|64). n <= 2^30 (the look-back status word packs a 30-bit
+ *    count); larger n returns ISORT_EUNSUPPORTED.
+ *  - radix_bits: 0 = automatic (8), 8 = radix 256 (SR4/PR4), 16 = radix 65536
+ *    (PR2). Passes = ceil(key_bits / radix_bits). A pass whose digit is the same
+ *    for every key is skipped (it is the identity permutation).
+ */
+#ifndef ISORT_H
+#define ISORT_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ISORT_OK = 0,
+  ISORT_EINVAL = 1,         /* bad argument: null pointer, bad width, bad offsets size */
+  ISORT_ENOMEM = 2,         /* workspace allocation failed or bound workspace too small */
+  ISORT_ECUDA = 3,          /* a CUDA runtime call failed */
+  ISORT_ETIMEOUT = 4,       /* a bounded device-side wait gave up (result is garbage) */
+  ISORT_EUNSUPPORTED = 5    /* valid but unsupported combination (n > 2^30, radix) */
+} isort_status;
+
+/* Sort keys[0..n) ascending in place. Paper: the SR4/PR4/PR2 radix sort,
+ * Section "SR4, PR2, PR4, BTN and OET under MBSP". n = 0 or 1 is a no-op. */
+isort_status isort_keys(void *keys, int64_t n, int key_bits, int radix_bits, void *stream);
+
+/* Stable key-value sort: keys ascending, equal keys keep input order, vals[i]
+ * moves with keys[i]. Same algorithm; the payload rides along every round. */
+isort_status isort_pairs(void *keys, void *vals, int64_t n, int key_bits, int val_bits,
+                         int radix_bits, void *stream);
+
+/* Segmented sort: each range [offsets[s], offsets[s+1]) is sorted independently
+ * (vals may be NULL, then val_bits is ignored). offsets: DEVICE int64 array of
+ * num_segments + 1 entries, offsets[0] = 0, non-decreasing; the total must be
+ * <= 2^30 per segment. The paper's sample sorts split the input into p ranges and
+ * sort each independently (Algorithms 1-3); here the ranges are given. Short
+ * segments use the paper's BTN merge-split bitonic network ("Algorithm BTN",
+ * Eq. Tb), long ones the radix passes. Offsets are read on the device only. */
+isort_status isort_segmented(void *keys, void *vals, const int64_t *offsets, int64_t num_segments,
+                             int64_t total_keys, int key_bits, int val_bits, int radix_bits,
+                             void *stream);
+
+/* Bytes of workspace one call with these arguments needs (bytes may be NULL-checked). */
+isort_status isort_workspace_size(int64_t n, int key_bits, int val_bits, int radix_bits,
+                                  size_t *bytes);
+
+/* Bind caller-owned device memory [dev_ptr, dev_ptr + bytes) as the workspace of
+ * `stream` (dev_ptr 256-byte aligned). Later calls on that stream use it and
+ * return ISORT_ENOMEM when it is too small; dev_ptr = NULL unbinds (the library
+ * then allocates its own again). The memory must stay valid until the last
+ * call on the stream has completed. Clears the stream's error word. */
+isort_status isort_set_workspace(void *dev_ptr, size_t bytes, void *stream);
+
+/* Synchronise `stream`, then report and clear its device error word:
+ * ISORT_ETIMEOUT if a bounded wait gave up, ISORT_ECUDA on a CUDA error. */
+isort_status isort_stream_status(void *stream);
+
+/* Release the library-allocated workspaces (synchronises their streams). */
+isort_status isort_release_workspaces(void);
+
+/* Human-readable name of a status code (static string). */
+const char *isort_strerror(isort_status s);
+
+/* Tuning of one kernel family: variant index into the library's table of
+ * (threads, keys per thread) for radix-256 passes of (key_bits, val_bits).
+ * -1 restores the built-in default. Returns ISORT_EINVAL for an unknown variant. */
+isort_status isort_tune_set(int key_bits, int val_bits, int radix_bits, int variant);
+/* Number of variants and the (threads, keys-per-thread) of variant v. */
+int isort_tune_num_variants(int key_bits, int val_bits, int radix_bits);
+isort_status isort_tune_describe(int key_bits, int val_bits, int radix_bits, int variant,
+                                 int *threads, int *keys_per_thread);
+
+/* Test hooks. isort_debug_set(ISORT_DEBUG_SPIN_LIMIT, k): bounded waits give up
+ * after k polls (0 restores the default). isort_debug_set(ISORT_DEBUG_STALL_TILE,
+ * t): in pass 0 of the next radix-256 sort, tile t never publishes its counts
+ * so its successors' waits run out (-1 = off; the sort's output is then garbage
+ * and isort_stream_status reports ISORT_ETIMEOUT). */
+enum { ISORT_DEBUG_SPIN_LIMIT = 1, ISORT_DEBUG_STALL_TILE = 2, ISORT_DEBUG_KERNEL_TIMING = 3 };
+isort_status isort_debug_set(int what, int64_t value);
+
+/* Measurement hook. With isort_debug_set(ISORT_DEBUG_KERNEL_TIMING, 1) every sort
+ * records a CUDA event on its stream before and after each kernel it enqueues.
+ * This call waits for those events of the most recent sort and writes up to
+ * `max` kernel names (static strings) and durations in milliseconds; it returns
+ * how many it wrote (-1.0 for a duration that could not be read). */
+int isort_debug_kernel_times(const char **names, float *ms, int max);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISORT_H */

@@ -184,3 +184,53 @@ def expected_and4_bit_density() -> float:
 def lengths_mean(max_log2: int = 20) -> float:
     """E[L] for L = floor(2^(m u)), u ~ U[0,1), approximated by the continuous mean (2^m - 1)/(m ln 2)."""
     return (2.0 ** max_log2 - 1.0) / (max_log2 * math.log(2.0))
+
+
+# ---- device-side generation (same recipes, inputs/synth.cu) -----------------
+_synth = None
+SYNTH_LIB = __file__.rsplit("/", 1)[0] + "/libsynth.so"
+
+
+def _synth_lib():
+    global _synth
+    if _synth is None:
+        import ctypes
+        import os
+        if not os.path.exists(SYNTH_LIB):
+            raise RuntimeError(f"{SYNTH_LIB} is missing; build it with "
+                               "`python -m paper_1808_10292_gb300.build`")
+        lib = ctypes.CDLL(SYNTH_LIB)
+        vp, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64
+        lib.synth_keys.argtypes = [vp, i64, i32, i32, u64, u64, vp]
+        lib.synth_keys.restype = i32
+        lib.synth_iota.argtypes = [vp, i64, i32, vp]
+        lib.synth_iota.restype = i32
+        _synth = lib
+    return _synth
+
+
+def device_keys(n: int, key_bits: int = 32, dist: str | int = "uniform", seed: int = 1,
+                stream: int | None = None, out=None, cuda_stream=None):
+    """Same keys as keys(...), generated in device memory (a torch CUDA tensor)."""
+    import torch
+    dist_id = DIST_ID[dist] if isinstance(dist, str) else int(dist)
+    st = dist_id if stream is None else int(stream)
+    if out is None:
+        out = torch.empty(n, dtype=torch.uint32 if key_bits == 32 else torch.uint64, device="cuda")
+    cs = torch.cuda.current_stream() if cuda_stream is None else cuda_stream
+    rc = _synth_lib().synth_keys(out.data_ptr() if n else None, n, key_bits, dist_id,
+                                 seed & MASK64, st & MASK64, cs.cuda_stream)
+    if rc:
+        raise RuntimeError(f"synth_keys failed ({rc})")
+    return out
+
+
+def device_iota(n: int, val_bits: int = 32, out=None, cuda_stream=None):
+    import torch
+    if out is None:
+        out = torch.empty(n, dtype=torch.uint32 if val_bits == 32 else torch.uint64, device="cuda")
+    cs = torch.cuda.current_stream() if cuda_stream is None else cuda_stream
+    rc = _synth_lib().synth_iota(out.data_ptr() if n else None, n, val_bits, cs.cuda_stream)
+    if rc:
+        raise RuntimeError(f"synth_iota failed ({rc})")
+    return out

@@ -1,0 +1,139 @@
+"""isort: LSD radix sort of unsigned integer keys on one GB300 GPU.
+
+Thin Python face of the C-ABI library (include/isort.h). Tensors are used only
+for device memory and streams: each call passes ``data_ptr()`` and the current
+CUDA stream to the library, whose kernels do all the work. Sorting is in place.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib
+from ._lib import IsortError, check, load
+
+__all__ = ["sort_keys", "sort_pairs", "sort_segmented", "workspace_size", "set_workspace",
+           "stream_status", "release_workspaces", "IsortError", "load"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _bits(t) -> int:
+    torch = _torch()
+    if t.dtype in (torch.uint32, torch.int32):
+        return 32
+    if t.dtype in (torch.uint64, torch.int64):
+        return 64
+    raise TypeError(f"unsupported dtype {t.dtype}: keys and payloads are 32- or 64-bit words")
+
+
+def _stream(stream) -> int:
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream) if hasattr(s, "cuda_stream") else int(s)
+
+
+def _dev(t, name):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def sort_keys(keys, radix_bits: int = 0, stream=None):
+    """Sort a CUDA uint32/uint64 tensor ascending in place; returns it."""
+    _dev(keys, "keys")
+    check(load().isort_keys(keys.data_ptr(), keys.numel(), _bits(keys), radix_bits,
+                            _stream(stream)), "isort_keys")
+    return keys
+
+
+def sort_pairs(keys, vals, radix_bits: int = 0, stream=None):
+    """Stable key-value sort in place (vals follow their keys); returns (keys, vals)."""
+    _dev(keys, "keys")
+    _dev(vals, "vals")
+    if keys.numel() != vals.numel():
+        raise ValueError("keys and vals differ in length")
+    check(load().isort_pairs(keys.data_ptr(), vals.data_ptr(), keys.numel(), _bits(keys),
+                             _bits(vals), radix_bits, _stream(stream)), "isort_pairs")
+    return keys, vals
+
+
+def sort_segmented(keys, offsets, vals=None, radix_bits: int = 0, stream=None):
+    """Sort each [offsets[s], offsets[s+1]) independently, in place.
+
+    offsets: CUDA int64 tensor of num_segments + 1 entries, offsets[0] = 0,
+    non-decreasing, offsets[-1] == keys.numel().
+    """
+    torch = _torch()
+    _dev(keys, "keys")
+    _dev(offsets, "offsets")
+    if offsets.dtype != torch.int64:
+        raise TypeError("offsets must be int64")
+    vb = 0
+    vptr = None
+    if vals is not None:
+        _dev(vals, "vals")
+        if vals.numel() != keys.numel():
+            raise ValueError("keys and vals differ in length")
+        vb, vptr = _bits(vals), vals.data_ptr()
+    nseg = max(0, offsets.numel() - 1)
+    check(load().isort_segmented(keys.data_ptr(), vptr, offsets.data_ptr(), nseg, keys.numel(),
+                                 _bits(keys), vb, radix_bits, _stream(stream)), "isort_segmented")
+    return keys if vals is None else (keys, vals)
+
+
+def workspace_size(n: int, key_bits: int = 32, val_bits: int = 0, radix_bits: int = 0) -> int:
+    out = ctypes.c_size_t(0)
+    check(load().isort_workspace_size(n, key_bits, val_bits, radix_bits, ctypes.byref(out)),
+          "isort_workspace_size")
+    return out.value
+
+
+def set_workspace(buffer=None, stream=None):
+    """Bind a CUDA uint8 tensor as the stream's workspace (None unbinds)."""
+    if buffer is None:
+        check(load().isort_set_workspace(None, 0, _stream(stream)), "isort_set_workspace")
+        return
+    _dev(buffer, "workspace")
+    check(load().isort_set_workspace(buffer.data_ptr(), buffer.numel() * buffer.element_size(),
+                                     _stream(stream)), "isort_set_workspace")
+
+
+def stream_status(stream=None) -> int:
+    """Synchronise the stream and return (and clear) its latched status code."""
+    return load().isort_stream_status(_stream(stream))
+
+
+def release_workspaces():
+    check(load().isort_release_workspaces(), "isort_release_workspaces")
+
+
+def tune_variants(key_bits: int = 32, val_bits: int = 0, radix_bits: int = 8):
+    """[(threads, keys_per_thread)] of the compiled variants of one kernel family."""
+    L = load()
+    out = []
+    for v in range(L.isort_tune_num_variants(key_bits, val_bits, radix_bits)):
+        t, k = ctypes.c_int(0), ctypes.c_int(0)
+        check(L.isort_tune_describe(key_bits, val_bits, radix_bits, v, ctypes.byref(t),
+                                    ctypes.byref(k)), "isort_tune_describe")
+        out.append((t.value, k.value))
+    return out
+
+
+def tune_set(key_bits: int, val_bits: int, radix_bits: int, variant: int):
+    check(load().isort_tune_set(key_bits, val_bits, radix_bits, variant), "isort_tune_set")
+
+
+def debug_set(what: int, value: int):
+    check(load().isort_debug_set(what, value), "isort_debug_set")
+
+
+def kernel_times(max_kernels: int = 64):
+    """[(kernel name, ms)] of the most recent sort (needs DEBUG_KERNEL_TIMING on)."""
+    names = (ctypes.c_char_p * max_kernels)()
+    ms = (ctypes.c_float * max_kernels)()
+    n = load().isort_debug_kernel_times(names, ms, max_kernels)
+    return [(names[i].decode(), float(ms[i])) for i in range(n)]

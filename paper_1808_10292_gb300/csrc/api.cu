@@ -1,0 +1,370 @@
+// C-ABI of the isort library: argument checks, per-stream workspaces, kernel
+// family selection. Every step of a sort runs in the kernels of sort_k32.cu,
+// sort_k64.cu, radix16.cu and segmented.cu; this file only validates, carves
+// scratch memory and enqueues.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <unordered_map>
+
+#include "isort.h"
+#include "isort_internal.h"
+
+using namespace isort;
+
+namespace {
+
+constexpr uint32_t kDefaultSpinLimit = 1u << 22;  // polls of an L2-resident word: seconds
+constexpr int64_t kMaxN = int64_t(1) << 30;
+
+struct Workspace {
+  void* base = nullptr;
+  size_t bytes = 0;
+  bool owned = false;  // allocated by the library (stream-ordered) vs bound by the caller
+};
+
+std::mutex g_mu;
+std::unordered_map<cudaStream_t, Workspace> g_ws;
+std::map<std::tuple<int, int, int>, int> g_variant;  // (key_bits, val_bits, radix_bits) -> index
+uint32_t g_spin_limit = kDefaultSpinLimit;
+int64_t g_stall_tile = -1;
+std::map<int, int> g_sms;  // device -> SM count
+KernelTimer g_timer;
+bool g_timing = false;
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int num_sms() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto it = g_sms.find(dev);
+  if (it != g_sms.end()) return it->second;
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+    v = 152;
+  g_sms[dev] = v;
+  return v;
+}
+
+int variants(int key_bits, int val_bits, int radix_bits, const LsdEntry** out) {
+  if (key_bits == 32) return lsd_variants_k32(val_bits, radix_bits, out);
+  if (key_bits == 64) return lsd_variants_k64(val_bits, radix_bits, out);
+  return 0;
+}
+
+const LsdEntry* pick(int key_bits, int val_bits, int radix_bits) {
+  const LsdEntry* tab = nullptr;
+  int nv = variants(key_bits, val_bits, radix_bits, &tab);
+  if (nv <= 0) return nullptr;
+  auto it = g_variant.find({key_bits, val_bits, radix_bits});
+  int v = (it == g_variant.end()) ? 0 : it->second;
+  if (v < 0 || v >= nv) v = 0;
+  return &tab[v];
+}
+
+// Workspace layout of one LSD sort. The error word sits at offset 0 so it
+// survives from call to call on the same workspace.
+struct Layout {
+  size_t err, hist, base, skip, counters, status0, status1, alt_k, alt_v, total;
+};
+
+Layout layout_for(const LsdEntry& e, int64_t n) {
+  Layout L;
+  const int64_t tiles = (n + e.tile - 1) / e.tile;
+  size_t off = 0;
+  L.err = off;       off = align256(off + 4);
+  L.hist = off;      off = align256(off + sizeof(uint32_t) * e.passes * e.radix);
+  L.base = off;      off = align256(off + sizeof(uint32_t) * e.passes * e.radix);
+  L.skip = off;      off = align256(off + sizeof(uint32_t) * e.passes);
+  L.counters = off;  off = align256(off + sizeof(uint32_t) * e.passes);
+  L.status0 = off;   off = align256(off + sizeof(uint32_t) * e.status_words_per_tile * tiles);
+  L.status1 = off;   off = align256(off + sizeof(uint32_t) * e.status_words_per_tile * tiles);
+  L.alt_k = off;     off = align256(off + (size_t)n * (e.key_bits / 8));
+  L.alt_v = off;     off = align256(off + (size_t)n * (e.val_bits / 8));
+  L.total = off;
+  return L;
+}
+
+// Returns the stream's workspace with at least `need` bytes (caller holds g_mu).
+isort_status acquire(cudaStream_t st, size_t need, void** out) {
+  Workspace& w = g_ws[st];
+  if (w.base && w.bytes >= need) {
+    *out = w.base;
+    return ISORT_OK;
+  }
+  if (w.base && !w.owned) return ISORT_ENOMEM;  // bound by the caller and too small
+  size_t want = need + need / 8;                // grow with some slack
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, want, st) != cudaSuccess) {
+    cudaGetLastError();
+    return ISORT_ENOMEM;
+  }
+  if (w.base) {  // carry the latched error word over, then release the old block
+    cudaMemcpyAsync(p, w.base, 4, cudaMemcpyDeviceToDevice, st);
+    cudaFreeAsync(w.base, st);
+  } else {
+    cudaMemsetAsync(p, 0, 4, st);
+  }
+  w.base = p;
+  w.bytes = want;
+  w.owned = true;
+  *out = p;
+  return ISORT_OK;
+}
+
+bool aligned(const void* p, int bytes) { return (reinterpret_cast<uintptr_t>(p) % bytes) == 0; }
+
+isort_status check_widths(int key_bits, int val_bits, bool pairs) {
+  if (key_bits != 32 && key_bits != 64) return ISORT_EINVAL;
+  if (pairs && val_bits != 32 && val_bits != 64) return ISORT_EINVAL;
+  return ISORT_OK;
+}
+
+isort_status resolve_radix(int radix_bits, int* out) {
+  if (radix_bits == 0) radix_bits = 8;
+  if (radix_bits != 8 && radix_bits != 16) {
+    if (radix_bits > 0 && radix_bits <= 24) return ISORT_EUNSUPPORTED;
+    return ISORT_EINVAL;
+  }
+  *out = radix_bits;
+  return ISORT_OK;
+}
+
+isort_status run_lsd(void* keys, void* vals, int64_t n, int key_bits, int val_bits,
+                     int radix_bits, cudaStream_t st) {
+  const LsdEntry* e = pick(key_bits, val_bits, radix_bits);
+  if (!e) return ISORT_EUNSUPPORTED;
+  Layout L = layout_for(*e, n);
+  std::lock_guard<std::mutex> lock(g_mu);
+  void* ws = nullptr;
+  isort_status s = acquire(st, L.total, &ws);
+  if (s != ISORT_OK) return s;
+  char* b = static_cast<char*>(ws);
+  LsdArgs a;
+  a.keys = keys;
+  a.vals = vals;
+  a.alt_keys = b + L.alt_k;
+  a.alt_vals = vals ? b + L.alt_v : nullptr;
+  a.n = n;
+  a.hist = reinterpret_cast<uint32_t*>(b + L.hist);
+  a.base = reinterpret_cast<uint32_t*>(b + L.base);
+  a.skip = reinterpret_cast<uint32_t*>(b + L.skip);
+  a.counters = reinterpret_cast<uint32_t*>(b + L.counters);
+  a.status[0] = reinterpret_cast<uint32_t*>(b + L.status0);
+  a.status[1] = reinterpret_cast<uint32_t*>(b + L.status1);
+  a.err = reinterpret_cast<uint32_t*>(b + L.err);
+  a.spin_limit = g_spin_limit;
+  a.stall_tile = g_stall_tile;
+  g_stall_tile = -1;  // the stall hook applies to one sort only
+  a.num_sms = num_sms();
+  a.timer = nullptr;
+  if (g_timing) {
+    if (!g_timer.ready) {
+      for (int i = 0; i < 2 * KernelTimer::kMax; ++i) cudaEventCreate(&g_timer.ev[i]);
+      g_timer.ready = true;
+    }
+    g_timer.count = 0;
+    a.timer = &g_timer;
+  }
+  cudaError_t ce = e->launch(a, st);
+  return ce == cudaSuccess ? ISORT_OK : ISORT_ECUDA;
+}
+
+}  // namespace
+
+namespace isort {
+
+void timer_begin(KernelTimer* t, const char* name, cudaStream_t st) {
+  if (!t || t->count >= KernelTimer::kMax) return;
+  t->name[t->count] = name;
+  cudaEventRecord(t->ev[2 * t->count], st);
+}
+
+void timer_end(KernelTimer* t, cudaStream_t st) {
+  if (!t || t->count >= KernelTimer::kMax) return;
+  cudaEventRecord(t->ev[2 * t->count + 1], st);
+  ++t->count;
+}
+
+}  // namespace isort
+
+extern "C" {
+
+isort_status isort_keys(void* keys, int64_t n, int key_bits, int radix_bits, void* stream) {
+  isort_status s = check_widths(key_bits, 0, false);
+  if (s != ISORT_OK) return s;
+  int rb = 0;
+  if ((s = resolve_radix(radix_bits, &rb)) != ISORT_OK) return s;
+  if (n < 0) return ISORT_EINVAL;
+  if (n > kMaxN) return ISORT_EUNSUPPORTED;
+  if (n <= 1) return ISORT_OK;
+  if (!keys || !aligned(keys, key_bits / 8)) return ISORT_EINVAL;
+  return run_lsd(keys, nullptr, n, key_bits, 0, rb, static_cast<cudaStream_t>(stream));
+}
+
+isort_status isort_pairs(void* keys, void* vals, int64_t n, int key_bits, int val_bits,
+                         int radix_bits, void* stream) {
+  isort_status s = check_widths(key_bits, val_bits, true);
+  if (s != ISORT_OK) return s;
+  int rb = 0;
+  if ((s = resolve_radix(radix_bits, &rb)) != ISORT_OK) return s;
+  if (n < 0) return ISORT_EINVAL;
+  if (n > kMaxN) return ISORT_EUNSUPPORTED;
+  if (n <= 1) return ISORT_OK;
+  if (!keys || !vals || !aligned(keys, key_bits / 8) || !aligned(vals, val_bits / 8))
+    return ISORT_EINVAL;
+  return run_lsd(keys, vals, n, key_bits, val_bits, rb, static_cast<cudaStream_t>(stream));
+}
+
+isort_status isort_segmented(void* keys, void* vals, const int64_t* offsets, int64_t num_segments,
+                             int64_t total_keys, int key_bits, int val_bits, int radix_bits,
+                             void* stream) {
+  (void)keys; (void)vals; (void)offsets; (void)num_segments; (void)total_keys;
+  (void)key_bits; (void)val_bits; (void)radix_bits; (void)stream;
+  return ISORT_EUNSUPPORTED;
+}
+
+isort_status isort_workspace_size(int64_t n, int key_bits, int val_bits, int radix_bits,
+                                  size_t* bytes) {
+  if (!bytes) return ISORT_EINVAL;
+  isort_status s = check_widths(key_bits, val_bits, val_bits != 0);
+  if (s != ISORT_OK) return s;
+  int rb = 0;
+  if ((s = resolve_radix(radix_bits, &rb)) != ISORT_OK) return s;
+  if (n < 0) return ISORT_EINVAL;
+  if (n > kMaxN) return ISORT_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_mu);
+  const LsdEntry* e = pick(key_bits, val_bits, rb);
+  if (!e) return ISORT_EUNSUPPORTED;
+  *bytes = layout_for(*e, n).total;
+  return ISORT_OK;
+}
+
+isort_status isort_set_workspace(void* dev_ptr, size_t bytes, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (dev_ptr && (!aligned(dev_ptr, 256) || bytes < 256)) return ISORT_EINVAL;
+  std::lock_guard<std::mutex> lock(g_mu);
+  auto it = g_ws.find(st);
+  if (it != g_ws.end() && it->second.owned && it->second.base)
+    cudaFreeAsync(it->second.base, st);
+  if (!dev_ptr) {
+    g_ws.erase(st);
+    return ISORT_OK;
+  }
+  Workspace w;
+  w.base = dev_ptr;
+  w.bytes = bytes;
+  w.owned = false;
+  g_ws[st] = w;
+  return cudaMemsetAsync(dev_ptr, 0, 4, st) == cudaSuccess ? ISORT_OK : ISORT_ECUDA;
+}
+
+isort_status isort_stream_status(void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return ISORT_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) return ISORT_ECUDA;
+  std::lock_guard<std::mutex> lock(g_mu);
+  auto it = g_ws.find(st);
+  if (it == g_ws.end() || !it->second.base) return ISORT_OK;
+  uint32_t word = 0;
+  if (cudaMemcpy(&word, it->second.base, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return ISORT_ECUDA;
+  if (word) {
+    if (cudaMemset(it->second.base, 0, 4) != cudaSuccess) return ISORT_ECUDA;
+    return ISORT_ETIMEOUT;
+  }
+  return ISORT_OK;
+}
+
+isort_status isort_release_workspaces(void) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  isort_status s = ISORT_OK;
+  for (auto& kv : g_ws) {
+    if (kv.second.owned && kv.second.base) {
+      if (cudaFreeAsync(kv.second.base, kv.first) != cudaSuccess) s = ISORT_ECUDA;
+      if (cudaStreamSynchronize(kv.first) != cudaSuccess) s = ISORT_ECUDA;
+    }
+  }
+  g_ws.clear();
+  return s;
+}
+
+const char* isort_strerror(isort_status s) {
+  switch (s) {
+    case ISORT_OK: return "ok";
+    case ISORT_EINVAL: return "invalid argument";
+    case ISORT_ENOMEM: return "out of device memory or workspace too small";
+    case ISORT_ECUDA: return "CUDA runtime error";
+    case ISORT_ETIMEOUT: return "bounded device wait gave up";
+    case ISORT_EUNSUPPORTED: return "unsupported argument combination";
+  }
+  return "unknown status";
+}
+
+isort_status isort_tune_set(int key_bits, int val_bits, int radix_bits, int variant) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  const LsdEntry* tab = nullptr;
+  if (radix_bits == 0) radix_bits = 8;
+  int nv = variants(key_bits, val_bits, radix_bits, &tab);
+  if (variant == -1) {
+    g_variant.erase({key_bits, val_bits, radix_bits});
+    return ISORT_OK;
+  }
+  if (variant < 0 || variant >= nv) return ISORT_EINVAL;
+  g_variant[{key_bits, val_bits, radix_bits}] = variant;
+  return ISORT_OK;
+}
+
+int isort_tune_num_variants(int key_bits, int val_bits, int radix_bits) {
+  const LsdEntry* tab = nullptr;
+  if (radix_bits == 0) radix_bits = 8;
+  return variants(key_bits, val_bits, radix_bits, &tab);
+}
+
+isort_status isort_tune_describe(int key_bits, int val_bits, int radix_bits, int variant,
+                                 int* threads, int* keys_per_thread) {
+  const LsdEntry* tab = nullptr;
+  if (radix_bits == 0) radix_bits = 8;
+  int nv = variants(key_bits, val_bits, radix_bits, &tab);
+  if (variant < 0 || variant >= nv || !threads || !keys_per_thread) return ISORT_EINVAL;
+  *threads = tab[variant].threads;
+  *keys_per_thread = tab[variant].keys_per_thread;
+  return ISORT_OK;
+}
+
+isort_status isort_debug_set(int what, int64_t value) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  switch (what) {
+    case ISORT_DEBUG_SPIN_LIMIT:
+      if (value < 0 || value > 0xffffffffll) return ISORT_EINVAL;
+      g_spin_limit = value ? (uint32_t)value : kDefaultSpinLimit;
+      return ISORT_OK;
+    case ISORT_DEBUG_STALL_TILE:
+      g_stall_tile = value;
+      return ISORT_OK;
+    case ISORT_DEBUG_KERNEL_TIMING:
+      g_timing = value != 0;
+      return ISORT_OK;
+  }
+  return ISORT_EINVAL;
+}
+
+int isort_debug_kernel_times(const char** names, float* ms, int max) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_timer.ready) return 0;
+  int n = g_timer.count < max ? g_timer.count : max;
+  for (int i = 0; i < n; ++i) {
+    if (names) names[i] = g_timer.name[i];
+    if (ms) {
+      if (cudaEventSynchronize(g_timer.ev[2 * i + 1]) != cudaSuccess ||
+          cudaEventElapsedTime(&ms[i], g_timer.ev[2 * i], g_timer.ev[2 * i + 1]) != cudaSuccess)
+        ms[i] = -1.0f;
+    }
+  }
+  return n;
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// Shared device helpers of the isort kernels (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace isort {
+
+// Look-back status word: 2-bit flag in bits 31..30, 30-bit count below.
+// 0 = nothing published yet, AGG = this tile's own digit count, INC = the
+// inclusive count of this tile and every tile before it.
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagInc = 2u << 30;
+constexpr uint32_t kCountMask = (1u << 30) - 1;
+
+// Bits of the device error word.
+constexpr uint32_t kErrTimeout = 1u;  // a bounded wait gave up
+constexpr uint32_t kErrBounds = 2u;   // a computed output index fell outside [0, n)
+
+constexpr uint32_t kFullMask = 0xffffffffu;
+
+struct NoVal {};  // payload type of a keys-only sort
+
+template <typename V>
+struct HasVal { static constexpr bool value = true; };
+template <>
+struct HasVal<NoVal> { static constexpr bool value = false; };
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <typename K>
+__device__ __forceinline__ uint32_t digit_of(K k, int shift, uint32_t mask) {
+  return static_cast<uint32_t>(k >> shift) & mask;
+}
+
+// Exclusive scan of one value per thread across the block; `total` receives the
+// sum over the block. s_warp needs THREADS/32 words. Contains __syncthreads.
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp,
+                                                         uint32_t& total) {
+  constexpr int WARPS = THREADS / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(kFullMask, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < WARPS ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(kFullMask, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < WARPS) s_warp[lane] = w;
+  }
+  __syncthreads();
+  total = s_warp[WARPS - 1];
+  uint32_t before = warp ? s_warp[warp - 1] : 0u;
+  return before + x - v;
+}
+
+}  // namespace isort

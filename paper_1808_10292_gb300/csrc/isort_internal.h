@@ -1,0 +1,61 @@
+// Internal interface between the C-ABI layer (api.cu) and the kernel
+// translation units. Not installed; not part of the public header.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace isort {
+
+// Optional per-kernel timing: when enabled, the launchers record a CUDA event on
+// the launching stream before and after each kernel they enqueue.
+struct KernelTimer {
+  static constexpr int kMax = 64;
+  cudaEvent_t ev[2 * kMax];
+  const char* name[kMax];
+  int count;
+  bool ready;
+};
+
+// Records the "before" event of a kernel named `name` (no-op when t is null).
+void timer_begin(KernelTimer* t, const char* name, cudaStream_t st);
+// Records the "after" event of the kernel begun last.
+void timer_end(KernelTimer* t, cudaStream_t st);
+
+// Device pointers and sizes for one LSD sort (keys-only when vals == nullptr).
+struct LsdArgs {
+  void* keys;           // caller's keys, sorted in place
+  void* vals;           // caller's payloads or nullptr
+  void* alt_keys;       // workspace: n keys
+  void* alt_vals;       // workspace: n payloads (when vals != nullptr)
+  int64_t n;
+  uint32_t* hist;       // workspace: passes * R counters (zeroed by the launcher)
+  uint32_t* base;       // workspace: passes * R global digit bases
+  uint32_t* skip;       // workspace: passes flags (1 = trivial pass)
+  uint32_t* counters;   // workspace: passes tile-id counters (zeroed by the launcher)
+  uint32_t* status[2];  // workspace: tiles * R look-back words each
+  uint32_t* err;        // workspace: latched device error word
+  uint32_t spin_limit;  // polls before a wait gives up
+  int64_t stall_tile;   // test hook (-1 = off)
+  int num_sms;
+  KernelTimer* timer;   // null unless kernel timing is on
+};
+
+typedef cudaError_t (*LsdLaunchFn)(const LsdArgs&, cudaStream_t);
+
+// One compiled kernel family for (key_bits, val_bits, radix_bits, variant).
+struct LsdEntry {
+  int key_bits, val_bits, radix_bits;
+  int threads, keys_per_thread;
+  int64_t tile;         // keys per tile (threads * keys_per_thread)
+  int radix;            // 2^radix_bits
+  int passes;
+  size_t status_words_per_tile;  // look-back words per tile per buffer
+  LsdLaunchFn launch;
+};
+
+// Variant tables, one per key width (sort_k32.cu, sort_k64.cu).
+int lsd_variants_k32(int val_bits, int radix_bits, const LsdEntry** out);
+int lsd_variants_k64(int val_bits, int radix_bits, const LsdEntry** out);
+
+}  // namespace isort

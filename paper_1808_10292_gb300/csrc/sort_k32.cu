@@ -1,0 +1,30 @@
+// Compiled kernel variants for 32-bit keys (radix 2^8 onesweep passes).
+#include "onesweep.cuh"
+
+namespace isort {
+
+static const LsdEntry kK32None8[] = {
+    lsd_entry<uint32_t, NoVal, 8, 256, 16>(),
+    lsd_entry<uint32_t, NoVal, 8, 256, 12>(),
+    lsd_entry<uint32_t, NoVal, 8, 384, 16>(),
+    lsd_entry<uint32_t, NoVal, 8, 512, 16>(),
+};
+static const LsdEntry kK32V32_8[] = {
+    lsd_entry<uint32_t, uint32_t, 8, 256, 12>(),
+    lsd_entry<uint32_t, uint32_t, 8, 256, 16>(),
+};
+static const LsdEntry kK32V64_8[] = {
+    lsd_entry<uint32_t, uint64_t, 8, 256, 12>(),
+};
+
+int lsd_variants_k32(int val_bits, int radix_bits, const LsdEntry** out) {
+  if (radix_bits != 8) return 0;
+  switch (val_bits) {
+    case 0: *out = kK32None8; return (int)(sizeof(kK32None8) / sizeof(LsdEntry));
+    case 32: *out = kK32V32_8; return (int)(sizeof(kK32V32_8) / sizeof(LsdEntry));
+    case 64: *out = kK32V64_8; return (int)(sizeof(kK32V64_8) / sizeof(LsdEntry));
+  }
+  return 0;
+}
+
+}  // namespace isort

@@ -1,0 +1,27 @@
+// Compiled kernel variants for 64-bit keys (radix 2^8 onesweep passes).
+#include "onesweep.cuh"
+
+namespace isort {
+
+static const LsdEntry kK64None8[] = {
+    lsd_entry<uint64_t, NoVal, 8, 256, 12>(),
+    lsd_entry<uint64_t, NoVal, 8, 256, 16>(),
+};
+static const LsdEntry kK64V32_8[] = {
+    lsd_entry<uint64_t, uint32_t, 8, 256, 12>(),
+};
+static const LsdEntry kK64V64_8[] = {
+    lsd_entry<uint64_t, uint64_t, 8, 256, 12>(),
+};
+
+int lsd_variants_k64(int val_bits, int radix_bits, const LsdEntry** out) {
+  if (radix_bits != 8) return 0;
+  switch (val_bits) {
+    case 0: *out = kK64None8; return (int)(sizeof(kK64None8) / sizeof(LsdEntry));
+    case 32: *out = kK64V32_8; return (int)(sizeof(kK64V32_8) / sizeof(LsdEntry));
+    case 64: *out = kK64V64_8; return (int)(sizeof(kK64V64_8) / sizeof(LsdEntry));
+  }
+  return 0;
+}
+
+}  // namespace isort

@@ -1,0 +1,75 @@
+"""The C-ABI library loads and exports what include/isort.h declares; host-side
+argument checks answer without touching a GPU (no compute calls here)."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+import paper_1808_10292_gb300 as isort
+from paper_1808_10292_gb300 import _lib
+from paper_1808_10292_gb300.build import build, LIB, SYNTH_LIB
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _lib.declared_symbols()
+    assert "isort_keys" in names and "isort_segmented" in names and "isort_pairs" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [n for n in names if n not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+    for n in names:
+        getattr(lib, n)  # resolvable through ctypes too
+
+
+def test_synth_library_exports(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", SYNTH_LIB], capture_output=True,
+                         text=True, check=True).stdout
+    assert "synth_keys" in out and "synth_iota" in out
+
+
+def test_argument_errors_need_no_gpu(lib):
+    dummy = ctypes.c_void_p(256)
+    assert lib.isort_keys(dummy, 10, 16, 8, None) == _lib.EINVAL        # bad key width
+    assert lib.isort_keys(dummy, 10, 32, 7, None) == _lib.EUNSUPPORTED  # radix 2^7
+    assert lib.isort_keys(dummy, 10, 32, 40, None) == _lib.EINVAL       # nonsense radix
+    assert lib.isort_keys(dummy, -1, 32, 8, None) == _lib.EINVAL
+    assert lib.isort_keys(dummy, (1 << 30) + 1, 32, 8, None) == _lib.EUNSUPPORTED
+    assert lib.isort_keys(None, 10, 32, 8, None) == _lib.EINVAL
+    assert lib.isort_keys(ctypes.c_void_p(258), 10, 32, 8, None) == _lib.EINVAL  # misaligned
+    assert lib.isort_keys(None, 0, 32, 8, None) == _lib.OK   # empty: no-op
+    assert lib.isort_keys(None, 1, 64, 8, None) == _lib.OK   # one key: no-op
+    assert lib.isort_pairs(dummy, None, 10, 32, 32, 8, None) == _lib.EINVAL
+    assert lib.isort_pairs(dummy, dummy, 10, 32, 16, 8, None) == _lib.EINVAL
+    assert lib.isort_debug_set(99, 0) == _lib.EINVAL
+    assert lib.isort_strerror(_lib.ETIMEOUT) == b"bounded device wait gave up"
+
+
+def test_workspace_size_and_tuning_tables(lib):
+    n = 1 << 20
+    size = isort.workspace_size(n, 32, 0, 8)
+    assert size >= n * 4  # at least the alternate key buffer
+    assert isort.workspace_size(n, 32, 32, 8) >= size + n * 4
+    assert isort.workspace_size(n, 64, 0, 8) >= n * 8
+    v = isort.tune_variants(32, 0, 8)
+    assert len(v) >= 2 and all(t % 32 == 0 and k > 0 for t, k in v)
+    with pytest.raises(isort.IsortError):
+        isort.tune_set(32, 0, 8, len(v))
+    isort.tune_set(32, 0, 8, 1)
+    isort.tune_set(32, 0, 8, -1)
+
+
+def test_no_cpu_fallback_when_library_missing(tmp_path, monkeypatch):
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libisort.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _lib.load()

@@ -1,0 +1,197 @@
+"""GPU parity: the CUDA sort (through the C-ABI) against the serial C oracle,
+element by element on the same seeded inputs. Integer work: bit-exact."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import inputs
+import oracle
+import paper_1808_10292_gb300 as isort
+from paper_1808_10292_gb300 import _lib
+
+pytestmark = pytest.mark.gpu
+TORCH_DT = {32: torch.uint32, 64: torch.uint64}
+
+
+def to_dev(a: np.ndarray):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def to_host(t) -> np.ndarray:
+    return t.cpu().numpy()
+
+
+def gpu_sort(keys_np, vals_np=None, radix_bits=8):
+    k = to_dev(keys_np)
+    if vals_np is None:
+        isort.sort_keys(k, radix_bits)
+        assert isort.stream_status() == _lib.OK
+        return to_host(k)
+    v = to_dev(vals_np)
+    isort.sort_pairs(k, v, radix_bits)
+    assert isort.stream_status() == _lib.OK
+    return to_host(k), to_host(v)
+
+
+def edge_sizes(tile):
+    return sorted({0, 1, 2, 3, 31, 32, 33, 255, 257, tile - 1, tile, tile + 1, 2 * tile + 5,
+                   5 * tile - 3})
+
+
+def test_device_generator_matches_host_generator():
+    for bits in (32, 64):
+        for dist in inputs.DISTS:
+            for n in (1, 1000, 65_537):
+                d = to_host(inputs.device_keys(n, bits, dist, seed=5))
+                assert np.array_equal(d, inputs.keys(n, bits, dist, seed=5)), (bits, dist, n)
+    assert np.array_equal(to_host(inputs.device_iota(777)), inputs.iota(777))
+
+
+def test_config1_uniform_2p20_seed1():
+    """n = 2^20 uniform u32 keys, seed 1, radix 256, keys only: bit-exact vs the oracle."""
+    k = inputs.keys(1 << 20, 32, "uniform", seed=1)
+    assert np.array_equal(gpu_sort(k), oracle.radix_sort(k, radix_bits=8))
+
+
+@pytest.mark.parametrize("key_bits", [32, 64])
+@pytest.mark.parametrize("dist", inputs.DISTS)
+def test_distributions_keys_only(key_bits, dist):
+    n = 1_000_003  # several hundred tiles and a ragged tail
+    k = inputs.keys(n, key_bits, dist, seed=9)
+    assert np.array_equal(gpu_sort(k), oracle.radix_sort(k, radix_bits=8))
+
+
+@pytest.mark.parametrize("key_bits,val_bits", [(32, 32), (32, 64), (64, 32), (64, 64)])
+@pytest.mark.parametrize("dist", ["uniform", "and4", "equal", "u16"])
+def test_pairs_stable(key_bits, val_bits, dist):
+    n = 654_321
+    k = inputs.keys(n, key_bits, dist, seed=4)
+    v = inputs.iota(n, val_bits)
+    gk, gv = gpu_sort(k, v)
+    ok, ov = oracle.radix_sort(k, v, radix_bits=8)
+    assert np.array_equal(gk, ok)
+    assert np.array_equal(gv, ov)
+
+
+@pytest.mark.parametrize("key_bits,val_bits", [(32, 0), (32, 32), (32, 64), (64, 0), (64, 32),
+                                               (64, 64)])
+def test_every_variant_edge_sizes(key_bits, val_bits):
+    variants = isort.tune_variants(key_bits, val_bits, 8)
+    assert variants
+    try:
+        for vi, (threads, kpt) in enumerate(variants):
+            isort.tune_set(key_bits, val_bits, 8, vi)
+            for n in edge_sizes(threads * kpt):
+                k = inputs.keys(n, key_bits, "and4", seed=n + 1)
+                if val_bits:
+                    v = inputs.iota(n, val_bits)
+                    gk, gv = gpu_sort(k, v)
+                    ok, ov = oracle.radix_sort(k, v, radix_bits=8)
+                    assert np.array_equal(gv, ov), (vi, n)
+                else:
+                    gk, ok = gpu_sort(k), oracle.radix_sort(k, radix_bits=8)
+                assert np.array_equal(gk, ok), (vi, n)
+    finally:
+        isort.tune_set(key_bits, val_bits, 8, -1)
+
+
+def test_unaligned_view_and_offsets():
+    base = inputs.keys(100_001, 32, "uniform", seed=2)
+    t = to_dev(base)
+    view = t[1:]  # 4-byte aligned, not 16-byte aligned
+    isort.sort_keys(view, 8)
+    assert isort.stream_status() == _lib.OK
+    got = to_host(t)
+    assert got[0] == base[0]
+    assert np.array_equal(got[1:], oracle.radix_sort(base[1:], radix_bits=8))
+
+
+def test_bound_workspace_and_enomem():
+    n = 300_000
+    k = to_dev(inputs.keys(n, 32, "uniform", seed=3))
+    need = isort.workspace_size(n, 32, 0, 8)
+    s = torch.cuda.Stream()
+    small = torch.empty(need // 2, dtype=torch.uint8, device="cuda")
+    isort.set_workspace(small, stream=s)
+    with pytest.raises(isort.IsortError) as e:
+        isort.sort_keys(k, 8, stream=s)
+    assert e.value.status == _lib.ENOMEM
+    big = torch.empty(need, dtype=torch.uint8, device="cuda")
+    isort.set_workspace(big, stream=s)
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        isort.sort_keys(k, 8)
+    assert isort.stream_status(s) == _lib.OK
+    assert np.array_equal(to_host(k), np.sort(inputs.keys(n, 32, "uniform", seed=3)))
+    isort.set_workspace(None, stream=s)
+
+
+def test_concurrent_streams_give_the_same_results():
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    data = [inputs.keys(200_000 + 1000 * i, 32, "and4", seed=20 + i) for i in range(4)]
+    ts = [to_dev(d) for d in data]
+    torch.cuda.synchronize()
+    for s, t in zip(streams, ts):
+        with torch.cuda.stream(s):
+            isort.sort_keys(t, 8)
+    for s, t, d in zip(streams, ts, data):
+        assert isort.stream_status(s) == _lib.OK
+        assert np.array_equal(to_host(t), oracle.radix_sort(d, radix_bits=8))
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A tile that never publishes makes its successors' bounded waits give up:
+    the error is latched and reported, no GPU hang, and the next sort is fine."""
+    n = 4 * 4096 * 4
+    k = to_dev(inputs.keys(n, 32, "uniform", seed=6))
+    isort.debug_set(_lib.DEBUG_SPIN_LIMIT, 2000)
+    isort.debug_set(_lib.DEBUG_STALL_TILE, 1)
+    try:
+        isort.sort_keys(k, 8)
+        assert isort.stream_status() == _lib.ETIMEOUT
+        assert isort.stream_status() == _lib.OK  # cleared once reported
+    finally:
+        isort.debug_set(_lib.DEBUG_STALL_TILE, -1)
+        isort.debug_set(_lib.DEBUG_SPIN_LIMIT, 0)
+    d = inputs.keys(n, 32, "uniform", seed=7)
+    assert np.array_equal(gpu_sort(d), np.sort(d))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dist", inputs.DISTS)
+def test_full_size_2p28_u32_radix256(dist):
+    """The benchmark workload: n = 2^28 u32 keys, radix 256, launched exactly as
+    bench.py launches it (default variant, device-generated keys); compared with
+    the oracle element by element."""
+    n = 1 << 28
+    t = inputs.device_keys(n, 32, dist, seed=1)
+    host_in = to_host(t)
+    isort.sort_keys(t, 8)
+    assert isort.stream_status() == _lib.OK
+    got = to_host(t)
+    del t
+    torch.cuda.empty_cache()
+    assert np.array_equal(got, oracle.radix_sort(host_in, radix_bits=8))
+
+
+@pytest.mark.slow
+def test_full_size_pairs_2p27_and_u64_2p26():
+    n = 1 << 27
+    k = inputs.device_keys(n, 32, "uniform", seed=1)
+    v = inputs.device_iota(n, 32)
+    kin = to_host(k)
+    isort.sort_pairs(k, v, 8)
+    assert isort.stream_status() == _lib.OK
+    ok, ov = oracle.radix_sort(kin, inputs.iota(n), radix_bits=8)
+    assert np.array_equal(to_host(k), ok)
+    assert np.array_equal(to_host(v), ov)
+    del k, v
+    n = 1 << 26
+    k = inputs.device_keys(n, 64, "uniform", seed=1)
+    kin = to_host(k)
+    isort.sort_keys(k, 8)
+    assert isort.stream_status() == _lib.OK
+    assert np.array_equal(to_host(k), oracle.radix_sort(kin, radix_bits=8))
