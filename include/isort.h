@@ -105,7 +105,18 @@ isort_status isort_tune_describe(int key_bits, int val_bits, int radix_bits, int
  * t): in pass 0 of the next radix-256 sort, tile t never publishes its counts
  * so its successors' waits run out (-1 = off; the sort's output is then garbage
  * and isort_stream_status reports ISORT_ETIMEOUT). */
-enum { ISORT_DEBUG_SPIN_LIMIT = 1, ISORT_DEBUG_STALL_TILE = 2, ISORT_DEBUG_KERNEL_TIMING = 3 };
+enum {
+  ISORT_DEBUG_SPIN_LIMIT = 1,
+  ISORT_DEBUG_STALL_TILE = 2,
+  ISORT_DEBUG_KERNEL_TIMING = 3,
+  /* value = device pointer to tiles * 8 uint64 words (0 = off): radix-256 sorts
+   * then record, for every tile of pass ISORT_DEBUG_TRACE_PASS, %globaltimer at
+   * tile start, after ranking, before and after the look-back, after the
+   * shared-memory reorder and at the end, then the look-back window count of
+   * digit 0 and the SM id. A measurement hook; it does not change results. */
+  ISORT_DEBUG_TRACE_PTR = 4,
+  ISORT_DEBUG_TRACE_PASS = 5
+};
 isort_status isort_debug_set(int what, int64_t value);
 
 /* Measurement hook. With isort_debug_set(ISORT_DEBUG_KERNEL_TIMING, 1) every sort

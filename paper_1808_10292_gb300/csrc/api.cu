@@ -34,6 +34,8 @@ int64_t g_stall_tile = -1;
 std::map<int, int> g_sms;  // device -> SM count
 KernelTimer g_timer;
 bool g_timing = false;
+unsigned long long* g_trace = nullptr;
+int g_trace_pass = 0;
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -160,6 +162,8 @@ isort_status run_lsd(void* keys, void* vals, int64_t n, int key_bits, int val_bi
   a.stall_tile = g_stall_tile;
   g_stall_tile = -1;  // the stall hook applies to one sort only
   a.num_sms = num_sms();
+  a.trace = g_trace;
+  a.trace_pass = g_trace_pass;
   a.timer = nullptr;
   if (g_timing) {
     if (!g_timer.ready) {
@@ -347,6 +351,12 @@ isort_status isort_debug_set(int what, int64_t value) {
       return ISORT_OK;
     case ISORT_DEBUG_KERNEL_TIMING:
       g_timing = value != 0;
+      return ISORT_OK;
+    case ISORT_DEBUG_TRACE_PTR:
+      g_trace = reinterpret_cast<unsigned long long*>(value);
+      return ISORT_OK;
+    case ISORT_DEBUG_TRACE_PASS:
+      g_trace_pass = (int)value;
       return ISORT_OK;
   }
   return ISORT_EINVAL;

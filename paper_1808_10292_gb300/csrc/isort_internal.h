@@ -39,6 +39,8 @@ struct LsdArgs {
   int64_t stall_tile;   // test hook (-1 = off)
   int num_sms;
   KernelTimer* timer;   // null unless kernel timing is on
+  unsigned long long* trace;  // measurement hook: per-tile phase timestamps of one pass
+  int trace_pass;
 };
 
 typedef cudaError_t (*LsdLaunchFn)(const LsdArgs&, cudaStream_t);

@@ -4,17 +4,19 @@
 namespace isort {
 
 static const LsdEntry kK32None8[] = {
-    lsd_entry<uint32_t, NoVal, 8, 256, 16>(),
-    lsd_entry<uint32_t, NoVal, 8, 256, 12>(),
-    lsd_entry<uint32_t, NoVal, 8, 384, 16>(),
-    lsd_entry<uint32_t, NoVal, 8, 512, 16>(),
+    lsd_entry<uint32_t, NoVal, 8, 256, 16, 4>(),
+    lsd_entry<uint32_t, NoVal, 8, 256, 12, 4>(),
+    lsd_entry<uint32_t, NoVal, 8, 384, 16, 2>(),
+    lsd_entry<uint32_t, NoVal, 8, 512, 16, 1>(),
+    lsd_entry<uint32_t, NoVal, 8, 256, 24, 2>(),
+    lsd_entry<uint32_t, NoVal, 8, 512, 12, 2>(),
 };
 static const LsdEntry kK32V32_8[] = {
-    lsd_entry<uint32_t, uint32_t, 8, 256, 12>(),
-    lsd_entry<uint32_t, uint32_t, 8, 256, 16>(),
+    lsd_entry<uint32_t, uint32_t, 8, 256, 12, 3>(),
+    lsd_entry<uint32_t, uint32_t, 8, 256, 16, 2>(),
 };
 static const LsdEntry kK32V64_8[] = {
-    lsd_entry<uint32_t, uint64_t, 8, 256, 12>(),
+    lsd_entry<uint32_t, uint64_t, 8, 256, 12, 2>(),
 };
 
 int lsd_variants_k32(int val_bits, int radix_bits, const LsdEntry** out) {

@@ -4,14 +4,14 @@
 namespace isort {
 
 static const LsdEntry kK64None8[] = {
-    lsd_entry<uint64_t, NoVal, 8, 256, 12>(),
-    lsd_entry<uint64_t, NoVal, 8, 256, 16>(),
+    lsd_entry<uint64_t, NoVal, 8, 256, 12, 3>(),
+    lsd_entry<uint64_t, NoVal, 8, 256, 16, 2>(),
 };
 static const LsdEntry kK64V32_8[] = {
-    lsd_entry<uint64_t, uint32_t, 8, 256, 12>(),
+    lsd_entry<uint64_t, uint32_t, 8, 256, 12, 2>(),
 };
 static const LsdEntry kK64V64_8[] = {
-    lsd_entry<uint64_t, uint64_t, 8, 256, 12>(),
+    lsd_entry<uint64_t, uint64_t, 8, 256, 12, 2>(),
 };
 
 int lsd_variants_k64(int val_bits, int radix_bits, const LsdEntry** out) {
