@@ -70,6 +70,27 @@ isort_status isort_segmented(void *keys, void *vals, const int64_t *offsets, int
                              int64_t total_keys, int key_bits, int val_bits, int radix_bits,
                              void *stream);
 
+/* Sort without allocating: isort_keys for 32-bit keys, radix 256, whose scratch
+ * memory is a fixed array inside the library (about 5 MiB of device memory per
+ * GPU that loads the library, held until the process exits) instead of a
+ * workspace. The paper has no counterpart; this exists for callers that must
+ * not allocate device memory while running -- a framework that owns all device
+ * memory through its own pool, a latency-critical loop where cudaMalloc could
+ * synchronise the device, code that must not hit out-of-memory after start-up.
+ *  - keys: DEVICE array of n uint32 keys, sorted ascending in place.
+ *  - n > ISORT_NOALLOC_MAX_KEYS returns ISORT_ENOMEM (the array is too small);
+ *    n = 0 or 1 is a no-op.
+ *  - err_out: optional DEVICE word; device-side error bits are OR-ed into it
+ *    (the caller zeroes it); NULL = not reported.
+ *  - The first call on a device looks up the array's device address (with that
+ *    device current); make that first call before any stream capture.
+ *  - Every call shares the one array, which keeps the previous call's contents
+ *    (the call clears what must start at zero). Calls that overlap on the GPU
+ *    -- on different streams, or from different threads -- race on it and give
+ *    wrong results: serialise them. */
+#define ISORT_NOALLOC_MAX_KEYS (1 << 20)
+isort_status isort_keys_noalloc(void *keys, int64_t n, uint32_t *err_out, void *stream);
+
 /* Bytes of workspace one call with these arguments needs (bytes may be NULL-checked). */
 isort_status isort_workspace_size(int64_t n, int key_bits, int val_bits, int radix_bits,
                                   size_t *bytes);

@@ -50,6 +50,19 @@ def sort_keys(keys, radix_bits: int = 0, stream=None):
     return keys
 
 
+def sort_keys_noalloc(keys, err_word=None, stream=None):
+    """Sort a CUDA uint32 tensor in place with the library's fixed scratch array
+    (isort_keys_noalloc): no device memory is allocated. At most
+    NOALLOC_MAX_KEYS keys; calls must not overlap on the GPU."""
+    _dev(keys, "keys")
+    if _bits(keys) != 32:
+        raise TypeError("isort_keys_noalloc sorts 32-bit keys")
+    eptr = None if err_word is None else err_word.data_ptr()
+    check(load().isort_keys_noalloc(keys.data_ptr(), keys.numel(), eptr, _stream(stream)),
+          "isort_keys_noalloc")
+    return keys
+
+
 def sort_pairs(keys, vals, radix_bits: int = 0, stream=None):
     """Stable key-value sort in place (vals follow their keys); returns (keys, vals)."""
     _dev(keys, "keys")

@@ -18,6 +18,7 @@ STATUS = {0: "ISORT_OK", 1: "ISORT_EINVAL", 2: "ISORT_ENOMEM", 3: "ISORT_ECUDA",
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
 DEBUG_SPIN_LIMIT, DEBUG_STALL_TILE, DEBUG_KERNEL_TIMING = 1, 2, 3
 DEBUG_TRACE_PTR, DEBUG_TRACE_PASS = 4, 5
+NOALLOC_MAX_KEYS = 1 << 20
 
 _lib = None
 
@@ -42,6 +43,7 @@ def _sig(lib):
         "isort_tune_num_variants": [i32, i32, i32],
         "isort_tune_describe": [i32, i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)],
         "isort_debug_set": [i32, i64],
+        "isort_keys_noalloc": [vp, i64, vp, vp],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
