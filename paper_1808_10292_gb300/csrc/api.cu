@@ -52,6 +52,7 @@ int num_sms() {
 }
 
 int variants(int key_bits, int val_bits, int radix_bits, const LsdEntry** out) {
+  if (radix_bits == 16) return r16_variants(key_bits, val_bits, out);
   if (key_bits == 32) return lsd_variants_k32(val_bits, radix_bits, out);
   if (key_bits == 64) return lsd_variants_k64(val_bits, radix_bits, out);
   return 0;
@@ -83,7 +84,9 @@ Layout layout_for(const LsdEntry& e, int64_t n) {
   L.skip = off;      off = align256(off + sizeof(uint32_t) * e.passes);
   L.counters = off;  off = align256(off + sizeof(uint32_t) * e.passes);
   L.status0 = off;   off = align256(off + sizeof(uint32_t) * e.status_words_per_tile * tiles);
-  L.status1 = off;   off = align256(off + sizeof(uint32_t) * e.status_words_per_tile * tiles);
+  L.status1 = off;
+  if (e.status_buffers > 1)
+    off = align256(off + sizeof(uint32_t) * e.status_words_per_tile * tiles);
   L.alt_k = off;     off = align256(off + (size_t)n * (e.key_bits / 8));
   L.alt_v = off;     off = align256(off + (size_t)n * (e.val_bits / 8));
   L.total = off;

@@ -53,11 +53,14 @@ struct LsdEntry {
   int radix;            // 2^radix_bits
   int passes;
   size_t status_words_per_tile;  // look-back words per tile per buffer
+  int status_buffers;            // look-back buffers (2: alternate by pass)
   LsdLaunchFn launch;
 };
 
 // Variant tables, one per key width (sort_k32.cu, sort_k64.cu).
 int lsd_variants_k32(int val_bits, int radix_bits, const LsdEntry** out);
 int lsd_variants_k64(int val_bits, int radix_bits, const LsdEntry** out);
+// Radix-65536 path (radix16.cu): one entry per (key_bits, val_bits).
+int r16_variants(int key_bits, int val_bits, const LsdEntry** out);
 
 }  // namespace isort

@@ -573,6 +573,7 @@ constexpr LsdEntry lsd_entry() {
                   S::R,
                   DigitLayout<K, BITS>::PASSES,
                   (size_t)S::R,
+                  2,
                   &lsd_launch<K, V, BITS, THREADS, KPT, MINB>};
 }
 

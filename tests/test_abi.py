@@ -41,6 +41,7 @@ def test_argument_errors_need_no_gpu(lib):
     dummy = ctypes.c_void_p(256)
     assert lib.isort_keys(dummy, 10, 16, 8, None) == _lib.EINVAL        # bad key width
     assert lib.isort_keys(dummy, 10, 32, 7, None) == _lib.EUNSUPPORTED  # radix 2^7
+    assert lib.isort_keys(dummy, 10, 32, 11, None) == _lib.EUNSUPPORTED  # radix 2^11
     assert lib.isort_keys(dummy, 10, 32, 40, None) == _lib.EINVAL       # nonsense radix
     assert lib.isort_keys(dummy, -1, 32, 8, None) == _lib.EINVAL
     assert lib.isort_keys(dummy, (1 << 30) + 1, 32, 8, None) == _lib.EUNSUPPORTED
@@ -60,6 +61,8 @@ def test_workspace_size_and_tuning_tables(lib):
     assert size >= n * 4  # at least the alternate key buffer
     assert isort.workspace_size(n, 32, 32, 8) >= size + n * 4
     assert isort.workspace_size(n, 64, 0, 8) >= n * 8
+    assert isort.workspace_size(n, 32, 0, 16) >= n * 4 + 2 * 65536 * 4  # radix 65536: matrix
+    assert len(isort.tune_variants(32, 0, 16)) == 1
     v = isort.tune_variants(32, 0, 8)
     assert len(v) >= 2 and all(t % 32 == 0 and k > 0 for t, k in v)
     with pytest.raises(isort.IsortError):

@@ -24,7 +24,7 @@ def to_host(t) -> np.ndarray:
     return t.cpu().numpy()
 
 
-def gpu_sort(keys_np, vals_np=None, radix_bits=8):
+def gpu_sort(keys_np, vals_np=None, radix_bits=8):  # noqa: D401
     k = to_dev(keys_np)
     if vals_np is None:
         isort.sort_keys(k, radix_bits)
@@ -158,6 +158,55 @@ def test_bounded_wait_reports_timeout_and_context_survives():
         isort.debug_set(_lib.DEBUG_SPIN_LIMIT, 0)
     d = inputs.keys(n, 32, "uniform", seed=7)
     assert np.array_equal(gpu_sort(d), np.sort(d))
+
+
+R16_BLOCK = 1 << 19  # keys per count-matrix row of the radix-65536 path
+
+
+@pytest.mark.parametrize("key_bits", [32, 64])
+@pytest.mark.parametrize("dist", inputs.DISTS)
+def test_radix65536_distributions(key_bits, dist):
+    n = 1_234_567  # three count blocks (2^19 keys), many 4096-key sub-tiles, a ragged tail
+    k = inputs.keys(n, key_bits, dist, seed=12)
+    assert np.array_equal(gpu_sort(k, radix_bits=16), oracle.radix_sort(k, radix_bits=16))
+
+
+@pytest.mark.parametrize("key_bits,val_bits", [(32, 32), (32, 64), (64, 32), (64, 64)])
+@pytest.mark.parametrize("dist", ["uniform", "and4", "u16"])
+def test_radix65536_pairs_stable(key_bits, val_bits, dist):
+    n = 700_001
+    k = inputs.keys(n, key_bits, dist, seed=13)
+    v = inputs.iota(n, val_bits)
+    gk, gv = gpu_sort(k, v, radix_bits=16)
+    ok, ov = oracle.radix_sort(k, v, radix_bits=16)
+    assert np.array_equal(gk, ok)
+    assert np.array_equal(gv, ov)
+
+
+def test_radix65536_edge_sizes():
+    for n in sorted({0, 1, 2, 3, 4095, 4096, 4097, 9000, R16_BLOCK - 1, R16_BLOCK, R16_BLOCK + 1,
+                     2 * R16_BLOCK + 4097}):
+        k = inputs.keys(n, 32, "and4", seed=n + 3)
+        v = inputs.iota(n)
+        gk, gv = gpu_sort(k, v, radix_bits=16)
+        ok, ov = oracle.radix_sort(k, v, radix_bits=16)
+        assert np.array_equal(gk, ok), n
+        assert np.array_equal(gv, ov), n
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dist", inputs.DISTS)
+def test_full_size_2p28_u32_radix65536(dist):
+    """n = 2^28 u32 keys at radix 65536 (two passes), element by element."""
+    n = 1 << 28
+    t = inputs.device_keys(n, 32, dist, seed=1)
+    host_in = to_host(t)
+    isort.sort_keys(t, 16)
+    assert isort.stream_status() == _lib.OK
+    got = to_host(t)
+    del t
+    torch.cuda.empty_cache()
+    assert np.array_equal(got, oracle.radix_sort(host_in, radix_bits=16))
 
 
 @pytest.mark.slow
