@@ -38,9 +38,13 @@ WORKLOADS = {
     "pairs_2p27": (1 << 27, 32, 32, 8, "stable pairs, 2^27 uint32 keys + uint32 index payloads"),
     "u64_2p26": (1 << 26, 64, 0, 8, "plain sort, 2^26 uint64 keys, radix 256 (8 passes)"),
     "u32_128M_paper": (131_072_000, 32, 0, 8, "the paper's 128M (1M = 1,024,000) uint32 keys"),
+    # n is the total over 20,000 ranges with log-uniform lengths in [1, 2^20]
+    "segmented_20000": (0, 32, 0, 8, "batched segmented sort, 20,000 ranges, lengths "
+                                     "log-uniform in [1, 2^20], uniform uint32 keys"),
 }
 ALIASES = {"r16": "u32_2p28_r65536", "pairs": "pairs_2p27", "u64": "u64_2p26",
-           "paper128m": "u32_128M_paper", "default": "u32_2p28_r256"}
+           "paper128m": "u32_128M_paper", "default": "u32_2p28_r256",
+           "segmented": "segmented_20000"}
 
 
 def parse():
@@ -254,6 +258,48 @@ def run_reference(a):
     return 0
 
 
+def run_reference_segmented(a):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    import inputs
+    import oracle
+    L = inputs.segment_lengths(20_000, seed=a.seed)
+    off = inputs.segment_offsets(L)
+    # each step: the oracle sorts the next 200 ranges of the workload
+    host = inputs.keys(int(off[min(len(L), 200 * (a.steps + a.warmup))]), 32, a.dist, a.seed)
+    times, keys_done = [], []
+    s = 0
+    for step in range(a.steps + a.warmup):
+        t0 = time.perf_counter()
+        k = 0
+        for _ in range(200):
+            if s >= len(L):
+                break
+            seg = host[off[s]:off[s + 1]]
+            oracle.radix_sort(seg)
+            k += len(seg)
+            s += 1
+        times.append(time.perf_counter() - t0)
+        keys_done.append(k)
+    t, kd = sum(times[a.warmup:]), sum(keys_done[a.warmup:])
+    value = kd / t
+    line = {"impl": "reference",
+            "metric": "batched-segment keys/s (20,000 ranges, log-uniform lengths in [1, 2^20])",
+            "value": value, "unit": "keys/s", "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1000 * t / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": a.workload, "num_segments": 20000, "dist": a.dist,
+                       "seed": a.seed},
+            "cpu_baseline": {"value": value, "unit": "keys/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{a.steps} steps of 200 consecutive ranges each, one "
+                                       f"oracle sort per range, 1 thread"},
+            "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # --------------------------------------------------------------------------- our arm
 def run_ours(a):
     import torch
@@ -448,8 +494,151 @@ def measure_e2e(a, n, kb, vb, rb, torch, isort, inputs, stream):
             "d2h_bytes_per_step": bi, "ms_per_step": ms, "steps": steps}
 
 
+def run_ours_segmented(a):
+    """Batched segmented sort vs one plain sort launch per range, same GPU."""
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    rep = Replicas(world, rank, local, "nccl")
+    import inputs
+    import paper_1808_10292_gb300 as isort
+    from paper_1808_10292_gb300 import _lib, tune
+
+    applied = tune.apply(32, 0)
+    nseg = 20_000
+    L = inputs.segment_lengths(nseg, seed=a.seed)
+    off = inputs.segment_offsets(L)
+    n = int(off[-1])
+    pristine = inputs.device_keys(n, 32, a.dist, a.seed)
+    keys = torch.empty_like(pristine)
+    d_off = torch.from_numpy(off).cuda()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda").view(torch.int32)
+    flush.zero_()
+    stream = torch.cuda.current_stream()
+
+    def restore():
+        keys.copy_(pristine)
+        flush.sum()
+
+    for _ in range(a.warmup):
+        restore()
+        isort.sort_segmented(keys, d_off)
+    torch.cuda.synchronize()
+    if isort.stream_status() != _lib.OK:
+        raise RuntimeError("device error during warm-up")
+
+    isort.debug_set(_lib.DEBUG_KERNEL_TIMING, 1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    kernel_ms = {}
+    launches = 0
+    clocks = ClockSampler(local)
+    rep.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(a.steps):
+        restore()
+        ev[i][0].record(stream)
+        isort.sort_segmented(keys, d_off)
+        ev[i][1].record(stream)
+        for name, ms in isort.kernel_times():
+            kernel_ms.setdefault(name, []).append(ms)
+            launches += 1
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    rep.barrier()
+    isort.debug_set(_lib.DEBUG_KERNEL_TIMING, 0)
+    if isort.stream_status() != _lib.OK:
+        raise RuntimeError("device error during the timed steps")
+    total_s = rep.max(sum(s.elapsed_time(e) for s, e in ev) / 1000.0)
+    value = n * a.steps * world / total_s
+
+    # baseline: one plain sort per range through the public call, same GPU
+    restore()
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for s in range(nseg):
+        if L[s] > 1:
+            isort.sort_keys(keys[off[s]:off[s + 1]], 8)
+    s1.record(stream)
+    s1.synchronize()
+    base_ms = s0.elapsed_time(s1)
+    if isort.stream_status() != _lib.OK:
+        raise RuntimeError("device error in the per-range baseline")
+    got = keys.cpu().numpy()
+    restore()
+    isort.sort_segmented(keys, d_off)
+    if not np.array_equal(got, keys.cpu().numpy()):
+        raise RuntimeError("batched and per-range results differ")
+
+    btn_max = (applied.get("segmented") or {}).get("btn_max", 4096)
+    n_radix = int(L[L > btn_max].sum())
+    dom = "k_seg_onesweep"
+    dom_ms = statistics.mean(kernel_ms[dom])
+    alg_bytes = 2 * n_radix * 4
+    peak, peak_kind = measured_peak_hbm()
+    achieved = alg_bytes / (dom_ms / 1000.0) / 1e9
+    cpu = None
+    if not a.no_cpu_baseline and rank == 0 and world == 1:
+        import oracle
+        host = pristine.cpu().numpy()
+        oracle.radix_sort(host[:1024])
+        done_keys, t_cpu, t_end = 0, 0.0, time.perf_counter() + a.cpu_seconds
+        s = 0
+        while time.perf_counter() < t_end and s < nseg:
+            seg = host[off[s]:off[s + 1]]
+            t0 = time.perf_counter()
+            oracle.radix_sort(seg)
+            t_cpu += time.perf_counter() - t0
+            done_keys += len(seg)
+            s += 1
+        cpu = {"value": done_keys / max(t_cpu, 1e-9), "unit": "keys/s", "cores": 1,
+               "kind": "oracle",
+               "sample": f"the first {s} of the 20,000 ranges ({done_keys} keys), one oracle "
+                         f"sort per range, 1 thread"}
+    line = {
+        "metric": "batched-segment keys/s (20,000 ranges, log-uniform lengths in [1, 2^20])",
+        "value": value,
+        "unit": "keys/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": 1000 * total_s / a.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": a.workload, "num_segments": nseg, "keys": n, "dist": a.dist,
+                   "seed": a.seed, "tuned": applied, "radix_keys": n_radix,
+                   "l2": "inputs (6 GB) larger than L2; restored and L2 flushed before each step"},
+        "per_range_baseline": {"value": n / (base_ms / 1000.0), "unit": "keys/s",
+                               "ms": base_ms, "calls": int((L > 1).sum()),
+                               "how": "one isort_keys call per range (radix 256), same GPU"},
+        "speedup_vs_per_range": (n / total_s * a.steps) / (n / (base_ms / 1000.0)),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": dom_ms},
+        "kernels": {k: {"launches": len(v), "mean_ms": statistics.mean(v), "total_ms": sum(v)}
+                    for k, v in kernel_ms.items()},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    rep.close()
+    return 0
+
+
 def main():
     a = parse()
+    if a.workload == "segmented_20000":
+        if a.impl == "reference":
+            return run_reference_segmented(a)
+        return run_ours_segmented(a)
     if a.impl == "reference":
         return run_reference(a)
     return run_ours(a)

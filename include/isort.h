@@ -61,11 +61,14 @@ isort_status isort_pairs(void *keys, void *vals, int64_t n, int key_bits, int va
 
 /* Segmented sort: each range [offsets[s], offsets[s+1]) is sorted independently
  * (vals may be NULL, then val_bits is ignored). offsets: DEVICE int64 array of
- * num_segments + 1 entries, offsets[0] = 0, non-decreasing; the total must be
- * <= 2^30 per segment. The paper's sample sorts split the input into p ranges and
- * sort each independently (Algorithms 1-3); here the ranges are given. Short
- * segments use the paper's BTN merge-split bitonic network ("Algorithm BTN",
- * Eq. Tb), long ones the radix passes. Offsets are read on the device only. */
+ * num_segments + 1 entries, offsets[0] = 0, non-decreasing, offsets[num_segments]
+ * = total_keys; each segment at most 2^30 keys. The paper's sample sorts split
+ * the input into p ranges and sort each independently (Algorithms 1-3); here
+ * the ranges are given. Short segments use the paper's BTN merge-split bitonic
+ * network ("Algorithm BTN", Eq. Tb), long ones the radix-256 passes, all
+ * segments of a class in the same launch. Offsets are read on the device only:
+ * a segment that breaks these rules is skipped (left as it is) and
+ * isort_stream_status reports ISORT_EINVAL. radix_bits: 0 or 8. */
 isort_status isort_segmented(void *keys, void *vals, const int64_t *offsets, int64_t num_segments,
                              int64_t total_keys, int key_bits, int val_bits, int radix_bits,
                              void *stream);
@@ -91,6 +94,15 @@ isort_status isort_segmented(void *keys, void *vals, const int64_t *offsets, int
 #define ISORT_NOALLOC_MAX_KEYS (1 << 20)
 isort_status isort_keys_noalloc(void *keys, int64_t n, uint32_t *err_out, void *stream);
 
+/* Segmented sort tuning: ranges of at most btn_max_keys keys use the BTN
+ * network, longer ones the radix passes (capped by the BTN capacity, 4096
+ * keys for 32-bit keys, 2048 for 64-bit; < 0 restores the default). */
+isort_status isort_tune_segmented(int key_bits, int val_bits, int64_t btn_max_keys);
+
+/* Bytes of workspace one isort_segmented call with these arguments needs. */
+isort_status isort_segmented_workspace_size(int64_t num_segments, int64_t total_keys, int key_bits,
+                                            int val_bits, size_t *bytes);
+
 /* Bytes of workspace one call with these arguments needs (bytes may be NULL-checked). */
 isort_status isort_workspace_size(int64_t n, int key_bits, int val_bits, int radix_bits,
                                   size_t *bytes);
@@ -103,7 +115,9 @@ isort_status isort_workspace_size(int64_t n, int key_bits, int val_bits, int rad
 isort_status isort_set_workspace(void *dev_ptr, size_t bytes, void *stream);
 
 /* Synchronise `stream`, then report and clear its device error word:
- * ISORT_ETIMEOUT if a bounded wait gave up, ISORT_ECUDA on a CUDA error. */
+ * ISORT_ETIMEOUT if a bounded wait gave up, ISORT_EINVAL if isort_segmented
+ * met offsets that are not a valid partition, ISORT_ECUDA on a CUDA error or
+ * a failed output bounds check. */
 isort_status isort_stream_status(void *stream);
 
 /* Release the library-allocated workspaces (synchronises their streams). */

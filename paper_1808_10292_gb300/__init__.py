@@ -136,6 +136,20 @@ def tune_variants(key_bits: int = 32, val_bits: int = 0, radix_bits: int = 8):
     return out
 
 
+def tune_segmented(key_bits: int = 32, val_bits: int = 0, btn_max_keys: int = -1):
+    """Ranges of at most btn_max_keys keys take the BTN network (-1: default)."""
+    check(load().isort_tune_segmented(key_bits, val_bits, btn_max_keys), "isort_tune_segmented")
+
+
+def segmented_workspace_size(num_segments: int, total_keys: int, key_bits: int = 32,
+                             val_bits: int = 0) -> int:
+    out = ctypes.c_size_t(0)
+    check(load().isort_segmented_workspace_size(num_segments, total_keys, key_bits, val_bits,
+                                                ctypes.byref(out)),
+          "isort_segmented_workspace_size")
+    return out.value
+
+
 def tune_set(key_bits: int, val_bits: int, radix_bits: int, variant: int):
     check(load().isort_tune_set(key_bits, val_bits, radix_bits, variant), "isort_tune_set")
 

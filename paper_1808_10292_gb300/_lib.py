@@ -44,6 +44,8 @@ def _sig(lib):
         "isort_tune_describe": [i32, i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)],
         "isort_debug_set": [i32, i64],
         "isort_keys_noalloc": [vp, i64, vp, vp],
+        "isort_tune_segmented": [i32, i32, i64],
+        "isort_segmented_workspace_size": [i64, i64, i32, i32, ctypes.POINTER(sz)],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)

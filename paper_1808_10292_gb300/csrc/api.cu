@@ -122,6 +122,50 @@ isort_status acquire(cudaStream_t st, size_t need, void** out) {
 
 bool aligned(const void* p, int bytes) { return (reinterpret_cast<uintptr_t>(p) % bytes) == 0; }
 
+// ---- segmented sort workspace ----
+std::map<std::pair<int, int>, int64_t> g_seg_btn_max;  // (key_bits, val_bits) -> threshold
+
+// Longest range that takes the BTN path: the tuned threshold, capped by the
+// capacity of the 256-thread BTN class (256 threads x cta_m keys).
+int64_t seg_btn_max(const SegConfig& c) {
+  const int64_t cap = 256LL * c.cta_m;
+  auto it = g_seg_btn_max.find({c.key_bits, c.val_bits});
+  int64_t v = it == g_seg_btn_max.end() ? cap : it->second;
+  if (v > cap) v = cap;
+  if (v < 64LL * c.mid_m) v = 64LL * c.mid_m;
+  return v;
+}
+
+struct SegLayout {
+  size_t err, cnt, lists, slot_first, tile_slot, seg_hist, seg_base, status0, status1, alt_k,
+      alt_v, total;
+  int64_t max_tiles;
+};
+
+SegLayout seg_layout(const SegConfig& c, int64_t nseg, int64_t total, int64_t btn_max) {
+  SegLayout L;
+  // radix ranges are longer than btn_max, so there are at most total/(btn_max+1)
+  int64_t slots = total / (btn_max + 1);
+  if (slots > nseg) slots = nseg;
+  if (slots < 1) slots = 1;
+  L.max_tiles = total / c.tile + slots + 1;
+  const size_t per_slot = sizeof(uint32_t) * (size_t)c.passes * c.radix;
+  size_t off = 0;
+  L.err = off;         off = align256(off + 4);
+  L.cnt = off;         off = align256(off + sizeof(uint32_t) * kCntWords);
+  L.lists = off;       off = align256(off + sizeof(int32_t) * 4 * (size_t)nseg);
+  L.slot_first = off;  off = align256(off + sizeof(uint32_t) * (size_t)nseg);
+  L.tile_slot = off;   off = align256(off + sizeof(int32_t) * (size_t)L.max_tiles);
+  L.seg_hist = off;    off = align256(off + per_slot * (size_t)nseg);
+  L.seg_base = off;    off = align256(off + per_slot * (size_t)nseg);
+  L.status0 = off;     off = align256(off + sizeof(uint32_t) * c.radix * (size_t)L.max_tiles);
+  L.status1 = off;     off = align256(off + sizeof(uint32_t) * c.radix * (size_t)L.max_tiles);
+  L.alt_k = off;       off = align256(off + (size_t)total * (c.key_bits / 8));
+  L.alt_v = off;       off = align256(off + (size_t)total * (c.val_bits / 8));
+  L.total = off;
+  return L;
+}
+
 isort_status check_widths(int key_bits, int val_bits, bool pairs) {
   if (key_bits != 32 && key_bits != 64) return ISORT_EINVAL;
   if (pairs && val_bits != 32 && val_bits != 64) return ISORT_EINVAL;
@@ -229,9 +273,79 @@ isort_status isort_pairs(void* keys, void* vals, int64_t n, int key_bits, int va
 isort_status isort_segmented(void* keys, void* vals, const int64_t* offsets, int64_t num_segments,
                              int64_t total_keys, int key_bits, int val_bits, int radix_bits,
                              void* stream) {
-  (void)keys; (void)vals; (void)offsets; (void)num_segments; (void)total_keys;
-  (void)key_bits; (void)val_bits; (void)radix_bits; (void)stream;
-  return ISORT_EUNSUPPORTED;
+  if (!vals) val_bits = 0;
+  isort_status s = check_widths(key_bits, val_bits, vals != nullptr);
+  if (s != ISORT_OK) return s;
+  if (radix_bits != 0 && radix_bits != 8)
+    return (radix_bits > 0 && radix_bits <= 24) ? ISORT_EUNSUPPORTED : ISORT_EINVAL;
+  if (num_segments < 0 || total_keys < 0 || num_segments > INT32_MAX) return ISORT_EINVAL;
+  if (num_segments == 0 || total_keys == 0) return ISORT_OK;
+  if (!offsets || !keys || !aligned(keys, key_bits / 8) ||
+      (vals && !aligned(vals, val_bits / 8)) || !aligned(offsets, 8))
+    return ISORT_EINVAL;
+  const SegConfig* c = key_bits == 32 ? seg_config_k32(val_bits) : seg_config_k64(val_bits);
+  if (!c) return ISORT_EUNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lock(g_mu);
+  SegLayout L = seg_layout(*c, num_segments, total_keys, seg_btn_max(*c));
+  void* ws = nullptr;
+  if ((s = acquire(st, L.total, &ws)) != ISORT_OK) return s;
+  char* b = static_cast<char*>(ws);
+  SegArgs a;
+  a.keys = keys;
+  a.vals = vals;
+  a.alt_keys = b + L.alt_k;
+  a.alt_vals = vals ? b + L.alt_v : nullptr;
+  a.offsets = offsets;
+  a.nseg = num_segments;
+  a.total = total_keys;
+  a.btn_max = seg_btn_max(*c);
+  a.max_tiles = L.max_tiles;
+  a.lists = reinterpret_cast<int32_t*>(b + L.lists);
+  a.cnt = reinterpret_cast<uint32_t*>(b + L.cnt);
+  a.slot_first = reinterpret_cast<uint32_t*>(b + L.slot_first);
+  a.tile_slot = reinterpret_cast<int32_t*>(b + L.tile_slot);
+  a.seg_hist = reinterpret_cast<uint32_t*>(b + L.seg_hist);
+  a.seg_base = reinterpret_cast<uint32_t*>(b + L.seg_base);
+  a.status[0] = reinterpret_cast<uint32_t*>(b + L.status0);
+  a.status[1] = reinterpret_cast<uint32_t*>(b + L.status1);
+  a.err = reinterpret_cast<uint32_t*>(b + L.err);
+  a.spin_limit = g_spin_limit;
+  a.num_sms = num_sms();
+  a.timer = nullptr;
+  if (g_timing) {
+    if (!g_timer.ready) {
+      for (int i = 0; i < 2 * KernelTimer::kMax; ++i) cudaEventCreate(&g_timer.ev[i]);
+      g_timer.ready = true;
+    }
+    g_timer.count = 0;
+    a.timer = &g_timer;
+  }
+  return c->launch(a, st) == cudaSuccess ? ISORT_OK : ISORT_ECUDA;
+}
+
+isort_status isort_tune_segmented(int key_bits, int val_bits, int64_t btn_max_keys) {
+  if (key_bits != 32 && key_bits != 64) return ISORT_EINVAL;
+  if (val_bits != 0 && val_bits != 32 && val_bits != 64) return ISORT_EINVAL;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (btn_max_keys < 0) {
+    g_seg_btn_max.erase({key_bits, val_bits});
+    return ISORT_OK;
+  }
+  g_seg_btn_max[{key_bits, val_bits}] = btn_max_keys;
+  return ISORT_OK;
+}
+
+isort_status isort_segmented_workspace_size(int64_t num_segments, int64_t total_keys, int key_bits,
+                                            int val_bits, size_t* bytes) {
+  if (!bytes || num_segments < 0 || total_keys < 0) return ISORT_EINVAL;
+  isort_status s = check_widths(key_bits, val_bits, val_bits != 0);
+  if (s != ISORT_OK) return s;
+  const SegConfig* c = key_bits == 32 ? seg_config_k32(val_bits) : seg_config_k64(val_bits);
+  if (!c) return ISORT_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_mu);
+  *bytes = seg_layout(*c, num_segments, total_keys, seg_btn_max(*c)).total;
+  return ISORT_OK;
 }
 
 isort_status isort_workspace_size(int64_t n, int key_bits, int val_bits, int radix_bits,
@@ -281,7 +395,9 @@ isort_status isort_stream_status(void* stream) {
     return ISORT_ECUDA;
   if (word) {
     if (cudaMemset(it->second.base, 0, 4) != cudaSuccess) return ISORT_ECUDA;
-    return ISORT_ETIMEOUT;
+    if (word & 1u) return ISORT_ETIMEOUT;  // a bounded wait gave up
+    if (word & 4u) return ISORT_EINVAL;    // segment offsets were not a valid partition
+    return ISORT_ECUDA;                    // an output index failed its bounds check
   }
   return ISORT_OK;
 }

@@ -63,4 +63,50 @@ int lsd_variants_k64(int val_bits, int radix_bits, const LsdEntry** out);
 // Radix-65536 path (radix16.cu): one entry per (key_bits, val_bits).
 int r16_variants(int key_bits, int val_bits, const LsdEntry** out);
 
+// ---- segmented sort (segmented.cuh) ----
+// Layout of the small counter block (uint32 words).
+enum {
+  kCntClassLen = 0,      // [4] ranges per class
+  kCntCursor = 4,        // [4] pop cursors of the persistent BTN kernels
+  kCntTiles = 8,         // tiles of all radix ranges
+  kCntPassTiles = 9,     // [passes] tile-id counters of the rounds
+  kCntWords = 32
+};
+
+struct SegArgs {
+  void* keys;
+  void* vals;
+  void* alt_keys;
+  void* alt_vals;
+  const int64_t* offsets;
+  int64_t nseg;
+  int64_t total;
+  int64_t btn_max;       // ranges longer than this take the radix path
+  int64_t max_tiles;     // upper bound on tiles of the radix ranges
+  int32_t* lists;        // [4][nseg]
+  uint32_t* cnt;         // [kCntWords]
+  uint32_t* slot_first;  // [nseg] first tile id of each radix range
+  int32_t* tile_slot;    // [max_tiles] radix range (slot) of each tile
+  uint32_t* seg_hist;    // [nseg][P][R]
+  uint32_t* seg_base;    // [nseg][P][R]
+  uint32_t* status[2];   // [max_tiles][R]
+  uint32_t* err;
+  uint32_t spin_limit;
+  int num_sms;
+  KernelTimer* timer;
+};
+
+// Host side: configuration of one (key, payload) family and its launcher.
+struct SegConfig {
+  int key_bits, val_bits;
+  int warp_m, mid_m, cta_m;  // keys per thread of the three BTN classes
+  int64_t tile;              // keys per radix tile
+  int passes, radix;
+  cudaError_t (*launch)(const SegArgs&, cudaStream_t);
+};
+
+// Segmented sort families (segmented_k32.cu, segmented_k64.cu).
+const SegConfig* seg_config_k32(int val_bits);
+const SegConfig* seg_config_k64(int val_bits);
+
 }  // namespace isort

@@ -258,12 +258,20 @@ __device__ __forceinline__ uint32_t lookback_exclusive(const uint32_t* status, u
 
 // One tile of one count-sort round. FULL: the tile holds TILE keys, so no
 // per-key bounds predicate is needed.
+//   tile       row of the look-back arrays (tile id in launch order)
+//   first      the tile opens its range (segment), so it has no predecessor
+//   tile_base  index of the tile's first key in kin / vin
+//   kout/vout  the range's output (positions are relative to the range start)
+//   base       [R] the range's exclusive digit bases for this pass
+//   bound      keys in the range (every output index is checked against it)
 template <typename K, typename V, int BITS, int THREADS, int KPT, bool FULL>
-__device__ __forceinline__ void onesweep_tile(const PassParams& p, uint32_t tile, int tile_n,
+__device__ __forceinline__ void onesweep_tile(const PassParams& p, uint32_t tile, bool first,
+                                              int64_t tile_base, int tile_n,
                                               const K* __restrict__ kin, K* __restrict__ kout,
-                                              const V* vin, V* vout, unsigned char* smem) {
+                                              const V* vin, V* vout, const uint32_t* base,
+                                              uint32_t bound, unsigned char* smem) {
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
-  constexpr int R = S::R, WARPS = S::WARPS, TILE = S::TILE, DPT = S::DPT;
+  constexpr int R = S::R, WARPS = S::WARPS, DPT = S::DPT;
   constexpr bool HV = S::HV;
   uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);  // [WARPS][R]
   uint32_t* s_adj = s_wcnt + WARPS * R;                   // [R]
@@ -272,7 +280,6 @@ __device__ __forceinline__ void onesweep_tile(const PassParams& p, uint32_t tile
   V* s_vals = reinterpret_cast<V*>(smem + S::HEADER_WORDS * 4);
   (void)s_vals;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t tile_base = (int64_t)tile * TILE;
   const bool publish = (int64_t)tile != p.stall_tile;
 
   // ---- load: warp w owns keys [w*32*KPT, (w+1)*32*KPT) of the tile, lane-striped
@@ -354,7 +361,7 @@ __device__ __forceinline__ void onesweep_tile(const PassParams& p, uint32_t tile
       dcnt[j] = sum;
       tsum += sum;
       if (publish)
-        st_relaxed(&p.status[(size_t)tile * R + d], (tile == 0 ? kFlagInc : kFlagAgg) | sum);
+        st_relaxed(&p.status[(size_t)tile * R + d], (first ? kFlagInc : kFlagAgg) | sum);
     }
   }
   uint32_t total;
@@ -370,12 +377,12 @@ __device__ __forceinline__ void onesweep_tile(const PassParams& p, uint32_t tile
       const uint32_t tstart = run;  // tile-local start of digit d
       run += dcnt[j];
       uint32_t excl = 0;
-      if (tile > 0) {
+      if (!first) {
         excl = lookback_exclusive<R, kLookbackWindow>(p.status, tile, d, p.spin_limit, p.err,
                                                       windows);
         if (publish) st_relaxed(&p.status[(size_t)tile * R + d], kFlagInc | (excl + dcnt[j]));
       }
-      s_adj[d] = p.base[d] + excl - tstart;
+      s_adj[d] = base[d] + excl - tstart;
 #pragma unroll
       for (int w = 0; w < WARPS; ++w) s_wcnt[w * R + d] += tstart;
     }
@@ -404,7 +411,7 @@ __device__ __forceinline__ void onesweep_tile(const PassParams& p, uint32_t tile
   // ---- write out: consecutive threads take consecutive tile slots, so each
   // digit's run lands on consecutive global addresses
   uint32_t gpos[HV ? KPT : 1];
-  const uint32_t n32 = (uint32_t)p.n;
+  const uint32_t n32 = bound;
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
     const int j = k * THREADS + tid;
@@ -468,10 +475,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
   K* kout = static_cast<K*>(src ? p.keys[0] : p.keys[1]);
   const V* vin = static_cast<const V*>(src ? p.vals[1] : p.vals[0]);
   V* vout = static_cast<V*>(src ? p.vals[0] : p.vals[1]);
+  const int64_t tile_base = (int64_t)tile * TILE;
   if (tile_n == TILE)
-    onesweep_tile<K, V, BITS, THREADS, KPT, true>(p, tile, tile_n, kin, kout, vin, vout, smem);
+    onesweep_tile<K, V, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n, kin, kout,
+                                                  vin, vout, p.base, (uint32_t)p.n, smem);
   else
-    onesweep_tile<K, V, BITS, THREADS, KPT, false>(p, tile, tile_n, kin, kout, vin, vout, smem);
+    onesweep_tile<K, V, BITS, THREADS, KPT, false>(p, tile, tile == 0, tile_base, tile_n, kin,
+                                                   kout, vin, vout, p.base, (uint32_t)p.n, smem);
 }
 
 // ---------------------------------------------------------------------------

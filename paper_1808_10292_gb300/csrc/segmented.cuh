@@ -1,0 +1,403 @@
+// Segmented sort: every range [offsets[s], offsets[s+1]) sorted independently.
+//
+// The paper's sample sorts (GSD, GER, GVR; Algorithms 1-3) end by splitting the
+// keys into p ranges and sorting each on its own; here the ranges are given by
+// the caller and thousands of them of very uneven length are sorted in one
+// batch. Short ranges go to the paper's BTN merge-split network (btn.cuh), long
+// ones to the radix-256 count-sort passes of onesweep.cuh, all ranges of a class
+// in the same launch:
+//
+//   k_seg_classify  one thread per range: checks the offsets, puts the range on
+//                   the list of its class (warp BTN, 64-thread BTN, 256-thread
+//                   BTN, radix) and gives each radix range a block of tile ids.
+//   k_seg_fill      tile id -> radix range.
+//   k_seg_btn<Q,M>  persistent: Q threads with M keys each sort one range at a
+//                   time, popped from the class list (Q = 32: one range per warp).
+//   k_seg_hist      digit histograms of every radix range, all passes, one read.
+//   k_seg_scan      per range and pass, exclusive digit bases.
+//   k_seg_onesweep  one count-sort round over the tiles of ALL radix ranges; the
+//                   look-back never crosses a range (the first tile of a range
+//                   publishes its counts as inclusive).
+// All passes run (4 for 32-bit keys, 8 for 64-bit): an even number, so the
+// result ends in the caller's arrays. Offsets are checked on the device; a bad
+// range is skipped and flagged in the error word.
+#pragma once
+#include "btn.cuh"
+#include "onesweep.cuh"
+
+namespace isort {
+
+constexpr uint32_t kErrOffsets = 4u;  // error bit: offsets not a valid partition
+
+// Classes of ranges.
+enum { kSegWarp = 0, kSegMid = 1, kSegCta = 2, kSegRadix = 3, kSegClasses = 4 };
+
+__device__ __forceinline__ void seg_range(const int64_t* off, int64_t s, int64_t total,
+                                          int64_t& start, int64_t& len) {
+  int64_t a = off[s], b = off[s + 1];
+  a = a < 0 ? 0 : (a > total ? total : a);
+  b = b < a ? a : (b > total ? total : b);
+  start = a;
+  len = b - a;
+}
+
+// ---------------------------------------------------------------------------
+template <int TILE>
+__global__ void k_seg_classify(const int64_t* __restrict__ off, int64_t nseg, int64_t total,
+                               int64_t warp_max, int64_t mid_max, int64_t btn_max,
+                               int32_t* __restrict__ lists, uint32_t* __restrict__ cnt,
+                               uint32_t* __restrict__ slot_first, uint32_t* err) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= nseg) return;
+  const int64_t a = off[s], b = off[s + 1];
+  bool bad = b < a || a < 0 || b > total || (s == 0 && a != 0) || (s == nseg - 1 && b != total);
+  int64_t start, len;
+  seg_range(off, s, total, start, len);
+  if (len > (int64_t(1) << 30)) bad = true;  // a range's counts must fit the 30-bit status
+  if (bad) {
+    atomicOr(err, kErrOffsets);
+    return;  // skipped: never read or written
+  }
+  if (len <= 1) return;
+  int c = len <= warp_max ? kSegWarp : len <= mid_max ? kSegMid : len <= btn_max ? kSegCta
+                                                                                  : kSegRadix;
+  const uint32_t idx = atomicAdd(&cnt[kCntClassLen + c], 1u);
+  lists[(size_t)c * nseg + idx] = (int32_t)s;
+  if (c == kSegRadix) slot_first[idx] = atomicAdd(&cnt[kCntTiles], (uint32_t)((len + TILE - 1) / TILE));
+}
+
+template <int TILE>
+__global__ void __launch_bounds__(256) k_seg_fill(const int64_t* __restrict__ off, int64_t nseg,
+                                                  int64_t total, const int32_t* __restrict__ lists,
+                                                  const uint32_t* __restrict__ cnt,
+                                                  const uint32_t* __restrict__ slot_first,
+                                                  int32_t* __restrict__ tile_slot) {
+  const uint32_t slot = blockIdx.x;
+  if (slot >= cnt[kCntClassLen + kSegRadix]) return;
+  int64_t start, len;
+  seg_range(off, lists[(size_t)kSegRadix * nseg + slot], total, start, len);
+  const int64_t tiles = (len + TILE - 1) / TILE;
+  const uint32_t first = slot_first[slot];
+  for (int64_t i = threadIdx.x; i < tiles; i += 256) tile_slot[first + i] = (int32_t)slot;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent BTN over one class list. Q = 32: every warp of the CTA sorts its
+// own ranges; Q > 32: the CTA (Q threads) sorts one range at a time.
+template <typename K, typename V, int Q, int M, int CTA>
+struct BtnShape {
+  static constexpr bool HV = HasVal<V>::value;
+  static constexpr int GROUPS = CTA / Q;  // independent sorters per CTA
+  static constexpr int CAP = Q * M;       // keys per range at most
+  using VS = typename std::conditional<HV, V, uint32_t>::type;
+  static constexpr size_t SMEM = (Q > 32 ? (sizeof(K) + sizeof(uint32_t)) * (size_t)CAP : 0) +
+                                 (HV ? sizeof(VS) * (size_t)CAP * GROUPS : 0) + 16;
+};
+
+template <typename K, typename V, int Q, int M, int CTA>
+__global__ void __launch_bounds__(CTA) k_seg_btn(K* __restrict__ keys, V* __restrict__ vals,
+                                                 const int64_t* __restrict__ off, int64_t nseg,
+                                                 int64_t total, const int32_t* __restrict__ list,
+                                                 uint32_t* __restrict__ cnt, int cls) {
+  using S = BtnShape<K, V, Q, M, CTA>;
+  constexpr bool HV = S::HV;
+  constexpr bool STABLE = HV;  // keys-only: equal keys are indistinguishable
+  extern __shared__ __align__(16) unsigned char smem[];
+  K* sk = reinterpret_cast<K*>(smem);
+  uint32_t* si = reinterpret_cast<uint32_t*>(smem + (Q > 32 ? sizeof(K) * S::CAP : 0));
+  typename S::VS* sv = reinterpret_cast<typename S::VS*>(
+      smem + (Q > 32 ? (sizeof(K) + sizeof(uint32_t)) * S::CAP : 0));
+  __shared__ uint32_t s_pop;
+  const int group = threadIdx.x / Q, t = threadIdx.x % Q;
+  typename S::VS* my_sv = sv + (size_t)group * S::CAP;
+  (void)my_sv;
+  const uint32_t count = cnt[kCntClassLen + cls];
+  while (true) {
+    uint32_t idx;
+    if constexpr (Q == 32) {
+      if (t == 0) idx = atomicAdd(&cnt[kCntCursor + cls], 1u);
+      idx = __shfl_sync(kFullMask, idx, 0);
+    } else {
+      if (threadIdx.x == 0) s_pop = atomicAdd(&cnt[kCntCursor + cls], 1u);
+      __syncthreads();
+      idx = s_pop;
+      __syncthreads();
+    }
+    if (idx >= count) break;
+    int64_t start, len;
+    seg_range(off, list[idx], total, start, len);
+    BtnItem<K, STABLE> x[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const int pos = i * Q + t;  // striped load: coalesced
+      if (pos < len) {
+        x[i].k = keys[start + pos];
+        if constexpr (STABLE) x[i].i = (uint32_t)pos;
+        if constexpr (HV) my_sv[pos] = vals[start + pos];
+      } else {  // padding sorts after every real item
+        x[i].k = ~K(0);
+        if constexpr (STABLE) x[i].i = 0xffffffffu;
+      }
+    }
+    btn_local_sort<STABLE>(x);
+    btn_network<STABLE, K, M, Q>(x, t, sk, si);
+    if constexpr (HV) {
+      if constexpr (Q == 32)
+        __syncwarp();
+      else
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const int pos = t * M + i;  // thread t holds sorted ranks [t*M, t*M + M)
+      if (pos < len) {
+        keys[start + pos] = x[i].k;
+        if constexpr (HV) vals[start + pos] = my_sv[x[i].i];
+      }
+    }
+    if constexpr (Q == 32)
+      __syncwarp();
+    else
+      __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Digit histograms of the radix ranges: CTA c walks a contiguous run of tiles,
+// counting into shared memory and flushing into seg_hist when the range changes.
+template <typename K, int BITS, int TILE>
+__global__ void __launch_bounds__(1024) k_seg_hist(const K* __restrict__ keys,
+                                                   const int64_t* __restrict__ off, int64_t nseg,
+                                                   int64_t total, const int32_t* __restrict__ list,
+                                                   const uint32_t* __restrict__ cnt,
+                                                   const uint32_t* __restrict__ slot_first,
+                                                   const int32_t* __restrict__ tile_slot,
+                                                   uint32_t* __restrict__ seg_hist) {
+  using L = DigitLayout<K, BITS>;
+  constexpr int R = L::R, P = L::PASSES, SUBS = 4;
+  __shared__ uint32_t s_hist[SUBS][P * R];
+  for (int i = threadIdx.x; i < SUBS * P * R; i += 1024) (&s_hist[0][0])[i] = 0;
+  const int64_t T = cnt[kCntTiles];
+  const int64_t t0 = T * blockIdx.x / gridDim.x, t1 = T * (blockIdx.x + 1) / gridDim.x;
+  uint32_t* my = s_hist[(threadIdx.x >> 5) % SUBS];
+  int32_t cur = -1;
+  __syncthreads();
+  auto flush = [&](int32_t slot) {
+    __syncthreads();
+    for (int j = threadIdx.x; j < P * R; j += 1024) {
+      uint32_t s = 0;
+#pragma unroll
+      for (int b = 0; b < SUBS; ++b) {
+        s += s_hist[b][j];
+        s_hist[b][j] = 0;
+      }
+      if (s) atomicAdd(&seg_hist[(size_t)slot * P * R + j], s);
+    }
+    __syncthreads();
+  };
+  for (int64_t t = t0; t < t1; ++t) {
+    const int32_t slot = tile_slot[t];
+    if (slot != cur) {
+      if (cur >= 0) flush(cur);
+      cur = slot;
+    }
+    int64_t start, len;
+    seg_range(off, list[(size_t)kSegRadix * nseg + slot], total, start, len);
+    const int64_t lo = start + (t - slot_first[slot]) * TILE;
+    const int64_t hi = min(start + len, lo + TILE);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += 1024) {
+      const K k = keys[i];
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+        atomicAdd(&my[p * R + digit_of(k, p * BITS, (1u << L::width(p)) - 1)], 1u);
+    }
+  }
+  if (cur >= 0) flush(cur);
+}
+
+// Per radix range: exclusive digit bases (relative to the range) of every pass.
+template <int BITS, int PASSES>
+__global__ void __launch_bounds__(1 << BITS) k_seg_scan(const uint32_t* __restrict__ cnt,
+                                                       const uint32_t* __restrict__ seg_hist,
+                                                       uint32_t* __restrict__ seg_base) {
+  constexpr int R = 1 << BITS;
+  __shared__ uint32_t s_warp[R / 32];
+  const uint32_t slot = blockIdx.x;
+  if (slot >= cnt[kCntClassLen + kSegRadix]) return;
+  for (int p = 0; p < PASSES; ++p) {
+    const size_t row = ((size_t)slot * PASSES + p) * R;
+    uint32_t tot;
+    seg_base[row + threadIdx.x] =
+        block_exclusive_scan<R>(seg_hist[row + threadIdx.x], s_warp, tot);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+struct SegPassParams {
+  PassParams p;  // keys/vals buffers, pass, shift, mask, status, counter, err...
+  const int64_t* off;
+  int64_t nseg;
+  int64_t total;
+  const int32_t* list;
+  const uint32_t* cnt;
+  const uint32_t* slot_first;
+  const int32_t* tile_slot;
+  const uint32_t* seg_base;
+  int passes;
+};
+
+template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp) {
+  using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
+  constexpr int R = S::R, WARPS = S::WARPS, TILE = S::TILE;
+  const PassParams& p = sp.p;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* s_misc = s_wcnt + WARPS * R + R;
+  uint32_t* s_stage = reinterpret_cast<uint32_t*>(smem + S::HEADER_WORDS * 4);
+  const int tid = threadIdx.x;
+  if (p.status_next)
+    for (int d = tid; d < R; d += THREADS) p.status_next[(size_t)blockIdx.x * R + d] = 0;
+  if (tid == 0) s_misc[0] = atomicAdd(p.counter, 1u);
+  for (int i = tid; i < WARPS * R; i += THREADS) s_wcnt[i] = 0;
+  for (int i = tid; i < WARPS * S::MASK_BUFS * R; i += THREADS) s_stage[i] = 0;
+  __syncthreads();
+  const uint32_t tile = s_misc[0];
+  if (tile >= sp.cnt[kCntTiles]) return;  // more CTAs than tiles: nothing left
+  const int32_t slot = sp.tile_slot[tile];
+  int64_t start, len;
+  seg_range(sp.off, sp.list[(size_t)kSegRadix * sp.nseg + slot], sp.total, start, len);
+  const int64_t lt = (int64_t)tile - sp.slot_first[slot];  // tile index within the range
+  const int64_t tile_base = start + lt * TILE;
+  const int tile_n = (int)min((int64_t)TILE, len - lt * TILE);
+  const int src = p.pass & 1;  // every round runs
+  const K* kin = static_cast<const K*>(src ? p.keys[1] : p.keys[0]);
+  K* kout = static_cast<K*>(src ? p.keys[0] : p.keys[1]) + start;
+  const V* vin = static_cast<const V*>(src ? p.vals[1] : p.vals[0]);
+  V* vout = static_cast<V*>(src ? p.vals[0] : p.vals[1]);
+  if constexpr (HasVal<V>::value) vout += start;
+  const uint32_t* base = sp.seg_base + ((size_t)slot * sp.passes + p.pass) * R;
+  if (tile_n == TILE)
+    onesweep_tile<K, V, BITS, THREADS, KPT, true>(p, tile, lt == 0, tile_base, tile_n, kin, kout,
+                                                  vin, vout, base, (uint32_t)len, smem);
+  else
+    onesweep_tile<K, V, BITS, THREADS, KPT, false>(p, tile, lt == 0, tile_base, tile_n, kin,
+                                                   kout, vin, vout, base, (uint32_t)len, smem);
+}
+
+// ---------------------------------------------------------------------------
+template <typename K, typename V, int WM, int MM, int CM, int THREADS, int KPT, int MINB>
+cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
+  using L = DigitLayout<K, 8>;
+  using OS = OnesweepShape<K, V, 8, THREADS, KPT>;
+  constexpr int R = L::R, P = L::PASSES, TILE = OS::TILE;
+  cudaError_t e;
+  const int64_t nslots = a.nseg;
+  if ((e = cudaMemsetAsync(a.cnt, 0, sizeof(uint32_t) * kCntWords, st))) return e;
+  if ((e = cudaMemsetAsync(a.seg_hist, 0, sizeof(uint32_t) * nslots * P * R, st))) return e;
+  if ((e = cudaMemsetAsync(a.status[0], 0, sizeof(uint32_t) * R * a.max_tiles, st))) return e;
+  if (a.nseg == 0) return cudaGetLastError();
+
+  timer_begin(a.timer, "k_seg_classify", st);
+  k_seg_classify<TILE><<<(unsigned)((a.nseg + 255) / 256), 256, 0, st>>>(
+      a.offsets, a.nseg, a.total, 32 * WM, 64 * MM, a.btn_max, a.lists, a.cnt, a.slot_first,
+      a.err);
+  timer_end(a.timer, st);
+  timer_begin(a.timer, "k_seg_fill", st);
+  k_seg_fill<TILE><<<(unsigned)a.nseg, 256, 0, st>>>(a.offsets, a.nseg, a.total, a.lists, a.cnt,
+                                                     a.slot_first, a.tile_slot);
+  timer_end(a.timer, st);
+
+  // short ranges: the three BTN classes, persistent grids
+  K* keys = static_cast<K*>(a.keys);
+  V* vals = static_cast<V*>(a.vals);
+  {
+    using B0 = BtnShape<K, V, 32, WM, 256>;
+    auto k0 = k_seg_btn<K, V, 32, WM, 256>;
+    using B1 = BtnShape<K, V, 64, MM, 64>;
+    auto k1 = k_seg_btn<K, V, 64, MM, 64>;
+    using B2 = BtnShape<K, V, 256, CM, 256>;
+    auto k2 = k_seg_btn<K, V, 256, CM, 256>;
+    if ((e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B2::SMEM)))
+      return e;
+    timer_begin(a.timer, "k_seg_btn_warp", st);
+    k0<<<a.num_sms * 4, 256, B0::SMEM, st>>>(keys, vals, a.offsets, a.nseg, a.total,
+                                             a.lists + (size_t)kSegWarp * a.nseg, a.cnt, kSegWarp);
+    timer_end(a.timer, st);
+    timer_begin(a.timer, "k_seg_btn_mid", st);
+    k1<<<a.num_sms * 8, 64, B1::SMEM, st>>>(keys, vals, a.offsets, a.nseg, a.total,
+                                            a.lists + (size_t)kSegMid * a.nseg, a.cnt, kSegMid);
+    timer_end(a.timer, st);
+    timer_begin(a.timer, "k_seg_btn_cta", st);
+    k2<<<a.num_sms * 2, 256, B2::SMEM, st>>>(keys, vals, a.offsets, a.nseg, a.total,
+                                             a.lists + (size_t)kSegCta * a.nseg, a.cnt, kSegCta);
+    timer_end(a.timer, st);
+  }
+
+  // long ranges: histograms, bases, then the rounds over all their tiles
+  timer_begin(a.timer, "k_seg_hist", st);
+  k_seg_hist<K, 8, TILE><<<a.num_sms, 1024, 0, st>>>(keys, a.offsets, a.nseg, a.total, a.lists,
+                                                     a.cnt, a.slot_first, a.tile_slot,
+                                                     a.seg_hist);
+  timer_end(a.timer, st);
+  timer_begin(a.timer, "k_seg_scan", st);
+  k_seg_scan<8, P><<<(unsigned)nslots, R, 0, st>>>(a.cnt, a.seg_hist, a.seg_base);
+  timer_end(a.timer, st);
+
+  auto kern = k_seg_onesweep<K, V, 8, THREADS, KPT, MINB>;
+  if (OS::SMEM > 48 * 1024) {
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)OS::SMEM)))
+      return e;
+  }
+  SegPassParams sp;
+  sp.off = a.offsets;
+  sp.nseg = a.nseg;
+  sp.total = a.total;
+  sp.list = a.lists;
+  sp.cnt = a.cnt;
+  sp.slot_first = a.slot_first;
+  sp.tile_slot = a.tile_slot;
+  sp.seg_base = a.seg_base;
+  sp.passes = P;
+  PassParams& pp = sp.p;
+  pp.keys[0] = a.keys;
+  pp.keys[1] = a.alt_keys;
+  pp.vals[0] = a.vals;
+  pp.vals[1] = a.alt_vals;
+  pp.n = a.total;
+  pp.base = nullptr;
+  pp.skip = nullptr;
+  pp.err = a.err;
+  pp.spin_limit = a.spin_limit;
+  pp.stall_tile = -1;
+  pp.trace = nullptr;
+  for (int q = 0; q < P; ++q) {
+    pp.pass = q;
+    pp.shift = q * 8;
+    pp.mask = (1u << L::width(q)) - 1;
+    pp.status = a.status[q & 1];
+    pp.status_next = (q + 1 < P) ? a.status[(q + 1) & 1] : nullptr;
+    pp.counter = a.cnt + kCntPassTiles + q;
+    timer_begin(a.timer, "k_seg_onesweep", st);
+    kern<<<(unsigned)a.max_tiles, THREADS, OS::SMEM, st>>>(sp);
+    timer_end(a.timer, st);
+  }
+  return cudaGetLastError();
+}
+
+template <typename K, typename V, int WM, int MM, int CM, int THREADS, int KPT, int MINB>
+constexpr SegConfig seg_config() {
+  return SegConfig{(int)(8 * sizeof(K)),
+                   HasVal<V>::value ? (int)(8 * sizeof(V)) : 0,
+                   WM,
+                   MM,
+                   CM,
+                   (int64_t)THREADS * KPT,
+                   DigitLayout<K, 8>::PASSES,
+                   256,
+                   &seg_launch<K, V, WM, MM, CM, THREADS, KPT, MINB>};
+}
+
+}  // namespace isort

@@ -1,0 +1,143 @@
+"""GPU parity of the segmented sort (BTN for short ranges, radix passes for long
+ones) against the serial oracle's per-range sort, element by element."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import inputs
+import oracle
+import paper_1808_10292_gb300 as isort
+from paper_1808_10292_gb300 import _lib
+
+pytestmark = pytest.mark.gpu
+
+# lengths around every class edge: warp BTN (<= 128), 64-thread BTN (<= 512),
+# 256-thread BTN (<= 4096 for 32-bit keys, 2048 for 64-bit), radix tiles (4096/3072)
+EDGE_LENGTHS = [0, 1, 2, 3, 31, 32, 33, 127, 128, 129, 511, 512, 513, 2047, 2048, 2049, 3071,
+                3072, 3073, 4095, 4096, 4097, 8191, 8193, 12289, 100_000, 0, 1, 5]
+
+
+def run_segmented(keys, offsets, vals=None, radix_bits=0):
+    k = torch.from_numpy(keys).cuda()
+    off = torch.from_numpy(offsets).cuda()
+    v = None if vals is None else torch.from_numpy(vals).cuda()
+    isort.sort_segmented(k, off, v, radix_bits)
+    status = isort.stream_status()
+    return status, k.cpu().numpy(), (None if v is None else v.cpu().numpy())
+
+
+@pytest.mark.parametrize("key_bits,val_bits", [(32, 0), (32, 32), (32, 64), (64, 0), (64, 32),
+                                               (64, 64)])
+@pytest.mark.parametrize("dist", ["uniform", "and4", "equal", "reverse"])
+def test_class_edges(key_bits, val_bits, dist):
+    L = np.array(EDGE_LENGTHS, dtype=np.int64)
+    off = inputs.segment_offsets(L)
+    n = int(off[-1])
+    k = inputs.keys(n, key_bits, dist, seed=41)
+    v = inputs.iota(n, val_bits) if val_bits else None
+    st, gk, gv = run_segmented(k, off, v)
+    assert st == _lib.OK
+    if v is None:
+        assert np.array_equal(gk, oracle.segmented_sort(k, off))
+    else:
+        ok, ov = oracle.segmented_sort(k, off, v)
+        assert np.array_equal(gk, ok)
+        assert np.array_equal(gv, ov)
+
+
+@pytest.mark.parametrize("key_bits", [32, 64])
+def test_log_uniform_lengths(key_bits):
+    """The batched workload's recipe at reduced scale: 3000 ranges, lengths
+    log-uniform in [1, 2^16]."""
+    L = inputs.segment_lengths(3000, seed=5, max_log2=16)
+    off = inputs.segment_offsets(L)
+    n = int(off[-1])
+    k = inputs.keys(n, key_bits, "uniform", seed=6)
+    v = inputs.iota(n, 32)
+    st, gk, gv = run_segmented(k, off, v)
+    assert st == _lib.OK
+    ok, ov = oracle.segmented_sort(k, off, v)
+    assert np.array_equal(gk, ok)
+    assert np.array_equal(gv, ov)
+
+
+def test_btn_threshold_tuning_keeps_results():
+    L = inputs.segment_lengths(800, seed=7, max_log2=13)
+    off = inputs.segment_offsets(L)
+    k = inputs.keys(int(off[-1]), 32, "and4", seed=8)
+    want = oracle.segmented_sort(k, off)
+    try:
+        for btn_max in (512, 1024, 4096):
+            isort.tune_segmented(32, 0, btn_max)
+            st, gk, _ = run_segmented(k, off)
+            assert st == _lib.OK
+            assert np.array_equal(gk, want), btn_max
+    finally:
+        isort.tune_segmented(32, 0, -1)
+
+
+def test_single_range_equals_plain_sort():
+    n = 300_001
+    k = inputs.keys(n, 32, "uniform", seed=9)
+    st, gk, _ = run_segmented(k, np.array([0, n], dtype=np.int64))
+    assert st == _lib.OK
+    assert np.array_equal(gk, oracle.radix_sort(k))
+
+
+def test_bad_offsets_are_flagged_not_faulted():
+    n = 10_000
+    k = inputs.keys(n, 32, "uniform", seed=10)
+    bad = np.array([0, 5000, 4000, n], dtype=np.int64)  # a decreasing pair
+    st, _, _ = run_segmented(k, bad)
+    assert st == _lib.EINVAL
+    bad_end = np.array([0, 5000, n - 7], dtype=np.int64)  # does not end at total
+    st, gk, _ = run_segmented(k, bad_end)
+    assert st == _lib.EINVAL
+    # valid offsets afterwards: the context is fine and the result exact
+    off = np.array([0, 5000, n], dtype=np.int64)
+    st, gk, _ = run_segmented(k, off)
+    assert st == _lib.OK
+    assert np.array_equal(gk, oracle.segmented_sort(k, off))
+
+
+def test_empty_and_degenerate():
+    st, gk, _ = run_segmented(np.zeros(0, np.uint32), np.array([0], dtype=np.int64))
+    assert st == _lib.OK and gk.size == 0
+    k = inputs.keys(64, 32, "uniform", seed=11)
+    off = np.arange(0, 65, dtype=np.int64)  # 64 ranges of one key: identity
+    st, gk, _ = run_segmented(k, off)
+    assert st == _lib.OK and np.array_equal(gk, k)
+
+
+@pytest.mark.slow
+def test_full_size_20000_ranges():
+    """The batched workload itself: 20,000 ranges, lengths log-uniform in [1, 2^20]
+    (about 1.5e9 uniform u32 keys), launched as the benchmark launches it.
+    Every range is checked to be sorted and to hold the same keys (sum and xor
+    per range); 300 seeded ranges are compared with the oracle element by element."""
+    L = inputs.segment_lengths(20_000, seed=1)
+    off = inputs.segment_offsets(L)
+    n = int(off[-1])
+    t = inputs.device_keys(n, 32, "uniform", seed=1)
+    before = t.cpu().numpy()
+    d_off = torch.from_numpy(off).cuda()
+    isort.sort_segmented(t, d_off)
+    assert isort.stream_status() == _lib.OK
+    after = t.cpu().numpy()
+    del t
+    torch.cuda.empty_cache()
+    starts = off[:-1][L > 0]
+    s64a, s64b = before.astype(np.uint64), after.astype(np.uint64)
+    assert np.array_equal(np.add.reduceat(s64a, starts), np.add.reduceat(s64b, starts))
+    assert np.array_equal(np.bitwise_xor.reduceat(before, starts),
+                          np.bitwise_xor.reduceat(after, starts))
+    inside = np.ones(n - 1, dtype=bool)
+    inside[off[1:-1] - 1] = False  # pairs that straddle a range boundary
+    assert (after[1:][inside] >= after[:-1][inside]).all()
+    rng = np.random.default_rng(3)
+    for s in rng.choice(len(L), 300, replace=False):
+        a, b = off[s], off[s + 1]
+        assert np.array_equal(after[a:b], oracle.radix_sort(before[a:b]))
