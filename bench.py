@@ -41,10 +41,13 @@ WORKLOADS = {
     # n is the total over 20,000 ranges with log-uniform lengths in [1, 2^20]
     "segmented_20000": (0, 32, 0, 8, "batched segmented sort, 20,000 ranges, lengths "
                                      "log-uniform in [1, 2^20], uniform uint32 keys"),
+    "serve_poisson": (0, 32, 32, 8, "serving loop: Poisson arrivals at 2,000 req/s, sizes "
+                                    "log-uniform in [2^10, 2^24] uint32 keys, half with "
+                                    "uint32 payloads, 40 GB admission budget"),
 }
 ALIASES = {"r16": "u32_2p28_r65536", "pairs": "pairs_2p27", "u64": "u64_2p26",
            "paper128m": "u32_128M_paper", "default": "u32_2p28_r256",
-           "segmented": "segmented_20000"}
+           "segmented": "segmented_20000", "serve": "serve_poisson"}
 
 
 def parse():
@@ -60,6 +63,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="duration of each arm of the serving workload")
     a = ap.parse_args()
     a.workload = ALIASES.get(a.workload, a.workload)
     if a.workload not in WORKLOADS:
@@ -633,8 +638,92 @@ def run_ours_segmented(a):
     return 0
 
 
+def run_ours_serve(a):
+    """Served (continuous batching) vs sequential plain sorts on one Poisson trace;
+    then both arms on a backlog (every request queued at once) for capacity."""
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    import inputs
+    import paper_1808_10292_gb300 as isort
+    from paper_1808_10292_gb300 import serve, tune
+    applied = tune.apply(32, 0)
+    tune.apply(32, 32)
+    arrivals, sizes, payload = inputs.requests(int(2000 * a.serve_seconds * 1.2) + 10, seed=a.seed)
+
+    def make_fill(rid, n, pay):
+        def fill(keys, vals, stream):
+            inputs.device_keys(n, 32, "uniform", seed=a.seed,
+                               stream=inputs.STREAM_REQUEST_BASE + rid, out=keys,
+                               cuda_stream=stream)
+            if vals is not None:
+                inputs.device_iota(n, 32, out=vals, cuda_stream=stream)
+        return fill
+
+    def arm(batching, arr, duration):
+        srv = serve.SortServer(budget_bytes=40 << 30, num_streams=4, max_batch_keys=1 << 27,
+                               max_batch_requests=2048, batching=batching)
+        # warm-up: a few requests through the same server
+        wa = np.zeros(16)
+        serve.drive(srv, wa, sizes[:16], payload[:16], make_fill, duration_s=1.0)
+        srv.close()
+        srv = serve.SortServer(budget_bytes=40 << 30, num_streams=4, max_batch_keys=1 << 27,
+                               max_batch_requests=2048, batching=batching)
+        t0 = time.perf_counter()
+        reqs = serve.drive(srv, arr, sizes, payload, make_fill, duration_s=duration)
+        srv.close()
+        wall = time.perf_counter() - t0
+        if srv.errors:
+            raise RuntimeError(f"serving errors: {srv.errors[:3]}")
+        out = serve.latency_summary(reqs)
+        out.update({"batches": srv.batches, "rejected": len(srv.rejected), "wall_s": wall})
+        del srv
+        torch.cuda.empty_cache()
+        return out
+
+    served = arm(True, arrivals, a.serve_seconds)
+    sequential = arm(False, arrivals, a.serve_seconds)
+    # capacity: a backlog of the first 4,000 requests, all queued at t = 0
+    backlog = np.zeros_like(arrivals)
+    cap_n = 4000
+    cap_served = arm(True, backlog[:cap_n], 1.0)
+    cap_seq = arm(False, backlog[:cap_n], 1.0)
+    line = {
+        "metric": "served keys/s and p50/p99 latency (Poisson 2,000 req/s, sizes log-uniform in "
+                  "[2^10, 2^24] uint32 keys, half with uint32 payloads, 40 GB budget)",
+        "value": served["keys_per_s"],
+        "unit": "keys/s",
+        "n_gpus": 1,
+        "steps": served["requests"],
+        "warmup": 16,
+        "ms_per_step": served["mean_ms"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32+u32",
+        "data": "synthetic",
+        "config": {"workload": a.workload, "rate_per_s": 2000, "seconds": a.serve_seconds,
+                   "budget_bytes": 40 << 30, "streams": 4, "max_batch_keys": 1 << 27,
+                   "tuned": applied, "seed": a.seed},
+        "served": served,
+        "sequential_plain_sorts": sequential,
+        "capacity_backlog_4000": {"served": cap_served, "sequential": cap_seq,
+                                  "speedup": cap_served["keys_per_s"] / cap_seq["keys_per_s"]},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = parse()
+    if a.workload == "serve_poisson":
+        if a.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the serving workload has "
+                              "no CPU counterpart; the oracle arm is timed on the plain and "
+                              "segmented workloads"}))
+            return 0
+        return run_ours_serve(a)
     if a.workload == "segmented_20000":
         if a.impl == "reference":
             return run_reference_segmented(a)
