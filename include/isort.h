@@ -150,7 +150,10 @@ enum {
    * shared-memory reorder and at the end, then the look-back window count of
    * digit 0 and the SM id. A measurement hook; it does not change results. */
   ISORT_DEBUG_TRACE_PTR = 4,
-  ISORT_DEBUG_TRACE_PASS = 5
+  ISORT_DEBUG_TRACE_PASS = 5,
+  /* value = L2 prefetch distance of the radix-256 rounds in tiles (0 = off,
+   * -1 = default: one wave, SMs x 4). A tuning knob; results are unchanged. */
+  ISORT_DEBUG_PREFETCH_TILES = 6
 };
 isort_status isort_debug_set(int what, int64_t value);
 

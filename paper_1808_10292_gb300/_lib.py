@@ -17,7 +17,7 @@ STATUS = {0: "ISORT_OK", 1: "ISORT_EINVAL", 2: "ISORT_ENOMEM", 3: "ISORT_ECUDA",
           4: "ISORT_ETIMEOUT", 5: "ISORT_EUNSUPPORTED"}
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
 DEBUG_SPIN_LIMIT, DEBUG_STALL_TILE, DEBUG_KERNEL_TIMING = 1, 2, 3
-DEBUG_TRACE_PTR, DEBUG_TRACE_PASS = 4, 5
+DEBUG_TRACE_PTR, DEBUG_TRACE_PASS, DEBUG_PREFETCH_TILES = 4, 5, 6
 NOALLOC_MAX_KEYS = 1 << 20
 
 _lib = None

@@ -36,6 +36,7 @@ KernelTimer g_timer;
 bool g_timing = false;
 unsigned long long* g_trace = nullptr;
 int g_trace_pass = 0;
+int64_t g_prefetch = -1;  // L2 prefetch distance in tiles; -1: one wave (SMs x 4)
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -211,6 +212,7 @@ isort_status run_lsd(void* keys, void* vals, int64_t n, int key_bits, int val_bi
   a.num_sms = num_sms();
   a.trace = g_trace;
   a.trace_pass = g_trace_pass;
+  a.prefetch_tiles = g_prefetch < 0 ? (int64_t)a.num_sms * 4 : g_prefetch;
   a.timer = nullptr;
   if (g_timing) {
     if (!g_timer.ready) {
@@ -476,6 +478,9 @@ isort_status isort_debug_set(int what, int64_t value) {
       return ISORT_OK;
     case ISORT_DEBUG_TRACE_PASS:
       g_trace_pass = (int)value;
+      return ISORT_OK;
+    case ISORT_DEBUG_PREFETCH_TILES:
+      g_prefetch = value;
       return ISORT_OK;
   }
   return ISORT_EINVAL;

@@ -41,6 +41,7 @@ struct LsdArgs {
   KernelTimer* timer;   // null unless kernel timing is on
   unsigned long long* trace;  // measurement hook: per-tile phase timestamps of one pass
   int trace_pass;
+  int64_t prefetch_tiles;     // L2 prefetch distance of the rounds, in tiles (0: off)
 };
 
 typedef cudaError_t (*LsdLaunchFn)(const LsdArgs&, cudaStream_t);
@@ -55,6 +56,7 @@ struct LsdEntry {
   size_t status_words_per_tile;  // look-back words per tile per buffer
   int status_buffers;            // look-back buffers (2: alternate by pass)
   LsdLaunchFn launch;
+  int cluster;                   // CTAs per cluster super-tile (1: none)
 };
 
 // Variant tables, one per key width (sort_k32.cu, sort_k64.cu).

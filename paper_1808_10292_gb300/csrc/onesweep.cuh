@@ -22,12 +22,16 @@
 //               digit in shared memory and write it out in runs.
 //   k_copy_back copies the result home when an odd number of rounds ran.
 #pragma once
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "common.cuh"
 #include "isort_internal.h"
 
 namespace isort {
+
+namespace cg = cooperative_groups;
 
 template <typename K, int BITS>
 struct DigitLayout {
@@ -177,7 +181,20 @@ struct PassParams {
   uint32_t spin_limit;
   int64_t stall_tile;
   unsigned long long* trace;  // measurement hook: per tile, phase timestamps (or null)
+  int64_t prefetch_tiles;     // L2-prefetch the input of the tile this many ids ahead (0: off)
 };
+
+// Keep DRAM busy while tiles are ranking: one thread of the CTA asks the copy
+// engine to bring the input of a tile about one wave ahead into L2, so that
+// tile's loads hit L2. Skipped when the range is not 16-byte aligned.
+template <typename T>
+__device__ __forceinline__ void prefetch_tile(const T* base, int64_t first, int64_t count) {
+  const char* a = reinterpret_cast<const char*>(base + first);
+  const uintptr_t mis = reinterpret_cast<uintptr_t>(a) & 15;
+  if (count <= 0 || mis) return;
+  const uint32_t bytes = (uint32_t)((count * (int64_t)sizeof(T)) & ~int64_t(15));
+  if (bytes) prefetch_l2(a, bytes);
+}
 
 __device__ __forceinline__ uint32_t lanemask_ge() {
   uint32_t m;
@@ -218,6 +235,7 @@ template <int R, int LB>
 __device__ __forceinline__ uint32_t lookback_exclusive(const uint32_t* status, uint32_t tile,
                                                        int d, uint32_t spin_limit, uint32_t* err,
                                                        uint32_t& windows) {
+  static_assert(LB <= 32, "window flags are kept in one word");
   uint32_t excl = 0, polls = 0;
   int64_t t = (int64_t)tile - 1;
   while (true) {
@@ -226,38 +244,181 @@ __device__ __forceinline__ uint32_t lookback_exclusive(const uint32_t* status, u
 #pragma unroll
     for (int k = 0; k < LB; ++k)  // below tile 0 reads as "inclusive, count 0"
       s[k] = (t - k >= 0) ? ld_relaxed(&status[(size_t)(t - k) * R + d]) : kFlagInc;
-    uint32_t add = 0;
-    int consumed = 0;
-    bool found_inc = false, blocked = false;
+    // Branch-free scan of the window: stop at the first word that is not
+    // published yet (poll it again) or that is inclusive (done after it).
+    uint32_t unpublished = 0, inclusive = 0;
 #pragma unroll
     for (int k = 0; k < LB; ++k) {
-      if (!found_inc && !blocked) {
-        const uint32_t f = s[k] & ~kCountMask;
-        if (f == 0) {
-          blocked = true;  // tile t-k has published nothing yet: poll it again
-        } else {
-          add += s[k] & kCountMask;
-          ++consumed;
-          found_inc = (f & kFlagInc) != 0;
-        }
-      }
+      unpublished |= (uint32_t)(s[k] < kFlagAgg) << k;
+      inclusive |= (s[k] >> 31) << k;
     }
-    excl += add;
-    if (found_inc) break;
-    t -= consumed;
-    if (blocked) {
+    const uint32_t stop = unpublished | inclusive;
+    const int first = stop ? __ffs(stop) - 1 : LB;
+    const bool done = (inclusive >> first) & 1u;  // LB <= 31: bit LB is 0 when no stop
+    const int take = first + (done ? 1 : 0);
+#pragma unroll
+    for (int k = 0; k < LB; ++k) excl += (k < take) ? (s[k] & kCountMask) : 0u;
+    if (done) break;
+    t -= take;
+    if (take < LB) {  // blocked on tile t: it has published nothing yet
       if (++polls >= spin_limit) {
         atomicOr(err, kErrTimeout);
         break;
       }
-      __nanosleep(32);
+      __nanosleep(64);
     }
   }
   return excl;
 }
 
-// One tile of one count-sort round. FULL: the tile holds TILE keys, so no
-// per-key bounds predicate is needed.
+// ---- the phases of one tile (shared by the plain, segmented and cluster
+// rounds). FULL: the tile holds TILE keys, so no per-key bounds predicate.
+
+// Load: warp w owns keys [w*32*KPT, (w+1)*32*KPT) of the tile, lane-striped,
+// so each warp instruction reads 32 consecutive keys.
+template <typename K, typename V, int KPT, bool FULL>
+__device__ __forceinline__ void tile_load(const K* __restrict__ kin, const V* vin,
+                                          int64_t tile_base, int tile_n, int wofs, K (&key)[KPT],
+                                          V (&val)[HasVal<V>::value ? KPT : 1]) {
+  const int64_t g0 = tile_base + wofs;
+#pragma unroll
+  for (int i = 0; i < KPT; ++i)
+    key[i] = (FULL || wofs + i * 32 < tile_n) ? kin[g0 + i * 32] : K(0);
+  if constexpr (HasVal<V>::value) {
+#pragma unroll
+    for (int i = 0; i < KPT; ++i)
+      val[i] = (FULL || wofs + i * 32 < tile_n) ? vin[g0 + i * 32] : V(0);
+  }
+}
+
+// Rank: position of each key among the warp's keys of the same digit, in input
+// order (i ascending, then lane ascending). Lanes find their peers (same digit,
+// same iteration) through a per-warp shared-memory mask per digit: each lane
+// ORs in its bit, and after a warp barrier reads the mask back. The highest
+// peer advances the warp's private counter of the digit with one atomic add
+// and hands the old value to its peers.
+// Ordering with one warp barrier per iteration: three mask buffers rotate, and
+// the slot used in iteration i-2 is cleared in iteration i -- after the barrier
+// of i-1 (so every read of it is done) and before the barrier of i (which
+// precedes the next OR into that buffer, in i+1). A counter update of
+// iteration i precedes the barrier of i+1, which precedes the next update.
+// The masks live in the staging area (zeroed), which is free until the
+// reorder. Ranks (< TILE <= 65536) are kept as 16-bit halves.
+template <typename K, int R, int KPT, int MASK_BUFS, bool FULL>
+__device__ __forceinline__ void tile_rank(const K (&key)[KPT], int shift, uint32_t mask,
+                                          int tile_n, int wofs, uint32_t* my, uint32_t* mm,
+                                          uint32_t (&rank2)[(KPT + 1) / 2]) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t ge = lanemask_ge();
+  const uint32_t bit = 1u << lane;
+  uint32_t* slot1 = mm;  // slot of iteration i-1
+  uint32_t* slot2 = mm;  // slot of iteration i-2
+  bool lead1 = false, lead2 = false;
+#pragma unroll
+  for (int i = 0; i < KPT; ++i) {
+    const bool valid = FULL || wofs + i * 32 < tile_n;
+    const uint32_t d = digit_of(key[i], shift, mask);
+    uint32_t* slot = mm + (i % MASK_BUFS) * R + d;
+    if (lead2) *slot2 = 0u;
+    if (valid) atomicOr(slot, bit);
+    __syncwarp();
+    const uint32_t peers = valid ? *slot : 0u;
+    const bool leader = valid && (peers >> lane) == 1u;  // highest peer
+    uint32_t after = 0;
+    if (leader) after = atomicAdd(&my[d], __popc(peers)) + __popc(peers);
+    after = __shfl_sync(kFullMask, after, (31 - __clz(peers)) & 31);
+    const uint32_t r = after - __popc(peers & ge);  // = old count + peers below me
+    rank2[i >> 1] = (i & 1) ? (rank2[i >> 1] | (r << 16)) : r;
+    slot2 = slot1;
+    lead2 = lead1;
+    slot1 = slot;
+    lead1 = leader;
+  }
+}
+
+// Per digit owned by this thread: turn the per-warp counts into warp-exclusive
+// offsets and return the tile's count of the digit.
+template <int R, int WARPS, int DPT>
+__device__ __forceinline__ uint32_t tile_digit_counts(uint32_t* s_wcnt, int tid,
+                                                      uint32_t (&dcnt)[DPT]) {
+  uint32_t tsum = 0;
+#pragma unroll
+  for (int j = 0; j < DPT; ++j) {
+    const int d = tid * DPT + j;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) {
+      const uint32_t c = s_wcnt[w * R + d];
+      s_wcnt[w * R + d] = sum;
+      sum += c;
+    }
+    dcnt[j] = sum;
+    tsum += sum;
+  }
+  return tsum;
+}
+
+// Reorder the tile by digit in shared memory (stable by construction); with
+// payloads, rank2 then holds each key's tile position.
+template <typename K, typename V, int KPT, bool FULL>
+__device__ __forceinline__ void tile_reorder(const K (&key)[KPT], uint32_t (&rank2)[(KPT + 1) / 2],
+                                             int shift, uint32_t mask, int tile_n, int wofs,
+                                             const uint32_t* myofs, K* s_keys) {
+#pragma unroll
+  for (int i = 0; i < KPT; ++i) {
+    if (FULL || wofs + i * 32 < tile_n) {
+      const uint32_t r = (rank2[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
+      const uint32_t pos = myofs[digit_of(key[i], shift, mask)] + r;
+      s_keys[pos] = key[i];
+      if constexpr (HasVal<V>::value) {  // keep the tile position for the payload pass
+        rank2[i >> 1] = (i & 1) ? ((rank2[i >> 1] & 0xffffu) | (pos << 16))
+                                : ((rank2[i >> 1] & 0xffff0000u) | pos);
+      }
+    }
+  }
+}
+
+// Write out: consecutive threads take consecutive tile slots, so each digit's
+// run lands on consecutive global addresses; every index is bounds-checked.
+// With payloads the staging area is reused for them (contains __syncthreads).
+template <typename K, typename V, int THREADS, int KPT, bool FULL>
+__device__ __forceinline__ void tile_scatter(const K* s_keys, V* s_vals, const uint32_t* s_adj,
+                                             const V (&val)[HasVal<V>::value ? KPT : 1],
+                                             const uint32_t (&rank2)[(KPT + 1) / 2], int shift,
+                                             uint32_t mask, int tile_n, int wofs, K* kout,
+                                             V* vout, uint32_t bound, uint32_t* err) {
+  constexpr bool HV = HasVal<V>::value;
+  const int tid = threadIdx.x;
+  uint32_t gpos[HV ? KPT : 1];
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    const int j = k * THREADS + tid;
+    if (FULL || j < tile_n) {
+      const K kk = s_keys[j];
+      const uint32_t g = s_adj[digit_of(kk, shift, mask)] + (uint32_t)j;
+      if (g < bound)
+        kout[g] = kk;
+      else
+        atomicOr(err, kErrBounds);
+      if constexpr (HV) gpos[k] = g;
+    }
+  }
+  if constexpr (HV) {
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < KPT; ++i)
+      if (FULL || wofs + i * 32 < tile_n)
+        s_vals[(rank2[i >> 1] >> ((i & 1) * 16)) & 0xffffu] = val[i];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const int j = k * THREADS + tid;
+      if ((FULL || j < tile_n) && gpos[k] < bound) vout[gpos[k]] = s_vals[j];
+    }
+  }
+}
+
+// One tile of one count-sort round with the decoupled look-back.
 //   tile       row of the look-back arrays (tile id in launch order)
 //   first      the tile opens its range (segment), so it has no predecessor
 //   tile_base  index of the tile's first key in kin / vin
@@ -278,91 +439,32 @@ __device__ __forceinline__ void onesweep_tile(const PassParams& p, uint32_t tile
   uint32_t* s_misc = s_adj + R;                           // [64]
   K* s_keys = reinterpret_cast<K*>(smem + S::HEADER_WORDS * 4);
   V* s_vals = reinterpret_cast<V*>(smem + S::HEADER_WORDS * 4);
-  (void)s_vals;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wofs = warp * 32 * KPT + lane;
   const bool publish = (int64_t)tile != p.stall_tile;
 
-  // ---- load: warp w owns keys [w*32*KPT, (w+1)*32*KPT) of the tile, lane-striped
   K key[KPT];
   V val[HV ? KPT : 1];
-  const int wofs = warp * 32 * KPT + lane;
-  const int64_t g0 = tile_base + wofs;
-#pragma unroll
-  for (int i = 0; i < KPT; ++i)
-    key[i] = (FULL || wofs + i * 32 < tile_n) ? kin[g0 + i * 32] : K(0);
-  if constexpr (HV) {
-#pragma unroll
-    for (int i = 0; i < KPT; ++i)
-      val[i] = (FULL || wofs + i * 32 < tile_n) ? vin[g0 + i * 32] : V(0);
-  }
-
-  // ---- rank: position of each key among the warp's keys of the same digit,
-  // in input order (i ascending, then lane ascending). Lanes find their peers
-  // (same digit, same iteration) through a per-warp shared-memory mask per
-  // digit: each lane ORs in its bit, and after a warp barrier reads the mask
-  // back. The highest peer advances the warp's private counter of the digit
-  // with one atomic add and hands the old value to its peers.
-  // Ordering with one warp barrier per iteration: three mask buffers rotate,
-  // and the slot used in iteration i-2 is cleared in iteration i -- after the
-  // barrier of i-1 (so every read of it is done) and before the barrier of i
-  // (which precedes the next OR into that buffer, in i+1). A counter update of
-  // iteration i precedes the barrier of i+1, which precedes the next update.
-  // The masks live in the staging area, which is free until the reorder.
-  // Ranks (< TILE <= 65536) are kept as 16-bit halves to save registers.
+  tile_load<K, V, KPT, FULL>(kin, vin, tile_base, tile_n, wofs, key, val);
   uint32_t rank2[(KPT + 1) / 2];
-  {
-    uint32_t* my = s_wcnt + warp * R;
-    uint32_t* mm = reinterpret_cast<uint32_t*>(s_keys) + warp * S::MASK_BUFS * R;
-    const uint32_t ge = lanemask_ge();
-    const uint32_t bit = 1u << lane;
-    uint32_t* slot1 = mm;  // slot of iteration i-1
-    uint32_t* slot2 = mm;  // slot of iteration i-2
-    bool lead1 = false, lead2 = false;
-#pragma unroll
-    for (int i = 0; i < KPT; ++i) {
-      const bool valid = FULL || wofs + i * 32 < tile_n;
-      const uint32_t d = digit_of(key[i], p.shift, p.mask);
-      uint32_t* slot = mm + (i % S::MASK_BUFS) * R + d;
-      if (lead2) *slot2 = 0u;
-      if (valid) atomicOr(slot, bit);
-      __syncwarp();
-      const uint32_t peers = valid ? *slot : 0u;
-      const bool leader = valid && (peers >> lane) == 1u;  // highest peer
-      uint32_t after = 0;
-      if (leader) after = atomicAdd(&my[d], __popc(peers)) + __popc(peers);
-      after = __shfl_sync(kFullMask, after, (31 - __clz(peers)) & 31);
-      const uint32_t r = after - __popc(peers & ge);  // = old count + peers below me
-      rank2[i >> 1] = (i & 1) ? (rank2[i >> 1] | (r << 16)) : r;
-      slot2 = slot1;
-      lead2 = lead1;
-      slot1 = slot;
-      lead1 = leader;
-    }
-  }
+  tile_rank<K, R, KPT, S::MASK_BUFS, FULL>(
+      key, p.shift, p.mask, tile_n, wofs, s_wcnt + warp * R,
+      reinterpret_cast<uint32_t*>(s_keys) + warp * S::MASK_BUFS * R, rank2);
   __syncthreads();
   if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 1] = globaltimer();
 
   // ---- per digit: warp-exclusive offsets and the tile's count, published at
-  // once (AGG, or INC for tile 0) so that later tiles can use it
+  // once (AGG, or INC for the first tile) so that later tiles can use it
   uint32_t dcnt[DPT];
   uint32_t tsum = 0;
   const bool owner = tid < S::DTHREADS;
   if (owner) {
+    tsum = tile_digit_counts<R, WARPS, DPT>(s_wcnt, tid, dcnt);
+    if (publish)
 #pragma unroll
-    for (int j = 0; j < DPT; ++j) {
-      const int d = tid * DPT + j;
-      uint32_t sum = 0;
-#pragma unroll
-      for (int w = 0; w < WARPS; ++w) {
-        const uint32_t c = s_wcnt[w * R + d];
-        s_wcnt[w * R + d] = sum;
-        sum += c;
-      }
-      dcnt[j] = sum;
-      tsum += sum;
-      if (publish)
-        st_relaxed(&p.status[(size_t)tile * R + d], (first ? kFlagInc : kFlagAgg) | sum);
-    }
+      for (int j = 0; j < DPT; ++j)
+        st_relaxed(&p.status[(size_t)tile * R + tid * DPT + j],
+                   (first ? kFlagInc : kFlagAgg) | dcnt[j]);
   }
   uint32_t total;
   uint32_t run = block_exclusive_scan<THREADS>(tsum, s_misc + 1, total);
@@ -391,53 +493,13 @@ __device__ __forceinline__ void onesweep_tile(const PassParams& p, uint32_t tile
   __syncthreads();
   if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 3] = globaltimer();
 
-  // ---- reorder the tile by digit in shared memory (stable by construction)
-  const uint32_t* myofs = s_wcnt + warp * R;
-#pragma unroll
-  for (int i = 0; i < KPT; ++i) {
-    if (FULL || wofs + i * 32 < tile_n) {
-      const uint32_t r = (rank2[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
-      const uint32_t pos = myofs[digit_of(key[i], p.shift, p.mask)] + r;
-      s_keys[pos] = key[i];
-      if constexpr (HV) {  // keep the tile position for the payload pass
-        rank2[i >> 1] = (i & 1) ? ((rank2[i >> 1] & 0xffffu) | (pos << 16))
-                                : ((rank2[i >> 1] & 0xffff0000u) | pos);
-      }
-    }
-  }
+  tile_reorder<K, V, KPT, FULL>(key, rank2, p.shift, p.mask, tile_n, wofs, s_wcnt + warp * R,
+                                s_keys);
   __syncthreads();
   if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 4] = globaltimer();
 
-  // ---- write out: consecutive threads take consecutive tile slots, so each
-  // digit's run lands on consecutive global addresses
-  uint32_t gpos[HV ? KPT : 1];
-  const uint32_t n32 = bound;
-#pragma unroll
-  for (int k = 0; k < KPT; ++k) {
-    const int j = k * THREADS + tid;
-    if (FULL || j < tile_n) {
-      const K kk = s_keys[j];
-      const uint32_t g = s_adj[digit_of(kk, p.shift, p.mask)] + (uint32_t)j;
-      if (g < n32)
-        kout[g] = kk;
-      else
-        atomicOr(p.err, kErrBounds);
-      if constexpr (HV) gpos[k] = g;
-    }
-  }
-  if constexpr (HV) {
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < KPT; ++i)
-      if (FULL || wofs + i * 32 < tile_n)
-        s_vals[(rank2[i >> 1] >> ((i & 1) * 16)) & 0xffffu] = val[i];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < KPT; ++k) {
-      const int j = k * THREADS + tid;
-      if ((FULL || j < tile_n) && gpos[k] < n32) vout[gpos[k]] = s_vals[j];
-    }
-  }
+  tile_scatter<K, V, THREADS, KPT, FULL>(s_keys, s_vals, s_adj, val, rank2, p.shift, p.mask,
+                                         tile_n, wofs, kout, vout, bound, p.err);
   if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 5] = globaltimer();
 }
 
@@ -466,6 +528,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
   __syncthreads();
   const uint32_t tile = s_misc[0];
   const int tile_n = (int)min((int64_t)TILE, p.n - (int64_t)tile * TILE);
+  if (p.prefetch_tiles && tid == 0) {
+    const int64_t pf = ((int64_t)tile + p.prefetch_tiles) * TILE;
+    const int64_t cnt = min((int64_t)TILE, p.n - pf);
+    prefetch_tile(static_cast<const K*>(src ? p.keys[1] : p.keys[0]), pf, cnt);
+    if constexpr (HasVal<V>::value)
+      prefetch_tile(static_cast<const V*>(src ? p.vals[1] : p.vals[0]), pf, cnt);
+  }
   if (p.trace && tid == 0) {
     p.trace[(size_t)tile * 8 + 0] = globaltimer();
     p.trace[(size_t)tile * 8 + 7] = smid();
@@ -485,6 +554,177 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
 }
 
 // ---------------------------------------------------------------------------
+// Cluster super-tiles: CL CTAs of one thread-block cluster handle CL
+// consecutive tiles (a super-tile). Each CTA ranks its tile, then stores its
+// digit counts into the leader CTA's shared memory (distributed shared memory).
+// The leader adds them up, publishes the super-tile's counts, runs ONE
+// decoupled look-back over earlier super-tiles (so the look-back chain moves
+// CL tiles per step), publishes the inclusive count and writes each CTA's
+// prefix (super-tile prefix + counts of the cluster's earlier tiles) into that
+// CTA's shared memory. Split-phase cluster barriers (arrive / wait) let every
+// CTA reorder its tile while the exchange is in flight.
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <typename K, typename V, int BITS, int THREADS, int KPT, int CL>
+struct ClusterShape {
+  using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
+  static constexpr size_t CCNT = S::HEADER_WORDS * 4 + S::STAGE_BYTES;  // [CL][R] counts
+  static constexpr size_t CPRE = CCNT + sizeof(uint32_t) * CL * S::R;   // [R] prefixes
+  static constexpr size_t SMEM = CPRE + sizeof(uint32_t) * S::R;
+};
+
+template <typename K, typename V, int BITS, int THREADS, int KPT, int CL, bool FULL>
+__device__ __forceinline__ void onesweep_cluster_tile(const PassParams& p, uint32_t super,
+                                                      unsigned rank, int64_t tile_base,
+                                                      int tile_n, const K* __restrict__ kin,
+                                                      K* __restrict__ kout, const V* vin, V* vout,
+                                                      unsigned char* smem) {
+  using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
+  using C = ClusterShape<K, V, BITS, THREADS, KPT, CL>;
+  constexpr int R = S::R, WARPS = S::WARPS, DPT = S::DPT;
+  constexpr bool HV = S::HV;
+  cg::cluster_group cluster = cg::this_cluster();
+  uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* s_adj = s_wcnt + WARPS * R;
+  uint32_t* s_misc = s_adj + R;
+  K* s_keys = reinterpret_cast<K*>(smem + S::HEADER_WORDS * 4);
+  V* s_vals = reinterpret_cast<V*>(smem + S::HEADER_WORDS * 4);
+  uint32_t* s_ccnt = reinterpret_cast<uint32_t*>(smem + C::CCNT);
+  uint32_t* s_cpre = reinterpret_cast<uint32_t*>(smem + C::CPRE);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wofs = warp * 32 * KPT + lane;
+  const bool leader = rank == 0;
+  const bool publish = (int64_t)super != p.stall_tile;
+
+  K key[KPT];
+  V val[HV ? KPT : 1];
+  tile_load<K, V, KPT, FULL>(kin, vin, tile_base, tile_n, wofs, key, val);
+  uint32_t rank2[(KPT + 1) / 2];
+  tile_rank<K, R, KPT, S::MASK_BUFS, FULL>(
+      key, p.shift, p.mask, tile_n, wofs, s_wcnt + warp * R,
+      reinterpret_cast<uint32_t*>(s_keys) + warp * S::MASK_BUFS * R, rank2);
+  __syncthreads();
+
+  // counts of this tile -> the leader's table; tile-local digit starts
+  uint32_t dcnt[DPT];
+  uint32_t tsum = 0;
+  const bool owner = tid < S::DTHREADS;
+  if (owner) {
+    tsum = tile_digit_counts<R, WARPS, DPT>(s_wcnt, tid, dcnt);
+    uint32_t* lc = cluster.map_shared_rank(s_ccnt, 0);
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) lc[rank * R + tid * DPT + j] = dcnt[j];
+  }
+  uint32_t total;
+  uint32_t run = block_exclusive_scan<THREADS>(tsum, s_misc + 1, total);
+  uint32_t tstart[DPT];
+  if (owner) {
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+      const int d = tid * DPT + j;
+      tstart[j] = run;
+#pragma unroll
+      for (int w = 0; w < WARPS; ++w) s_wcnt[w * R + d] += run;
+      run += dcnt[j];
+    }
+  }
+  cluster_arrive();  // phase 2: this CTA's counts are in the leader's table
+  __syncthreads();
+  tile_reorder<K, V, KPT, FULL>(key, rank2, p.shift, p.mask, tile_n, wofs, s_wcnt + warp * R,
+                                s_keys);
+  cluster_wait();
+  if (leader && owner) {
+    uint32_t windows = 0;
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+      const int d = tid * DPT + j;
+      uint32_t sum = 0;
+#pragma unroll
+      for (int r = 0; r < CL; ++r) sum += s_ccnt[r * R + d];
+      uint32_t excl = 0;
+      if (super == 0) {
+        if (publish) st_relaxed(&p.status[d], kFlagInc | sum);
+      } else {
+        if (publish) st_relaxed(&p.status[(size_t)super * R + d], kFlagAgg | sum);
+        excl = lookback_exclusive<R, kLookbackWindow>(p.status, super, d, p.spin_limit, p.err,
+                                                      windows);
+        if (publish) st_relaxed(&p.status[(size_t)super * R + d], kFlagInc | (excl + sum));
+      }
+#pragma unroll
+      for (int r = 0; r < CL; ++r) {
+        cluster.map_shared_rank(s_cpre, r)[d] = excl;
+        excl += s_ccnt[r * R + d];
+      }
+    }
+  }
+  cluster_arrive();  // phase 3: every CTA's prefixes are written
+  cluster_wait();
+  if (owner) {
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+      const int d = tid * DPT + j;
+      s_adj[d] = p.base[d] + s_cpre[d] - tstart[j];
+    }
+  }
+  __syncthreads();
+  tile_scatter<K, V, THREADS, KPT, FULL>(s_keys, s_vals, s_adj, val, rank2, p.shift, p.mask,
+                                         tile_n, wofs, kout, vout, (uint32_t)p.n, p.err);
+}
+
+template <typename K, typename V, int BITS, int THREADS, int KPT, int CL, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_onesweep_cl(PassParams p) {
+  using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
+  constexpr int R = S::R, WARPS = S::WARPS, TILE = S::TILE;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* s_misc = s_wcnt + WARPS * R + R;
+  uint32_t* s_stage = reinterpret_cast<uint32_t*>(smem + S::HEADER_WORDS * 4);
+  cg::cluster_group cluster = cg::this_cluster();
+  const unsigned rank = cluster.block_rank();
+  const int tid = threadIdx.x;
+  if (p.status_next && rank == 0)
+    for (int d = tid; d < R; d += THREADS)
+      p.status_next[(size_t)(blockIdx.x / CL) * R + d] = 0;
+  if (p.skip[p.pass]) return;  // the digit is constant: this round is the identity (all CTAs)
+
+  int src = 0;
+  for (int q = 0; q < p.pass; ++q) src ^= (p.skip[q] == 0);
+  for (int i = tid; i < WARPS * R; i += THREADS) s_wcnt[i] = 0;
+  for (int i = tid; i < WARPS * S::MASK_BUFS * R; i += THREADS) s_stage[i] = 0;
+  if (rank == 0 && tid == 0) s_misc[0] = atomicAdd(p.counter, 1u);  // super-tiles in launch order
+  // phase 1: every CTA of the cluster is running (so distributed shared memory
+  // may be used), shared memory is zeroed and the leader holds the id
+  cluster_arrive();
+  cluster_wait();
+  const uint32_t super = cluster.map_shared_rank(s_misc, 0)[0];
+  const int64_t tile_base = ((int64_t)super * CL + rank) * TILE;
+  if (p.prefetch_tiles && tid == 0) {
+    const int64_t pf = tile_base + p.prefetch_tiles * TILE;
+    const int64_t cnt = min((int64_t)TILE, p.n - pf);
+    prefetch_tile(static_cast<const K*>(src ? p.keys[1] : p.keys[0]), pf, cnt);
+    if constexpr (HasVal<V>::value)
+      prefetch_tile(static_cast<const V*>(src ? p.vals[1] : p.vals[0]), pf, cnt);
+  }
+  const int64_t left = p.n - tile_base;
+  const int tile_n = (int)(left < 0 ? 0 : (left > TILE ? TILE : left));
+  const K* kin = static_cast<const K*>(src ? p.keys[1] : p.keys[0]);
+  K* kout = static_cast<K*>(src ? p.keys[0] : p.keys[1]);
+  const V* vin = static_cast<const V*>(src ? p.vals[1] : p.vals[0]);
+  V* vout = static_cast<V*>(src ? p.vals[0] : p.vals[1]);
+  if (tile_n == TILE)
+    onesweep_cluster_tile<K, V, BITS, THREADS, KPT, CL, true>(p, super, rank, tile_base, tile_n,
+                                                              kin, kout, vin, vout, smem);
+  else
+    onesweep_cluster_tile<K, V, BITS, THREADS, KPT, CL, false>(p, super, rank, tile_base, tile_n,
+                                                               kin, kout, vin, vout, smem);
+}
+
+// ---------------------------------------------------------------------------
 // k_copy_back: after an odd number of executed rounds the sorted keys sit in
 // the alternate buffer; copy them (and payloads) home. Otherwise a no-op.
 template <typename K, typename V>
@@ -501,18 +741,21 @@ __global__ void k_copy_back(const uint32_t* __restrict__ skip, int passes, K* ke
 }
 
 // ---------------------------------------------------------------------------
-// Host launcher for one whole sort with a given kernel shape.
-template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB>
+// Host launcher for one whole sort with a given kernel shape. CL = 1: one tile
+// per CTA with a per-tile look-back (k_onesweep); CL > 1: CL-CTA cluster
+// super-tiles (k_onesweep_cl).
+template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB, int CL>
 cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
   using L = DigitLayout<K, BITS>;
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
   constexpr int R = L::R, P = L::PASSES;
   const int64_t tiles = (a.n + S::TILE - 1) / S::TILE;
+  const int64_t rows = (tiles + CL - 1) / CL;  // look-back rows (tiles or super-tiles)
   cudaError_t e;
   // hist and counters are zeroed; status[0] too (later passes clear their own)
   if ((e = cudaMemsetAsync(a.hist, 0, sizeof(uint32_t) * P * R, st))) return e;
   if ((e = cudaMemsetAsync(a.counters, 0, sizeof(uint32_t) * P, st))) return e;
-  if ((e = cudaMemsetAsync(a.status[0], 0, sizeof(uint32_t) * R * tiles, st))) return e;
+  if ((e = cudaMemsetAsync(a.status[0], 0, sizeof(uint32_t) * R * rows, st))) return e;
 
   // 32 counter columns for 32-bit keys (4 passes: 128 KiB), 16 for 64-bit
   // keys (8 passes: 128 KiB); one 1024-thread CTA per SM.
@@ -531,12 +774,6 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
   k_scan<256><<<P, 256, 0, st>>>(a.hist, a.base, a.skip, R, a.n);
   timer_end(a.timer, st);
 
-  auto kern = k_onesweep<K, V, BITS, THREADS, KPT, MINB>;
-  if (S::SMEM > 48 * 1024) {
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)S::SMEM)))
-      return e;
-  }
   PassParams pp;
   pp.keys[0] = a.keys;
   pp.keys[1] = a.alt_keys;
@@ -546,19 +783,60 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
   pp.skip = a.skip;
   pp.err = a.err;
   pp.spin_limit = a.spin_limit;
-  for (int q = 0; q < P; ++q) {
-    pp.pass = q;
-    pp.shift = q * BITS;
-    pp.mask = (1u << L::width(q)) - 1;
-    pp.base = a.base + (size_t)q * R;
-    pp.status = a.status[q & 1];
-    pp.status_next = (q + 1 < P) ? a.status[(q + 1) & 1] : nullptr;
-    pp.counter = a.counters + q;
-    pp.stall_tile = (q == 0) ? a.stall_tile : -1;
-    pp.trace = (q == a.trace_pass) ? a.trace : nullptr;
-    timer_begin(a.timer, "k_onesweep", st);
-    kern<<<(unsigned)tiles, THREADS, S::SMEM, st>>>(pp);
-    timer_end(a.timer, st);
+  pp.prefetch_tiles = a.prefetch_tiles;
+  if constexpr (CL == 1) {
+    auto kern = k_onesweep<K, V, BITS, THREADS, KPT, MINB>;
+    if (S::SMEM > 48 * 1024) {
+      if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)S::SMEM)))
+        return e;
+    }
+    for (int q = 0; q < P; ++q) {
+      pp.pass = q;
+      pp.shift = q * BITS;
+      pp.mask = (1u << L::width(q)) - 1;
+      pp.base = a.base + (size_t)q * R;
+      pp.status = a.status[q & 1];
+      pp.status_next = (q + 1 < P) ? a.status[(q + 1) & 1] : nullptr;
+      pp.counter = a.counters + q;
+      pp.stall_tile = (q == 0) ? a.stall_tile : -1;
+      pp.trace = (q == a.trace_pass) ? a.trace : nullptr;
+      timer_begin(a.timer, "k_onesweep", st);
+      kern<<<(unsigned)tiles, THREADS, S::SMEM, st>>>(pp);
+      timer_end(a.timer, st);
+    }
+  } else {
+    using C = ClusterShape<K, V, BITS, THREADS, KPT, CL>;
+    auto kern = k_onesweep_cl<K, V, BITS, THREADS, KPT, CL, MINB>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)C::SMEM)))
+      return e;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(rows * CL));
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    for (int q = 0; q < P; ++q) {
+      pp.pass = q;
+      pp.shift = q * BITS;
+      pp.mask = (1u << L::width(q)) - 1;
+      pp.base = a.base + (size_t)q * R;
+      pp.status = a.status[q & 1];
+      pp.status_next = (q + 1 < P) ? a.status[(q + 1) & 1] : nullptr;
+      pp.counter = a.counters + q;
+      pp.stall_tile = (q == 0) ? a.stall_tile : -1;
+      pp.trace = nullptr;
+      timer_begin(a.timer, "k_onesweep", st);
+      if ((e = cudaLaunchKernelEx(&cfg, kern, pp))) return e;
+      timer_end(a.timer, st);
+    }
   }
   int cblocks = (int)std::min<int64_t>((a.n + 255) / 256, (int64_t)a.num_sms * 8);
   timer_begin(a.timer, "k_copy_back", st);
@@ -571,7 +849,8 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
 }
 
 // MINB = CTAs that must fit on one SM (caps registers at 65536 / (THREADS * MINB)).
-template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB>
+// CL = CTAs per cluster super-tile (1: plain per-tile look-back).
+template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB, int CL = 1>
 constexpr LsdEntry lsd_entry() {
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
   return LsdEntry{(int)(8 * sizeof(K)),
@@ -579,12 +858,13 @@ constexpr LsdEntry lsd_entry() {
                   BITS,
                   THREADS,
                   KPT,
-                  S::TILE,
+                  (int64_t)S::TILE * CL,  // one look-back row per tile or super-tile
                   S::R,
                   DigitLayout<K, BITS>::PASSES,
                   (size_t)S::R,
                   2,
-                  &lsd_launch<K, V, BITS, THREADS, KPT, MINB>};
+                  &lsd_launch<K, V, BITS, THREADS, KPT, MINB, CL>,
+                  CL};
 }
 
 }  // namespace isort

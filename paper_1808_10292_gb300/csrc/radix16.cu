@@ -441,7 +441,8 @@ constexpr LsdEntry r16_entry() {
                   (int)(8 * sizeof(K)) / 16,
                   (size_t)kR16,        // the count matrix: one row per block
                   1,                   // in one buffer
-                  &r16_launch<K, V>};
+                  &r16_launch<K, V>,
+                  1};
 }
 
 static const LsdEntry kR16None32[] = {r16_entry<uint32_t, NoVal>()};

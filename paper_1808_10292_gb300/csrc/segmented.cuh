@@ -373,6 +373,7 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
   pp.spin_limit = a.spin_limit;
   pp.stall_tile = -1;
   pp.trace = nullptr;
+  pp.prefetch_tiles = 0;
   for (int q = 0; q < P; ++q) {
     pp.pass = q;
     pp.shift = q * 8;

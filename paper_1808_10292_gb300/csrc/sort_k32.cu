@@ -10,10 +10,14 @@ static const LsdEntry kK32None8[] = {
     lsd_entry<uint32_t, NoVal, 8, 512, 16, 1>(),
     lsd_entry<uint32_t, NoVal, 8, 256, 24, 2>(),
     lsd_entry<uint32_t, NoVal, 8, 512, 12, 2>(),
+    lsd_entry<uint32_t, NoVal, 8, 256, 16, 4, 8>(),  // 8-CTA cluster super-tiles
+    lsd_entry<uint32_t, NoVal, 8, 256, 16, 4, 4>(),
+    lsd_entry<uint32_t, NoVal, 8, 256, 24, 2, 8>(),
 };
 static const LsdEntry kK32V32_8[] = {
     lsd_entry<uint32_t, uint32_t, 8, 256, 12, 3>(),
     lsd_entry<uint32_t, uint32_t, 8, 256, 16, 2>(),
+    lsd_entry<uint32_t, uint32_t, 8, 256, 12, 3, 8>(),
 };
 static const LsdEntry kK32V64_8[] = {
     lsd_entry<uint32_t, uint64_t, 8, 256, 12, 2>(),

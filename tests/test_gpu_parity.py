@@ -37,8 +37,9 @@ def gpu_sort(keys_np, vals_np=None, radix_bits=8):  # noqa: D401
 
 
 def edge_sizes(tile):
+    # tile edges, and super-tile edges of the cluster variants (up to 8 tiles)
     return sorted({0, 1, 2, 3, 31, 32, 33, 255, 257, tile - 1, tile, tile + 1, 2 * tile + 5,
-                   5 * tile - 3})
+                   5 * tile - 3, 8 * tile - 1, 8 * tile + 1, 17 * tile + 3})
 
 
 def test_device_generator_matches_host_generator():
@@ -142,11 +143,14 @@ def test_concurrent_streams_give_the_same_results():
         assert np.array_equal(to_host(t), oracle.radix_sort(d, radix_bits=8))
 
 
-def test_bounded_wait_reports_timeout_and_context_survives():
+@pytest.mark.parametrize("variant", [0, -1])
+def test_bounded_wait_reports_timeout_and_context_survives(variant):
     """A tile that never publishes makes its successors' bounded waits give up:
     the error is latched and reported, no GPU hang, and the next sort is fine."""
-    n = 4 * 4096 * 4
+    n = 64 * 4096  # several look-back rows even for 8-tile cluster super-tiles
     k = to_dev(inputs.keys(n, 32, "uniform", seed=6))
+    nv = len(isort.tune_variants(32, 0, 8))
+    isort.tune_set(32, 0, 8, variant % nv)  # the plain variant and a cluster variant
     isort.debug_set(_lib.DEBUG_SPIN_LIMIT, 2000)
     isort.debug_set(_lib.DEBUG_STALL_TILE, 1)
     try:
@@ -156,6 +160,7 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     finally:
         isort.debug_set(_lib.DEBUG_STALL_TILE, -1)
         isort.debug_set(_lib.DEBUG_SPIN_LIMIT, 0)
+        isort.tune_set(32, 0, 8, -1)
     d = inputs.keys(n, 32, "uniform", seed=7)
     assert np.array_equal(gpu_sort(d), np.sort(d))
 
