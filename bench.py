@@ -65,6 +65,8 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="duration of each arm of the serving workload")
+    ap.add_argument("--n", type=int, default=0,
+                    help="override the key count of a plain workload (small profiling cases)")
     a = ap.parse_args()
     a.workload = ALIASES.get(a.workload, a.workload)
     if a.workload not in WORKLOADS:
@@ -316,6 +318,8 @@ def run_ours(a):
     from paper_1808_10292_gb300 import _lib
 
     n, kb, vb, rb, desc = WORKLOADS[a.workload]
+    if a.n:
+        n, desc = a.n, f"{desc}; n overridden to {a.n}"
     kdt = torch.uint32 if kb == 32 else torch.uint64
     pristine = inputs.device_keys(n, kb, a.dist, a.seed)
     keys = torch.empty_like(pristine)
