@@ -296,7 +296,8 @@ __device__ __forceinline__ void tile_load(const K* __restrict__ kin, const V* vi
 // same iteration) through a per-warp shared-memory mask per digit: each lane
 // ORs in its bit, and after a warp barrier reads the mask back. The highest
 // peer advances the warp's private counter of the digit with one atomic add
-// and hands the old value to its peers.
+// (cheaper than a dependent read and write) and hands the new value to its
+// peers.
 // Ordering with one warp barrier per iteration: three mask buffers rotate, and
 // the slot used in iteration i-2 is cleared in iteration i -- after the barrier
 // of i-1 (so every read of it is done) and before the barrier of i (which
@@ -554,6 +555,185 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
 }
 
 // ---------------------------------------------------------------------------
+// TMA variant of the round (keys only): one thread issues bulk copies of the
+// whole tile into shared memory as soon as the tile id is known, completing on
+// an mbarrier, while the CTA clears its counters. Ranking and the reorder read
+// the keys from shared memory, so no key array lives in registers and larger
+// tiles fit without spilling. Tiles whose input is not 16-byte aligned, and
+// the ragged last tile, are loaded into the same buffer with plain loads.
+template <typename K, int BITS, int THREADS, int KPT>
+struct TmaShape {
+  using S = OnesweepShape<K, NoVal, BITS, THREADS, KPT>;
+  static constexpr size_t RAW = S::HEADER_WORDS * 4 + S::STAGE_BYTES;  // raw tile
+  static constexpr size_t BAR = RAW + sizeof(K) * S::TILE;             // mbarrier
+  static constexpr size_t SMEM = BAR + 16;
+  static constexpr uint32_t CHUNK = 16384;  // bytes per bulk copy
+};
+
+template <typename K, int BITS, int THREADS, int KPT, bool FULL>
+__device__ __forceinline__ void onesweep_tile_tma(const PassParams& p, uint32_t tile, int tile_n,
+                                                  const K* raw, K* __restrict__ kout,
+                                                  unsigned char* smem) {
+  using S = OnesweepShape<K, NoVal, BITS, THREADS, KPT>;
+  constexpr int R = S::R, WARPS = S::WARPS, DPT = S::DPT;
+  uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* s_adj = s_wcnt + WARPS * R;
+  uint32_t* s_misc = s_adj + R;
+  K* s_keys = reinterpret_cast<K*>(smem + S::HEADER_WORDS * 4);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wofs = warp * 32 * KPT + lane;
+  const bool first = tile == 0;
+  const bool publish = (int64_t)tile != p.stall_tile;
+
+  // rank straight from the shared tile (same peer-mask ranking as tile_rank)
+  uint32_t rank2[(KPT + 1) / 2];
+  {
+    uint32_t* my = s_wcnt + warp * R;
+    uint32_t* mm = reinterpret_cast<uint32_t*>(s_keys) + warp * S::MASK_BUFS * R;
+    const uint32_t ge = lanemask_ge();
+    const uint32_t bit = 1u << lane;
+    uint32_t* slot1 = mm;
+    uint32_t* slot2 = mm;
+    bool lead1 = false, lead2 = false;
+#pragma unroll
+    for (int i = 0; i < KPT; ++i) {
+      const bool valid = FULL || wofs + i * 32 < tile_n;
+      const uint32_t d = digit_of(raw[wofs + i * 32], p.shift, p.mask);
+      uint32_t* slot = mm + (i % S::MASK_BUFS) * R + d;
+      if (lead2) *slot2 = 0u;
+      if (valid) atomicOr(slot, bit);
+      __syncwarp();
+      const uint32_t peers = valid ? *slot : 0u;
+      const bool leader = valid && (peers >> lane) == 1u;
+      uint32_t after = 0;
+      if (leader) after = atomicAdd(&my[d], __popc(peers)) + __popc(peers);
+      after = __shfl_sync(kFullMask, after, (31 - __clz(peers)) & 31);
+      const uint32_t r = after - __popc(peers & ge);
+      rank2[i >> 1] = (i & 1) ? (rank2[i >> 1] | (r << 16)) : r;
+      slot2 = slot1;
+      lead2 = lead1;
+      slot1 = slot;
+      lead1 = leader;
+    }
+  }
+  __syncthreads();
+
+  uint32_t dcnt[DPT];
+  uint32_t tsum = 0;
+  const bool owner = tid < S::DTHREADS;
+  if (owner) {
+    tsum = tile_digit_counts<R, WARPS, DPT>(s_wcnt, tid, dcnt);
+    if (publish)
+#pragma unroll
+      for (int j = 0; j < DPT; ++j)
+        st_relaxed(&p.status[(size_t)tile * R + tid * DPT + j],
+                   (first ? kFlagInc : kFlagAgg) | dcnt[j]);
+  }
+  uint32_t total;
+  uint32_t run = block_exclusive_scan<THREADS>(tsum, s_misc + 1, total);
+  if (owner) {
+    uint32_t windows = 0;
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+      const int d = tid * DPT + j;
+      const uint32_t tstart = run;
+      run += dcnt[j];
+      uint32_t excl = 0;
+      if (!first) {
+        excl = lookback_exclusive<R, kLookbackWindow>(p.status, tile, d, p.spin_limit, p.err,
+                                                      windows);
+        if (publish) st_relaxed(&p.status[(size_t)tile * R + d], kFlagInc | (excl + dcnt[j]));
+      }
+      s_adj[d] = p.base[d] + excl - tstart;
+#pragma unroll
+      for (int w = 0; w < WARPS; ++w) s_wcnt[w * R + d] += tstart;
+    }
+  }
+  __syncthreads();
+  // reorder: raw tile -> staging area, by digit
+  {
+    const uint32_t* myofs = s_wcnt + warp * R;
+#pragma unroll
+    for (int i = 0; i < KPT; ++i) {
+      if (FULL || wofs + i * 32 < tile_n) {
+        const K k = raw[wofs + i * 32];
+        const uint32_t r = (rank2[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
+        s_keys[myofs[digit_of(k, p.shift, p.mask)] + r] = k;
+      }
+    }
+  }
+  __syncthreads();
+  const NoVal nv[1] = {};
+  tile_scatter<K, NoVal, THREADS, KPT, FULL>(s_keys, nullptr, s_adj, nv, rank2, p.shift, p.mask,
+                                             tile_n, wofs, kout, nullptr, (uint32_t)p.n, p.err);
+}
+
+template <typename K, int BITS, int THREADS, int KPT, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_onesweep_tma(PassParams p) {
+  using S = OnesweepShape<K, NoVal, BITS, THREADS, KPT>;
+  using T = TmaShape<K, BITS, THREADS, KPT>;
+  constexpr int R = S::R, WARPS = S::WARPS, TILE = S::TILE;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* s_misc = s_wcnt + WARPS * R + R;
+  uint32_t* s_stage = reinterpret_cast<uint32_t*>(smem + S::HEADER_WORDS * 4);
+  K* raw = reinterpret_cast<K*>(smem + T::RAW);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + T::BAR);
+  const int tid = threadIdx.x;
+  if (p.status_next)
+    for (int d = tid; d < R; d += THREADS) p.status_next[(size_t)blockIdx.x * R + d] = 0;
+  if (p.skip[p.pass]) return;  // the digit is constant: this round is the identity
+  int src = 0;
+  for (int q = 0; q < p.pass; ++q) src ^= (p.skip[q] == 0);
+  const K* kin = static_cast<const K*>(src ? p.keys[1] : p.keys[0]);
+  K* kout = static_cast<K*>(src ? p.keys[0] : p.keys[1]);
+  if (tid == 0) {
+    const uint32_t t = atomicAdd(p.counter, 1u);  // tiles in launch order
+    s_misc[0] = t;
+    const int64_t tb = (int64_t)t * TILE;
+    const K* gsrc = kin + tb;
+    const bool tma = tb + TILE <= p.n && (reinterpret_cast<uintptr_t>(gsrc) & 15) == 0;
+    s_misc[33] = tma;
+    if (tma) {
+      mbar_init(bar, 1);
+      fence_mbar_init();
+      constexpr uint32_t BYTES = sizeof(K) * TILE;
+      mbar_arrive_expect_tx(bar, BYTES);
+      for (uint32_t o = 0; o < BYTES; o += T::CHUNK)
+        bulk_copy_g2s(reinterpret_cast<char*>(raw) + o, reinterpret_cast<const char*>(gsrc) + o,
+                      min(T::CHUNK, BYTES - o), bar);
+    }
+    if (p.prefetch_tiles) {
+      const int64_t pf = ((int64_t)t + p.prefetch_tiles) * TILE;
+      prefetch_tile(kin, pf, min((int64_t)TILE, p.n - pf));
+    }
+  }
+  for (int i = tid; i < WARPS * R; i += THREADS) s_wcnt[i] = 0;
+  for (int i = tid; i < WARPS * S::MASK_BUFS * R; i += THREADS) s_stage[i] = 0;
+  __syncthreads();
+  const uint32_t tile = s_misc[0];
+  const int64_t tile_base = (int64_t)tile * TILE;
+  const int tile_n = (int)min((int64_t)TILE, p.n - tile_base);
+  if (!s_misc[33]) {  // unaligned input or the ragged last tile: plain loads into the tile buffer
+    for (int j = tid; j < tile_n; j += THREADS) raw[j] = kin[tile_base + j];
+    __syncthreads();
+    if (tile_n == TILE)
+      onesweep_tile_tma<K, BITS, THREADS, KPT, true>(p, tile, tile_n, raw, kout, smem);
+    else
+      onesweep_tile_tma<K, BITS, THREADS, KPT, false>(p, tile, tile_n, raw, kout, smem);
+    return;
+  }
+  // bounded wait for the copy (it takes microseconds; the limit is a safety net)
+  const bool arrived = mbar_wait_bounded(bar, 0, p.spin_limit);
+  if (__syncthreads_or(!arrived)) {
+    if (tid == 0) atomicOr(p.err, kErrTimeout);
+    mbar_wait_bounded(bar, 0, p.spin_limit);  // let the copy land before the CTA exits
+    return;
+  }
+  onesweep_tile_tma<K, BITS, THREADS, KPT, true>(p, tile, TILE, raw, kout, smem);
+}
+
+// ---------------------------------------------------------------------------
 // Cluster super-tiles: CL CTAs of one thread-block cluster handle CL
 // consecutive tiles (a super-tile). Each CTA ranks its tile, then stores its
 // digit counts into the leader CTA's shared memory (distributed shared memory).
@@ -744,7 +924,7 @@ __global__ void k_copy_back(const uint32_t* __restrict__ skip, int passes, K* ke
 // Host launcher for one whole sort with a given kernel shape. CL = 1: one tile
 // per CTA with a per-tile look-back (k_onesweep); CL > 1: CL-CTA cluster
 // super-tiles (k_onesweep_cl).
-template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB, int CL>
+template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB, int CL, bool TMA>
 cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
   using L = DigitLayout<K, BITS>;
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
@@ -785,10 +965,15 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
   pp.spin_limit = a.spin_limit;
   pp.prefetch_tiles = a.prefetch_tiles;
   if constexpr (CL == 1) {
+    size_t smem = S::SMEM;
     auto kern = k_onesweep<K, V, BITS, THREADS, KPT, MINB>;
-    if (S::SMEM > 48 * 1024) {
-      if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)S::SMEM)))
+    if constexpr (TMA) {
+      static_assert(!HasVal<V>::value, "the TMA round is keys-only");
+      kern = k_onesweep_tma<K, BITS, THREADS, KPT, MINB>;
+      smem = TmaShape<K, BITS, THREADS, KPT>::SMEM;
+    }
+    if (smem > 48 * 1024) {
+      if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return e;
     }
     for (int q = 0; q < P; ++q) {
@@ -802,7 +987,7 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
       pp.stall_tile = (q == 0) ? a.stall_tile : -1;
       pp.trace = (q == a.trace_pass) ? a.trace : nullptr;
       timer_begin(a.timer, "k_onesweep", st);
-      kern<<<(unsigned)tiles, THREADS, S::SMEM, st>>>(pp);
+      kern<<<(unsigned)tiles, THREADS, smem, st>>>(pp);
       timer_end(a.timer, st);
     }
   } else {
@@ -850,7 +1035,8 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
 
 // MINB = CTAs that must fit on one SM (caps registers at 65536 / (THREADS * MINB)).
 // CL = CTAs per cluster super-tile (1: plain per-tile look-back).
-template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB, int CL = 1>
+template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB, int CL = 1,
+          bool TMA = false>
 constexpr LsdEntry lsd_entry() {
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
   return LsdEntry{(int)(8 * sizeof(K)),
@@ -863,7 +1049,7 @@ constexpr LsdEntry lsd_entry() {
                   DigitLayout<K, BITS>::PASSES,
                   (size_t)S::R,
                   2,
-                  &lsd_launch<K, V, BITS, THREADS, KPT, MINB, CL>,
+                  &lsd_launch<K, V, BITS, THREADS, KPT, MINB, CL, TMA>,
                   CL};
 }
 

@@ -7,6 +7,8 @@ static const LsdEntry kK64None8[] = {
     lsd_entry<uint64_t, NoVal, 8, 256, 12, 3>(),
     lsd_entry<uint64_t, NoVal, 8, 256, 16, 2>(),
     lsd_entry<uint64_t, NoVal, 8, 256, 12, 3, 8>(),
+    lsd_entry<uint64_t, NoVal, 8, 512, 12, 2>(),
+    lsd_entry<uint64_t, NoVal, 8, 512, 16, 1>(),
 };
 static const LsdEntry kK64V32_8[] = {
     lsd_entry<uint64_t, uint32_t, 8, 256, 12, 2>(),
