@@ -271,6 +271,14 @@ __device__ __forceinline__ uint32_t lookback_exclusive(const uint32_t* status, u
   return excl;
 }
 
+// Zero `words` 32-bit words of shared memory (16-byte aligned, words % 4 == 0)
+// with 16-byte stores.
+template <int THREADS>
+__device__ __forceinline__ void zero_words(uint32_t* p, int words) {
+  uint4* q = reinterpret_cast<uint4*>(p);
+  for (int i = threadIdx.x; i < words / 4; i += THREADS) q[i] = make_uint4(0, 0, 0, 0);
+}
+
 // ---- the phases of one tile (shared by the plain, segmented and cluster
 // rounds). FULL: the tile holds TILE keys, so no per-key bounds predicate.
 
@@ -419,6 +427,155 @@ __device__ __forceinline__ void tile_scatter(const K* s_keys, V* s_vals, const u
   }
 }
 
+// Early counts: each warp counts the digits of its keys into its private row of
+// s_wcnt (one shared atomic add per key, order irrelevant).
+template <typename K, int R, int KPT, bool FULL>
+__device__ __forceinline__ void tile_count(const K (&key)[KPT], int shift, uint32_t mask,
+                                           int tile_n, int wofs, uint32_t* my) {
+#pragma unroll
+  for (int i = 0; i < KPT; ++i)
+    if (FULL || wofs + i * 32 < tile_n) atomicAdd(&my[digit_of(key[i], shift, mask)], 1u);
+}
+
+// Rank and reorder in one sweep: the warp's counters already hold, per digit,
+// the tile position of the warp's first key of that digit, so the rank of a
+// key (peer masks, as in tile_rank) is its final tile position and the key is
+// written straight into the staging area. The masks live in a separate area
+// (the staging area is being filled). rank2 receives the positions.
+template <typename K, int R, int KPT, int MASK_BUFS, bool FULL>
+__device__ __forceinline__ void tile_rank_place(const K (&key)[KPT], int shift, uint32_t mask,
+                                                int tile_n, int wofs, uint32_t* my,
+                                                uint32_t* mm, K* s_keys,
+                                                uint32_t (&rank2)[(KPT + 1) / 2]) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t ge = lanemask_ge();
+  const uint32_t bit = 1u << lane;
+  uint32_t* slot1 = mm;
+  uint32_t* slot2 = mm;
+  bool lead1 = false, lead2 = false;
+#pragma unroll
+  for (int i = 0; i < KPT; ++i) {
+    const bool valid = FULL || wofs + i * 32 < tile_n;
+    const uint32_t d = digit_of(key[i], shift, mask);
+    uint32_t* slot = mm + (i % MASK_BUFS) * R + d;
+    if (lead2) *slot2 = 0u;
+    if (valid) atomicOr(slot, bit);
+    __syncwarp();
+    const uint32_t peers = valid ? *slot : 0u;
+    const bool leader = valid && (peers >> lane) == 1u;
+    uint32_t after = 0;
+    if (leader) after = atomicAdd(&my[d], __popc(peers)) + __popc(peers);
+    after = __shfl_sync(kFullMask, after, (31 - __clz(peers)) & 31);
+    const uint32_t pos = after - __popc(peers & ge);
+    if (valid) s_keys[pos] = key[i];
+    rank2[i >> 1] = (i & 1) ? (rank2[i >> 1] | (pos << 16)) : pos;
+    slot2 = slot1;
+    lead2 = lead1;
+    slot1 = slot;
+    lead1 = leader;
+  }
+}
+
+// Shared-memory layout of the early-counts round: the usual header and
+// staging area, then a separate peer-mask area.
+template <typename K, typename V, int BITS, int THREADS, int KPT>
+struct EarlyShape {
+  using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
+  static constexpr size_t STAGE = (size_t)S::TILE * S::STAGE_ELEM;
+  static constexpr size_t MASKS = S::HEADER_WORDS * 4 + STAGE;
+  static constexpr size_t SMEM = MASKS + (size_t)S::WARPS * S::MASK_BUFS * S::R * 4;
+};
+
+// One tile of one count-sort round, early-counts form: count, publish the
+// tile's counts, scan, rank straight into the reordered tile, look back,
+// publish the inclusive counts, write out.
+template <typename K, typename V, int BITS, int THREADS, int KPT, bool FULL>
+__device__ __forceinline__ void onesweep_tile_early(const PassParams& p, uint32_t tile, bool first,
+                                                    int64_t tile_base, int tile_n,
+                                                    const K* __restrict__ kin,
+                                                    K* __restrict__ kout, const V* vin, V* vout,
+                                                    const uint32_t* base, uint32_t bound,
+                                                    unsigned char* smem) {
+  using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
+  using E = EarlyShape<K, V, BITS, THREADS, KPT>;
+  constexpr int R = S::R, WARPS = S::WARPS, DPT = S::DPT;
+  constexpr bool HV = S::HV;
+  uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);  // [WARPS][R]
+  uint32_t* s_adj = s_wcnt + WARPS * R;                   // [R]
+  uint32_t* s_misc = s_adj + R;                           // [64]
+  K* s_keys = reinterpret_cast<K*>(smem + S::HEADER_WORDS * 4);
+  V* s_vals = reinterpret_cast<V*>(smem + S::HEADER_WORDS * 4);
+  uint32_t* s_masks = reinterpret_cast<uint32_t*>(smem + E::MASKS);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wofs = warp * 32 * KPT + lane;
+  const bool publish = (int64_t)tile != p.stall_tile;
+
+  K key[KPT];
+  V val[HV ? KPT : 1];
+  tile_load<K, V, KPT, FULL>(kin, vin, tile_base, tile_n, wofs, key, val);
+  tile_count<K, R, KPT, FULL>(key, p.shift, p.mask, tile_n, wofs, s_wcnt + warp * R);
+  __syncthreads();
+  if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 1] = globaltimer();
+
+  // per digit: the tile's count (published now), warp offsets, tile starts
+  uint32_t dcnt[DPT];
+  uint32_t tsum = 0;
+  const bool owner = tid < S::DTHREADS;
+  if (owner) {
+    tsum = tile_digit_counts<R, WARPS, DPT>(s_wcnt, tid, dcnt);
+    if (publish)
+#pragma unroll
+      for (int j = 0; j < DPT; ++j)
+        st_relaxed(&p.status[(size_t)tile * R + tid * DPT + j],
+                   (first ? kFlagInc : kFlagAgg) | dcnt[j]);
+  }
+  uint32_t total;
+  uint32_t run = block_exclusive_scan<THREADS>(tsum, s_misc + 1, total);
+  uint32_t tstart[DPT];
+  if (owner) {
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+      const int d = tid * DPT + j;
+      tstart[j] = run;
+#pragma unroll
+      for (int w = 0; w < WARPS; ++w) s_wcnt[w * R + d] += run;
+      run += dcnt[j];
+    }
+  }
+  __syncthreads();
+  uint32_t rank2[(KPT + 1) / 2];
+  tile_rank_place<K, R, KPT, S::MASK_BUFS, FULL>(key, p.shift, p.mask, tile_n, wofs,
+                                                 s_wcnt + warp * R,
+                                                 s_masks + warp * S::MASK_BUFS * R, s_keys,
+                                                 rank2);
+  if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 2] = globaltimer();
+
+  // look back over earlier tiles, publish the inclusive counts, output offsets
+  uint32_t windows = 0;
+  if (owner) {
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+      const int d = tid * DPT + j;
+      uint32_t excl = 0;
+      if (!first) {
+        excl = lookback_exclusive<R, kLookbackWindow>(p.status, tile, d, p.spin_limit, p.err,
+                                                      windows);
+        if (publish) st_relaxed(&p.status[(size_t)tile * R + d], kFlagInc | (excl + dcnt[j]));
+      }
+      s_adj[d] = base[d] + excl - tstart[j];
+    }
+  }
+  if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 6] = windows;
+  __syncthreads();
+  if (p.trace && tid == 0) {
+    p.trace[(size_t)tile * 8 + 3] = globaltimer();
+    p.trace[(size_t)tile * 8 + 4] = globaltimer();
+  }
+  tile_scatter<K, V, THREADS, KPT, FULL>(s_keys, s_vals, s_adj, val, rank2, p.shift, p.mask,
+                                         tile_n, wofs, kout, vout, bound, p.err);
+  if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 5] = globaltimer();
+}
+
 // One tile of one count-sort round with the decoupled look-back.
 //   tile       row of the look-back arrays (tile id in launch order)
 //   first      the tile opens its range (segment), so it has no predecessor
@@ -504,14 +661,15 @@ __device__ __forceinline__ void onesweep_tile(const PassParams& p, uint32_t tile
   if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 5] = globaltimer();
 }
 
-template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB>
+template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB, bool EARLY>
 __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
   constexpr int R = S::R, WARPS = S::WARPS, TILE = S::TILE;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
   uint32_t* s_misc = s_wcnt + WARPS * R + R;
-  uint32_t* s_stage = reinterpret_cast<uint32_t*>(smem + S::HEADER_WORDS * 4);
+  uint32_t* s_stage = reinterpret_cast<uint32_t*>(
+      smem + (EARLY ? EarlyShape<K, V, BITS, THREADS, KPT>::MASKS : S::HEADER_WORDS * 4));
   const int tid = threadIdx.x;
 
   // Rows of the next pass's look-back array are cleared here, so one memset
@@ -524,8 +682,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
   for (int q = 0; q < p.pass; ++q) src ^= (p.skip[q] == 0);
 
   if (tid == 0) s_misc[0] = atomicAdd(p.counter, 1u);  // tiles in launch order
-  for (int i = tid; i < WARPS * R; i += THREADS) s_wcnt[i] = 0;
-  for (int i = tid; i < WARPS * S::MASK_BUFS * R; i += THREADS) s_stage[i] = 0;
+  zero_words<THREADS>(s_wcnt, WARPS * R);
+  zero_words<THREADS>(s_stage, WARPS * S::MASK_BUFS * R);
   __syncthreads();
   const uint32_t tile = s_misc[0];
   const int tile_n = (int)min((int64_t)TILE, p.n - (int64_t)tile * TILE);
@@ -546,12 +704,23 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
   const V* vin = static_cast<const V*>(src ? p.vals[1] : p.vals[0]);
   V* vout = static_cast<V*>(src ? p.vals[0] : p.vals[1]);
   const int64_t tile_base = (int64_t)tile * TILE;
-  if (tile_n == TILE)
-    onesweep_tile<K, V, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n, kin, kout,
-                                                  vin, vout, p.base, (uint32_t)p.n, smem);
-  else
-    onesweep_tile<K, V, BITS, THREADS, KPT, false>(p, tile, tile == 0, tile_base, tile_n, kin,
-                                                   kout, vin, vout, p.base, (uint32_t)p.n, smem);
+  if constexpr (EARLY) {
+    if (tile_n == TILE)
+      onesweep_tile_early<K, V, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n,
+                                                          kin, kout, vin, vout, p.base,
+                                                          (uint32_t)p.n, smem);
+    else
+      onesweep_tile_early<K, V, BITS, THREADS, KPT, false>(p, tile, tile == 0, tile_base,
+                                                           tile_n, kin, kout, vin, vout, p.base,
+                                                           (uint32_t)p.n, smem);
+  } else {
+    if (tile_n == TILE)
+      onesweep_tile<K, V, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n, kin,
+                                                    kout, vin, vout, p.base, (uint32_t)p.n, smem);
+    else
+      onesweep_tile<K, V, BITS, THREADS, KPT, false>(p, tile, tile == 0, tile_base, tile_n, kin,
+                                                     kout, vin, vout, p.base, (uint32_t)p.n, smem);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -924,7 +1093,8 @@ __global__ void k_copy_back(const uint32_t* __restrict__ skip, int passes, K* ke
 // Host launcher for one whole sort with a given kernel shape. CL = 1: one tile
 // per CTA with a per-tile look-back (k_onesweep); CL > 1: CL-CTA cluster
 // super-tiles (k_onesweep_cl).
-template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB, int CL, bool TMA>
+template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB, int CL, bool TMA,
+          bool EARLY>
 cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
   using L = DigitLayout<K, BITS>;
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
@@ -965,8 +1135,8 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
   pp.spin_limit = a.spin_limit;
   pp.prefetch_tiles = a.prefetch_tiles;
   if constexpr (CL == 1) {
-    size_t smem = S::SMEM;
-    auto kern = k_onesweep<K, V, BITS, THREADS, KPT, MINB>;
+    size_t smem = EARLY ? EarlyShape<K, V, BITS, THREADS, KPT>::SMEM : S::SMEM;
+    auto kern = k_onesweep<K, V, BITS, THREADS, KPT, MINB, EARLY>;
     if constexpr (TMA) {
       static_assert(!HasVal<V>::value, "the TMA round is keys-only");
       kern = k_onesweep_tma<K, BITS, THREADS, KPT, MINB>;
@@ -1036,7 +1206,7 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
 // MINB = CTAs that must fit on one SM (caps registers at 65536 / (THREADS * MINB)).
 // CL = CTAs per cluster super-tile (1: plain per-tile look-back).
 template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB, int CL = 1,
-          bool TMA = false>
+          bool TMA = false, bool EARLY = false>
 constexpr LsdEntry lsd_entry() {
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
   return LsdEntry{(int)(8 * sizeof(K)),
@@ -1049,7 +1219,7 @@ constexpr LsdEntry lsd_entry() {
                   DigitLayout<K, BITS>::PASSES,
                   (size_t)S::R,
                   2,
-                  &lsd_launch<K, V, BITS, THREADS, KPT, MINB, CL, TMA>,
+                  &lsd_launch<K, V, BITS, THREADS, KPT, MINB, CL, TMA, EARLY>,
                   CL};
 }
 

@@ -250,12 +250,13 @@ struct SegPassParams {
 template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp) {
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
+  using E = EarlyShape<K, V, BITS, THREADS, KPT>;
   constexpr int R = S::R, WARPS = S::WARPS, TILE = S::TILE;
   const PassParams& p = sp.p;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
   uint32_t* s_misc = s_wcnt + WARPS * R + R;
-  uint32_t* s_stage = reinterpret_cast<uint32_t*>(smem + S::HEADER_WORDS * 4);
+  uint32_t* s_stage = reinterpret_cast<uint32_t*>(smem + E::MASKS);  // the peer masks
   const int tid = threadIdx.x;
   if (p.status_next)
     for (int d = tid; d < R; d += THREADS) p.status_next[(size_t)blockIdx.x * R + d] = 0;
@@ -279,11 +280,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp
   if constexpr (HasVal<V>::value) vout += start;
   const uint32_t* base = sp.seg_base + ((size_t)slot * sp.passes + p.pass) * R;
   if (tile_n == TILE)
-    onesweep_tile<K, V, BITS, THREADS, KPT, true>(p, tile, lt == 0, tile_base, tile_n, kin, kout,
-                                                  vin, vout, base, (uint32_t)len, smem);
+    onesweep_tile_early<K, V, BITS, THREADS, KPT, true>(p, tile, lt == 0, tile_base, tile_n, kin,
+                                                        kout, vin, vout, base, (uint32_t)len,
+                                                        smem);
   else
-    onesweep_tile<K, V, BITS, THREADS, KPT, false>(p, tile, lt == 0, tile_base, tile_n, kin,
-                                                   kout, vin, vout, base, (uint32_t)len, smem);
+    onesweep_tile_early<K, V, BITS, THREADS, KPT, false>(p, tile, lt == 0, tile_base, tile_n,
+                                                         kin, kout, vin, vout, base,
+                                                         (uint32_t)len, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -346,9 +349,10 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
   timer_end(a.timer, st);
 
   auto kern = k_seg_onesweep<K, V, 8, THREADS, KPT, MINB>;
-  if (OS::SMEM > 48 * 1024) {
+  constexpr size_t SEG_SMEM = EarlyShape<K, V, 8, THREADS, KPT>::SMEM;
+  if (SEG_SMEM > 48 * 1024) {
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)OS::SMEM)))
+                                  (int)SEG_SMEM)))
       return e;
   }
   SegPassParams sp;
@@ -382,7 +386,7 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
     pp.status_next = (q + 1 < P) ? a.status[(q + 1) & 1] : nullptr;
     pp.counter = a.cnt + kCntPassTiles + q;
     timer_begin(a.timer, "k_seg_onesweep", st);
-    kern<<<(unsigned)a.max_tiles, THREADS, OS::SMEM, st>>>(sp);
+    kern<<<(unsigned)a.max_tiles, THREADS, SEG_SMEM, st>>>(sp);
     timer_end(a.timer, st);
   }
   return cudaGetLastError();

@@ -5,9 +5,9 @@ namespace isort {
 
 // <K, V, warp M, mid M, CTA M, radix threads, keys per thread, min CTAs per SM>
 static const SegConfig kSeg32[] = {
-    seg_config<uint32_t, NoVal, 4, 8, 16, 512, 24, 2>(),
-    seg_config<uint32_t, uint32_t, 4, 8, 16, 256, 12, 3>(),
-    seg_config<uint32_t, uint64_t, 4, 8, 16, 256, 12, 2>(),
+    seg_config<uint32_t, NoVal, 4, 8, 16, 384, 32, 2>(),
+    seg_config<uint32_t, uint32_t, 4, 8, 16, 384, 16, 2>(),
+    seg_config<uint32_t, uint64_t, 4, 8, 16, 256, 16, 2>(),
 };
 
 const SegConfig* seg_config_k32(int val_bits) {
