@@ -17,9 +17,11 @@ distributions via --dist.
 from __future__ import annotations
 
 import argparse
+import atexit
 import hashlib
 import json
 import os
+import shutil
 import statistics
 import subprocess
 import sys
@@ -35,6 +37,8 @@ WORKLOADS = {
     # name: (n, key_bits, val_bits, radix_bits, description)
     "u32_2p28_r256": (1 << 28, 32, 0, 8, "plain sort, 2^28 uint32 keys, radix 256 (4 passes)"),
     "u32_2p28_r65536": (1 << 28, 32, 0, 16, "plain sort, 2^28 uint32 keys, radix 65536 (2 passes)"),
+    "u32_2p28_r2048": (1 << 28, 32, 0, 11, "plain sort, 2^28 uint32 keys, radix 2048 (3 passes: "
+                                           "11, 11, 10 bits)"),
     "pairs_2p27": (1 << 27, 32, 32, 8, "stable pairs, 2^27 uint32 keys + uint32 index payloads"),
     "u64_2p26": (1 << 26, 64, 0, 8, "plain sort, 2^26 uint64 keys, radix 256 (8 passes)"),
     "u32_128M_paper": (131_072_000, 32, 0, 8, "the paper's 128M (1M = 1,024,000) uint32 keys"),
@@ -45,7 +49,7 @@ WORKLOADS = {
                                     "log-uniform in [2^10, 2^24] uint32 keys, half with "
                                     "uint32 payloads, 40 GB admission budget"),
 }
-ALIASES = {"r16": "u32_2p28_r65536", "pairs": "pairs_2p27", "u64": "u64_2p26",
+ALIASES = {"r16": "u32_2p28_r65536", "r11": "u32_2p28_r2048", "pairs": "pairs_2p27", "u64": "u64_2p26",
            "paper128m": "u32_128M_paper", "default": "u32_2p28_r256",
            "segmented": "segmented_20000", "serve": "serve_poisson"}
 
@@ -116,44 +120,68 @@ class Replicas:
 
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    """nvidia-smi clock/throttle samples every 20 ms. start() before the warm-up
+    (nvidia-smi takes a while to come up), window(t0, t1) with the timed
+    region's host clock, stop() summarises the samples that arrived inside the
+    window (plus one sampling period); if none did, all samples since start."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 20
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []  # (host arrival time, csv line)
+        self.t0 = self.t1 = None
 
-    def start(self):
+    def start(self, wait_s: float = 3.0):
+        cmd = ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+               "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)]
+        if shutil.which("stdbuf"):
+            cmd = ["stdbuf", "-oL"] + cmd  # one line per sample through the pipe
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (OSError, ValueError):
             self.proc = None
+            return
+        atexit.register(self._end)  # no sampler outlives the process, even on an error
+        t_end = time.perf_counter() + wait_s
+        while not self.lines and time.perf_counter() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def _end(self):
+        if self.proc and self.proc.poll() is None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def window(self, t0: float, t1: float):
+        self.t0, self.t1 = t0, t1
 
     def stop(self):
         if not self.proc:
             return None
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
+        if self.t1 is not None:  # let the samples of the window's end arrive
+            time.sleep(max(0.0, self.t1 + 2 * self.PERIOD_MS / 1000 - time.perf_counter()))
+        self._end()
         self.t.join(timeout=2)
+        inside = [ln for t, ln in self.lines
+                  if self.t0 is not None and self.t0 <= t <= self.t1 + self.PERIOD_MS / 1000]
+        use = inside or [ln for _, ln in self.lines]
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in use:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -168,7 +196,8 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "samples_in_timed_region": len(inside),
+                "period_ms": self.PERIOD_MS}
 
 
 # --------------------------------------------------------------------------- helpers
@@ -347,6 +376,8 @@ def run_ours(a):
     if rb == 8:
         variant = isort.tune_variants(kb, vb, rb)[0]
 
+    clocks = ClockSampler(local)
+    clocks.start()  # streaming before the timed region begins
     # warm-up (also allocates the workspace)
     for _ in range(a.warmup):
         restore()
@@ -356,14 +387,12 @@ def run_ours(a):
         raise RuntimeError("device error during warm-up")
 
     isort.debug_set(_lib.DEBUG_KERNEL_TIMING, 1)
-    clocks = ClockSampler(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(a.steps)]
     kernel_ms = {}
     kernel_launches = 0
     rep.barrier()
     torch.cuda.synchronize()
-    clocks.start()
     t_wall0 = time.perf_counter()
     for i in range(a.steps):
         restore()
@@ -375,6 +404,7 @@ def run_ours(a):
             kernel_launches += 1
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
+    clocks.window(t_wall0, t_wall0 + t_wall)
     clk = clocks.stop()
     rep.barrier()
     isort.debug_set(_lib.DEBUG_KERNEL_TIMING, 0)
@@ -391,12 +421,12 @@ def run_ours(a):
         raise RuntimeError("benchmark result is not sorted")
     del sk
 
-    # dominant kernel: the onesweep pass (radix 256) or the radix-65536 scatter
+    # dominant kernel: the onesweep pass (radix 256) or the wide-radix scatter
     dom = max(kernel_ms, key=lambda k: sum(kernel_ms[k]))
     dom_ms = statistics.mean(kernel_ms[dom])
     bytes_per_key = (kb + vb) // 8
     passes = -(-kb // rb)
-    if dom in ("k_onesweep", "k_scatter16"):
+    if dom in ("k_onesweep", "k_scatter16", "k_scatter11"):
         # one count-sort round: read and write every key (and payload) once
         alg_bytes = 2 * n * bytes_per_key
     else:
@@ -530,6 +560,8 @@ def run_ours_segmented(a):
         keys.copy_(pristine)
         flush.sum()
 
+    clocks = ClockSampler(local)
+    clocks.start()  # streaming before the timed region begins
     for _ in range(a.warmup):
         restore()
         isort.sort_segmented(keys, d_off)
@@ -542,10 +574,9 @@ def run_ours_segmented(a):
           for _ in range(a.steps)]
     kernel_ms = {}
     launches = 0
-    clocks = ClockSampler(local)
     rep.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    t_wall0 = time.perf_counter()
     for i in range(a.steps):
         restore()
         ev[i][0].record(stream)
@@ -555,6 +586,7 @@ def run_ours_segmented(a):
             kernel_ms.setdefault(name, []).append(ms)
             launches += 1
     torch.cuda.synchronize()
+    clocks.window(t_wall0, time.perf_counter())
     clk = clocks.stop()
     rep.barrier()
     isort.debug_set(_lib.DEBUG_KERNEL_TIMING, 0)

@@ -29,8 +29,11 @@
  *    (val_bits 32|64). n <= 2^30 (the look-back status word packs a 30-bit
  *    count); larger n returns ISORT_EUNSUPPORTED.
  *  - radix_bits: 0 = automatic (8), 8 = radix 256 (SR4/PR4), 16 = radix 65536
- *    (PR2). Passes = ceil(key_bits / radix_bits). A pass whose digit is the same
- *    for every key is skipped (it is the identity permutation).
+ *    (PR2), 11 = radix 2048 (between the two; not one of the paper's
+ *    configurations). Passes = ceil(key_bits / radix_bits); when radix_bits does
+ *    not divide key_bits the last digit is narrower (11, 11, 10 bits for 32-bit
+ *    keys at radix_bits 11). A pass whose digit is the same for every key is
+ *    skipped (it is the identity permutation).
  */
 #ifndef ISORT_H
 #define ISORT_H

@@ -1,6 +1,6 @@
 // C-ABI of the isort library: argument checks, per-stream workspaces, kernel
 // family selection. Every step of a sort runs in the kernels of sort_k32.cu,
-// sort_k64.cu, radix16.cu and segmented.cu; this file only validates, carves
+// sort_k64.cu, radix_wide.cu and segmented.cu; this file only validates, carves
 // scratch memory and enqueues.
 #include <cstdio>
 #include <cstdlib>
@@ -53,7 +53,7 @@ int num_sms() {
 }
 
 int variants(int key_bits, int val_bits, int radix_bits, const LsdEntry** out) {
-  if (radix_bits == 16) return r16_variants(key_bits, val_bits, out);
+  if (radix_bits == 16 || radix_bits == 11) return wide_variants(key_bits, val_bits, radix_bits, out);
   if (key_bits == 32) return lsd_variants_k32(val_bits, radix_bits, out);
   if (key_bits == 64) return lsd_variants_k64(val_bits, radix_bits, out);
   return 0;
@@ -175,7 +175,7 @@ isort_status check_widths(int key_bits, int val_bits, bool pairs) {
 
 isort_status resolve_radix(int radix_bits, int* out) {
   if (radix_bits == 0) radix_bits = 8;
-  if (radix_bits != 8 && radix_bits != 16) {
+  if (radix_bits != 8 && radix_bits != 11 && radix_bits != 16) {
     if (radix_bits > 0 && radix_bits <= 24) return ISORT_EUNSUPPORTED;
     return ISORT_EINVAL;
   }

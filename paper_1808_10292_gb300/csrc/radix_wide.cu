@@ -1,28 +1,35 @@
-// Radix-65536 passes (the paper's PR2: 16-bit digits, two rounds on 32-bit keys).
+// Wide-radix passes: radix 65536 (the paper's PR2: 16-bit digits, two rounds
+// on 32-bit keys) and radix 2048 (11-bit digits: three rounds of 11, 11 and 10
+// bits on 32-bit keys, six on 64-bit keys).
 //
 // Paper mapping (Section "SR4, PR2, PR4, BTN and OET under MBSP", Eqs. Tp,
 // Tp2): each worker counts the digits of its share of the keys, the p x r count
 // matrix is exchanged (the 2prg term, which grows with r and is why the paper
 // found PR2 slower than PR4), and every worker routes its keys to their global
 // positions. With r = 65536 a per-tile decoupled look-back would need 256 KiB
-// of status per tile, so each round here is the paper's count-sort literally:
-// the input is read twice (count, then place) and written once.
+// of status per tile (8 KiB at r = 2048, still a quarter of a tile's keys), so
+// each round here is the paper's count-sort literally: the input is read twice
+// (count, then place) and written once. A "block" is one row of the count
+// matrix: 2^19 keys at r = 65536, 2^16 keys at r = 2048.
 //
-//   k_count16    per block of kBlockKeys keys, the 65536-bin digit histogram.
-//                A 2-CTA thread-block cluster holds it in distributed shared
-//                memory: CTA r owns bins [r*32768, (r+1)*32768) as 32-bit
-//                counters (128 KiB) and each CTA reads half of the block,
-//                adding into the owner's shared memory (local or remote).
-//   k_colscan16  per digit, the exclusive prefix over blocks (the count
-//                matrix exchange) and the digit totals.
-//   k_digscan16  exclusive prefix over the 65536 digit totals -> global bases;
-//                flags a pass whose digit is constant.
-//   k_scatter16  per block, in input order, sub-tiles of kSubKeys keys are
-//                sorted stably by the 16-bit digit in shared memory (two
-//                stable 8-bit partitions), then each key goes to
-//                base[d] + (earlier blocks' d-keys) + (this block's d-keys so
-//                far) + (its rank in the sub-tile's run of d). The per-block
-//                running offsets live in the block's column of the matrix.
+//   k_count16      (r = 65536) per block, the 65536-bin digit histogram. A
+//                  2-CTA thread-block cluster holds it in distributed shared
+//                  memory: CTA r owns bins [r*32768, (r+1)*32768) as 32-bit
+//                  counters (128 KiB) and each CTA reads half of the block,
+//                  adding into the owner's shared memory (local or remote).
+//   k_count_smem   (r = 2048) per block, the histogram in one CTA's shared
+//                  memory, eight copies of the bins to spread contention.
+//   k_colscan      per digit, the exclusive prefix over blocks (the count
+//                  matrix exchange), in place, and the digit totals.
+//   k_digscan      exclusive prefix over the digit totals -> global bases;
+//                  flags a pass whose digit is constant.
+//   k_scatter_wide per block, in input order, sub-tiles of kSubKeys keys are
+//                  sorted stably by the digit in shared memory (a stable
+//                  partition by its low 8 bits, then by the rest), then each
+//                  key goes to base[d] + (earlier blocks' d-keys) + (this
+//                  block's d-keys so far) + (its rank in the sub-tile's run of
+//                  d). The per-block running offsets live in the block's row
+//                  of the matrix.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -37,7 +44,22 @@ namespace {
 
 constexpr int kR16 = 65536;
 constexpr int kHalfBins = kR16 / 2;
-constexpr int64_t kBlockKeys = int64_t(1) << 19;  // keys per count-matrix row
+
+// Keys per count-matrix row (block) and kernel names, per digit width.
+template <int BITS>
+struct Wide;
+template <>
+struct Wide<16> {
+  static constexpr int64_t BLOCK_KEYS = int64_t(1) << 19;
+  static constexpr const char* COUNT = "k_count16";
+  static constexpr const char* SCATTER = "k_scatter16";
+};
+template <>
+struct Wide<11> {
+  static constexpr int64_t BLOCK_KEYS = int64_t(1) << 16;
+  static constexpr const char* COUNT = "k_count11";
+  static constexpr const char* SCATTER = "k_scatter11";
+};
 constexpr int kCountThreads = 1024;
 constexpr int kScatterThreads = 256;
 constexpr int kScatterKpt = 16;
@@ -54,6 +76,11 @@ constexpr uint32_t kNoDigit = 0x10000u;  // differs from every 16-bit digit
 template <typename K>
 __device__ __forceinline__ uint32_t digit16(K k, int shift) {
   return static_cast<uint32_t>(k >> shift) & 0xffffu;
+}
+
+template <typename K>
+__device__ __forceinline__ uint32_t digit_w(K k, int shift, uint32_t mask) {
+  return static_cast<uint32_t>(k >> shift) & mask;
 }
 
 __device__ __forceinline__ int input_parity(const uint32_t* skip, int pass) {
@@ -76,8 +103,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kCountThreads)
 
   const K* keys = input_parity(skip, pass) ? buf1 : buf0;
   const int64_t block = blockIdx.x / 2;
-  const int64_t lo = block * kBlockKeys;
-  const int64_t hi = min(n, lo + kBlockKeys);
+  const int64_t lo = block * Wide<16>::BLOCK_KEYS;
+  const int64_t hi = min(n, lo + Wide<16>::BLOCK_KEYS);
   const int64_t len = hi - lo;
   const int64_t half = (len + 1) / 2;
   const int64_t my_lo = lo + (rank ? half : 0);
@@ -94,36 +121,85 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kCountThreads)
   for (int i = threadIdx.x; i < kHalfBins; i += kCountThreads) row[i] = s_bins[i];
 }
 
-// Per digit: exclusive prefix over the blocks (in place) and the total.
-__global__ void __launch_bounds__(256) k_colscan16(uint32_t* counts, int64_t nblocks,
-                                                   uint32_t* total) {
-  const int d = blockIdx.x * 256 + threadIdx.x;
+// Per block of Wide<11>::BLOCK_KEYS keys, the R-bin digit histogram in shared
+// memory (R <= 4096): warp w adds into copy w % 8 of the bins, so equal digits
+// from different warps rarely meet on one counter; the copies are summed into
+// the block's row of the count matrix.
+template <typename K, int R>
+__global__ void __launch_bounds__(kCountThreads)
+    k_count_smem(const K* buf0, const K* buf1, const uint32_t* skip, int pass, int64_t n,
+                 int shift, uint32_t mask, uint32_t* counts) {
+  constexpr int COPIES = 8;
+  extern __shared__ __align__(16) uint32_t s_bins[];  // [COPIES][R]
+  for (int i = threadIdx.x; i < COPIES * R; i += kCountThreads) s_bins[i] = 0;
+  __syncthreads();
+  const K* keys = input_parity(skip, pass) ? buf1 : buf0;
+  const int64_t lo = (int64_t)blockIdx.x * Wide<11>::BLOCK_KEYS;
+  const int64_t hi = min(n, lo + Wide<11>::BLOCK_KEYS);
+  uint32_t* my = s_bins + ((threadIdx.x >> 5) % COPIES) * R;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += kCountThreads)
+    atomicAdd(&my[digit_w(keys[i], shift, mask)], 1u);
+  __syncthreads();
+  uint32_t* row = counts + (size_t)blockIdx.x * R;
+  for (int d = threadIdx.x; d < R; d += kCountThreads) {
+    uint32_t sum = 0;
+#pragma unroll
+    for (int c = 0; c < COPIES; ++c) sum += s_bins[c * R + d];
+    row[d] = sum;
+  }
+}
+
+// Per digit: exclusive prefix over the blocks (in place) and the total. One
+// CTA per 32 digits: lane = digit, warp w takes a contiguous slice of the
+// blocks (coalesced 128-byte rows), the 32 slice sums are scanned in shared
+// memory, and a second sweep writes the prefixes.
+template <int R>
+__global__ void __launch_bounds__(1024) k_colscan(uint32_t* counts, int64_t nblocks,
+                                                  uint32_t* total) {
+  __shared__ uint32_t s_sum[32][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int d = blockIdx.x * 32 + lane;
+  const int64_t per = (nblocks + 31) / 32;
+  const int64_t b0 = min(nblocks, warp * per), b1 = min(nblocks, b0 + per);
   uint32_t sum = 0;
-  int64_t b = 0;
-  for (; b + 4 <= nblocks; b += 4) {
+  int64_t b = b0;
+  for (; b + 4 <= b1; b += 4) {
     uint32_t c[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) c[u] = counts[(size_t)(b + u) * kR16 + d];
+    for (int u = 0; u < 4; ++u) c[u] = counts[(size_t)(b + u) * R + d];
+    sum += c[0] + c[1] + c[2] + c[3];
+  }
+  for (; b < b1; ++b) sum += counts[(size_t)b * R + d];
+  s_sum[warp][lane] = sum;
+  __syncthreads();
+  uint32_t run = 0;  // blocks before this warp's slice
+  for (int w = 0; w < warp; ++w) run += s_sum[w][lane];
+  if (warp == 31) total[d] = run + sum;
+  for (b = b0; b + 4 <= b1; b += 4) {
+    uint32_t c[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) c[u] = counts[(size_t)(b + u) * R + d];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      counts[(size_t)(b + u) * kR16 + d] = sum;
-      sum += c[u];
+      counts[(size_t)(b + u) * R + d] = run;
+      run += c[u];
     }
   }
-  for (; b < nblocks; ++b) {
-    const uint32_t c = counts[(size_t)b * kR16 + d];
-    counts[(size_t)b * kR16 + d] = sum;
-    sum += c;
+  for (; b < b1; ++b) {
+    const uint32_t c = counts[(size_t)b * R + d];
+    counts[(size_t)b * R + d] = run;
+    run += c;
   }
-  total[d] = sum;
 }
 
 // One CTA: base[d] = sum of totals below d; skip[pass] = (one digit holds all n).
-__global__ void __launch_bounds__(1024) k_digscan16(const uint32_t* total, uint32_t* base,
-                                                    uint32_t* skip, int pass, int64_t n) {
+template <int R>
+__global__ void __launch_bounds__(1024) k_digscan(const uint32_t* total, uint32_t* base,
+                                                  uint32_t* skip, int pass, int64_t n) {
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_trivial;
-  constexpr int PER = kR16 / 1024;
+  constexpr int PER = R / 1024;
+  static_assert(PER >= 1 && R % 1024 == 0, "at least one digit per thread");
   const int d0 = threadIdx.x * PER;
   if (threadIdx.x == 0) s_trivial = 0;
   uint32_t local = 0;
@@ -145,7 +221,7 @@ __global__ void __launch_bounds__(1024) k_digscan16(const uint32_t* total, uint3
 }
 
 // ---------------------------------------------------------------------------
-// Shared memory of k_scatter16.
+// Shared memory of k_scatter_wide.
 template <typename K, typename V>
 struct Scatter16Smem {
   static constexpr bool HV = HasVal<V>::value;
@@ -221,11 +297,17 @@ __device__ __forceinline__ void partition8(int n_sub, uint32_t* wcnt, uint32_t (
   for (int i = 0; i < kScatterKpt; ++i) pos[i] += wcnt[warp * 256 + digit(i)];
 }
 
-template <typename K, typename V, bool FULL>
-__device__ __forceinline__ void scatter16_subtile(Scatter16Smem<K, V>& sm, const K* kin, K* kout,
-                                                  const V* vin, V* vout, int64_t sub_base,
-                                                  int n_sub, int shift, uint32_t* col,
-                                                  const uint32_t* base, int64_t n, uint32_t* err) {
+// width = the pass's digit width (9..16 bits): the first partition takes its
+// low 8 bits, the second the remaining width - 8. col[d] = the block's running
+// offset of digit d; with COMBINED it already includes the global base[d]
+// (and base is not read).
+template <typename K, typename V, bool FULL, bool COMBINED>
+__device__ __forceinline__ void scatter_subtile(Scatter16Smem<K, V>& sm, const K* kin, K* kout,
+                                                const V* vin, V* vout, int64_t sub_base,
+                                                int n_sub, int shift, int width, uint32_t* col,
+                                                const uint32_t* base, int64_t n, uint32_t* err) {
+  const uint32_t wmask = (1u << width) - 1u;
+  const uint32_t hmask = (1u << (width - 8)) - 1u;
   constexpr bool HV = HasVal<V>::value;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wofs = warp * 32 * kScatterKpt + lane;
@@ -249,7 +331,7 @@ __device__ __forceinline__ void scatter16_subtile(Scatter16Smem<K, V>& sm, const
       sm.idx_a[pos[i]] = (uint16_t)(wofs + i * 32);
     }
   __syncthreads();
-  // then stably by the high byte: the sub-tile ends up ordered by the 16-bit digit
+  // then stably by the high bits: the sub-tile ends up ordered by the digit
   uint32_t idx[kScatterKpt];
 #pragma unroll
   for (int i = 0; i < kScatterKpt; ++i) {
@@ -257,7 +339,7 @@ __device__ __forceinline__ void scatter16_subtile(Scatter16Smem<K, V>& sm, const
     idx[i] = (FULL || wofs + i * 32 < n_sub) ? sm.idx_a[wofs + i * 32] : 0u;
   }
   partition8<FULL>(n_sub, &sm.wcnt[0][0], sm.masks[0], sm.warp_tot,
-                   [&](int i) { return static_cast<uint32_t>(key[i] >> (shift + 8)) & 0xffu; },
+                   [&](int i) { return static_cast<uint32_t>(key[i] >> (shift + 8)) & hmask; },
                    pos);
 #pragma unroll
   for (int i = 0; i < kScatterKpt; ++i)
@@ -280,12 +362,13 @@ __device__ __forceinline__ void scatter16_subtile(Scatter16Smem<K, V>& sm, const
     const bool valid = FULL || j < n_sub;
     kk[k] = valid ? sm.keys_b[padj(j)] : K(0);
     ix[k] = valid ? sm.idx_b[padj(j)] : 0u;
-    dg[k] = valid ? digit16(kk[k], shift) : kNoDigit;
+    dg[k] = valid ? digit_w(kk[k], shift, wmask) : kNoDigit;
   }
-  const uint32_t prev = j0 > 0 && (FULL || j0 - 1 < n_sub) ? digit16(sm.keys_b[padj(j0 - 1)], shift)
-                                                           : kNoDigit;
+  const uint32_t prev = j0 > 0 && (FULL || j0 - 1 < n_sub)
+                            ? digit_w(sm.keys_b[padj(j0 - 1)], shift, wmask)
+                            : kNoDigit;
   const uint32_t next = (FULL ? j0 + kScatterKpt < kSubKeys : j0 + kScatterKpt < n_sub)
-                            ? digit16(sm.keys_b[padj(j0 + kScatterKpt)], shift)
+                            ? digit_w(sm.keys_b[padj(j0 + kScatterKpt)], shift, wmask)
                             : kNoDigit;
   uint32_t starts = 0, ends = 0;  // bit k: position j0+k starts / ends a run
 #pragma unroll
@@ -317,7 +400,8 @@ __device__ __forceinline__ void scatter16_subtile(Scatter16Smem<K, V>& sm, const
 #pragma unroll
   for (int k = 0; k < kScatterKpt; ++k) {
     if ((starts >> k) & 1u) cur = j0 + k;
-    if (FULL || j0 + k < n_sub) gpos[k] = col[dg[k]] + base[dg[k]] + (uint32_t)(j0 + k - cur);
+    if (FULL || j0 + k < n_sub)
+      gpos[k] = col[dg[k]] + (COMBINED ? 0u : base[dg[k]]) + (uint32_t)(j0 + k - cur);
   }
   __syncthreads();  // every read of col[] precedes the updates below
   const uint32_t n32 = (uint32_t)n;
@@ -340,13 +424,11 @@ __device__ __forceinline__ void scatter16_subtile(Scatter16Smem<K, V>& sm, const
   __syncthreads();  // column updates visible to the next sub-tile; smem reusable
 }
 
-template <typename K, typename V>
-__global__ void __launch_bounds__(kScatterThreads) k_scatter16(K* kbuf0, K* kbuf1, V* vbuf0,
-                                                               V* vbuf1, const uint32_t* skip,
-                                                               int pass, int64_t n, int shift,
-                                                               uint32_t* counts,
-                                                               const uint32_t* base,
-                                                               uint32_t* err) {
+template <typename K, typename V, int BITS>
+__global__ void __launch_bounds__(kScatterThreads, 2)
+    k_scatter_wide(K* kbuf0, K* kbuf1, V* vbuf0, V* vbuf1, const uint32_t* skip, int pass,
+                   int64_t n, int shift, int width, uint32_t* counts, const uint32_t* base,
+                   uint32_t* err) {
   if (skip[pass]) return;  // the digit is constant: this round is the identity
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Scatter16Smem<K, V>& sm = *reinterpret_cast<Scatter16Smem<K, V>*>(smem_raw);
@@ -355,17 +437,36 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter16(K* kbuf0, K* kbuf
   K* kout = src ? kbuf0 : kbuf1;
   const V* vin = src ? vbuf1 : vbuf0;
   V* vout = src ? vbuf0 : vbuf1;
+  constexpr int R = 1 << BITS;
   const int64_t block = blockIdx.x;
-  const int64_t lo = block * kBlockKeys;
-  const int64_t hi = min(n, lo + kBlockKeys);
-  uint32_t* col = counts + (size_t)block * kR16;
-  for (int64_t sb = lo; sb < hi; sb += kSubKeys) {
-    const int n_sub = (int)min((int64_t)kSubKeys, hi - sb);
-    if (n_sub == kSubKeys)
-      scatter16_subtile<K, V, true>(sm, kin, kout, vin, vout, sb, n_sub, shift, col, base, n, err);
-    else
-      scatter16_subtile<K, V, false>(sm, kin, kout, vin, vout, sb, n_sub, shift, col, base, n,
-                                     err);
+  const int64_t lo = block * Wide<BITS>::BLOCK_KEYS;
+  const int64_t hi = min(n, lo + Wide<BITS>::BLOCK_KEYS);
+  uint32_t* col = counts + (size_t)block * R;
+  if constexpr (R <= 4096) {
+    // the block's running output positions (row offset + global base) fit in
+    // shared memory: one read of the row, no global traffic per key or run
+    uint32_t* s_pos = reinterpret_cast<uint32_t*>(smem_raw + sizeof(Scatter16Smem<K, V>));
+    for (int d = threadIdx.x; d < R; d += kScatterThreads) s_pos[d] = col[d] + base[d];
+    __syncthreads();
+    for (int64_t sb = lo; sb < hi; sb += kSubKeys) {
+      const int n_sub = (int)min((int64_t)kSubKeys, hi - sb);
+      if (n_sub == kSubKeys)
+        scatter_subtile<K, V, true, true>(sm, kin, kout, vin, vout, sb, n_sub, shift, width,
+                                          s_pos, nullptr, n, err);
+      else
+        scatter_subtile<K, V, false, true>(sm, kin, kout, vin, vout, sb, n_sub, shift, width,
+                                           s_pos, nullptr, n, err);
+    }
+  } else {
+    for (int64_t sb = lo; sb < hi; sb += kSubKeys) {
+      const int n_sub = (int)min((int64_t)kSubKeys, hi - sb);
+      if (n_sub == kSubKeys)
+        scatter_subtile<K, V, true, false>(sm, kin, kout, vin, vout, sb, n_sub, shift, width, col,
+                                           base, n, err);
+      else
+        scatter_subtile<K, V, false, false>(sm, kin, kout, vin, vout, sb, n_sub, shift, width,
+                                            col, base, n, err);
+    }
   }
 }
 
@@ -384,39 +485,54 @@ __global__ void k_copy_back16(const uint32_t* __restrict__ skip, int passes, K* 
 
 }  // namespace
 
-template <typename K, typename V>
-cudaError_t r16_launch(const LsdArgs& a, cudaStream_t st) {
-  constexpr int P = (8 * sizeof(K)) / 16;
-  const int64_t nblocks = (a.n + kBlockKeys - 1) / kBlockKeys;
+template <typename K, typename V, int BITS>
+cudaError_t wide_launch(const LsdArgs& a, cudaStream_t st) {
+  constexpr int KB = 8 * (int)sizeof(K);
+  constexpr int R = 1 << BITS;
+  constexpr int P = (KB + BITS - 1) / BITS;
+  constexpr int64_t BK = Wide<BITS>::BLOCK_KEYS;
+  const int64_t nblocks = (a.n + BK - 1) / BK;
   uint32_t* counts = a.status[0];  // the count matrix lives in the status area
-  uint32_t* total = a.hist;        // [65536]
-  uint32_t* base = a.base;         // [65536] (one pass at a time)
+  uint32_t* total = a.hist;        // [R]
+  uint32_t* base = a.base;         // [R] (one pass at a time)
   cudaError_t e;
-  const size_t count_smem = sizeof(uint32_t) * kHalfBins;
-  if ((e = cudaFuncSetAttribute(k_count16<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)count_smem)))
-    return e;
-  const size_t sc_smem = sizeof(Scatter16Smem<K, V>);
-  if ((e = cudaFuncSetAttribute(k_scatter16<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sc_smem)))
+  const size_t count_smem = BITS == 16 ? sizeof(uint32_t) * kHalfBins : sizeof(uint32_t) * 8 * R;
+  if constexpr (BITS == 16) {
+    if ((e = cudaFuncSetAttribute(k_count16<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)count_smem)))
+      return e;
+  } else {
+    if ((e = cudaFuncSetAttribute(k_count_smem<K, R>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)count_smem)))
+      return e;
+  }
+  const size_t sc_smem = sizeof(Scatter16Smem<K, V>) + (R <= 4096 ? sizeof(uint32_t) * R : 0);
+  if ((e = cudaFuncSetAttribute(k_scatter_wide<K, V, BITS>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc_smem)))
     return e;
   for (int q = 0; q < P; ++q) {
-    const int shift = 16 * q;
-    timer_begin(a.timer, "k_count16", st);
-    k_count16<K><<<(unsigned)(2 * nblocks), kCountThreads, count_smem, st>>>(
-        static_cast<const K*>(a.keys), static_cast<const K*>(a.alt_keys), a.skip, q, a.n, shift,
-        counts);
+    const int shift = BITS * q;
+    const int width = KB - shift < BITS ? KB - shift : BITS;
+    timer_begin(a.timer, Wide<BITS>::COUNT, st);
+    if constexpr (BITS == 16)
+      k_count16<K><<<(unsigned)(2 * nblocks), kCountThreads, count_smem, st>>>(
+          static_cast<const K*>(a.keys), static_cast<const K*>(a.alt_keys), a.skip, q, a.n, shift,
+          counts);
+    else
+      k_count_smem<K, R><<<(unsigned)nblocks, kCountThreads, count_smem, st>>>(
+          static_cast<const K*>(a.keys), static_cast<const K*>(a.alt_keys), a.skip, q, a.n, shift,
+          (1u << width) - 1u, counts);
     timer_end(a.timer, st);
-    timer_begin(a.timer, "k_colscan16", st);
-    k_colscan16<<<kR16 / 256, 256, 0, st>>>(counts, nblocks, total);
+    timer_begin(a.timer, "k_colscan", st);
+    k_colscan<R><<<R / 32, 1024, 0, st>>>(counts, nblocks, total);
     timer_end(a.timer, st);
-    timer_begin(a.timer, "k_digscan16", st);
-    k_digscan16<<<1, 1024, 0, st>>>(total, base, a.skip, q, a.n);
+    timer_begin(a.timer, "k_digscan", st);
+    k_digscan<R><<<1, 1024, 0, st>>>(total, base, a.skip, q, a.n);
     timer_end(a.timer, st);
-    timer_begin(a.timer, "k_scatter16", st);
-    k_scatter16<K, V><<<(unsigned)nblocks, kScatterThreads, sc_smem, st>>>(
+    timer_begin(a.timer, Wide<BITS>::SCATTER, st);
+    k_scatter_wide<K, V, BITS><<<(unsigned)nblocks, kScatterThreads, sc_smem, st>>>(
         static_cast<K*>(a.keys), static_cast<K*>(a.alt_keys), static_cast<V*>(a.vals),
-        static_cast<V*>(a.alt_vals), a.skip, q, a.n, shift, counts, base, a.err);
+        static_cast<V*>(a.alt_vals), a.skip, q, a.n, shift, width, counts, base, a.err);
     timer_end(a.timer, st);
   }
   const int cblocks = (int)std::min<int64_t>((a.n + 255) / 256, (int64_t)a.num_sms * 8);
@@ -429,35 +545,46 @@ cudaError_t r16_launch(const LsdArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename K, typename V>
-constexpr LsdEntry r16_entry() {
-  return LsdEntry{(int)(8 * sizeof(K)),
+template <typename K, typename V, int BITS>
+constexpr LsdEntry wide_entry() {
+  constexpr int KB = 8 * (int)sizeof(K);
+  return LsdEntry{KB,
                   HasVal<V>::value ? (int)(8 * sizeof(V)) : 0,
-                  16,
+                  BITS,
                   kScatterThreads,
                   kScatterKpt,
-                  kBlockKeys,          // "tile" = one count-matrix row
-                  kR16,
-                  (int)(8 * sizeof(K)) / 16,
-                  (size_t)kR16,        // the count matrix: one row per block
-                  1,                   // in one buffer
-                  &r16_launch<K, V>,
+                  Wide<BITS>::BLOCK_KEYS,  // "tile" = one count-matrix row
+                  1 << BITS,
+                  (KB + BITS - 1) / BITS,
+                  (size_t)1 << BITS,       // the count matrix: one row per block
+                  1,                       // in one buffer
+                  &wide_launch<K, V, BITS>,
                   1};
 }
 
-static const LsdEntry kR16None32[] = {r16_entry<uint32_t, NoVal>()};
-static const LsdEntry kR16V32_32[] = {r16_entry<uint32_t, uint32_t>()};
-static const LsdEntry kR16V64_32[] = {r16_entry<uint32_t, uint64_t>()};
-static const LsdEntry kR16None64[] = {r16_entry<uint64_t, NoVal>()};
-static const LsdEntry kR16V32_64[] = {r16_entry<uint64_t, uint32_t>()};
-static const LsdEntry kR16V64_64[] = {r16_entry<uint64_t, uint64_t>()};
+#define ISORT_WIDE_TABLES(B)                                                             \
+  static const LsdEntry kW##B##None32[] = {wide_entry<uint32_t, NoVal, B>()};            \
+  static const LsdEntry kW##B##V32_32[] = {wide_entry<uint32_t, uint32_t, B>()};         \
+  static const LsdEntry kW##B##V64_32[] = {wide_entry<uint32_t, uint64_t, B>()};         \
+  static const LsdEntry kW##B##None64[] = {wide_entry<uint64_t, NoVal, B>()};            \
+  static const LsdEntry kW##B##V32_64[] = {wide_entry<uint64_t, uint32_t, B>()};         \
+  static const LsdEntry kW##B##V64_64[] = {wide_entry<uint64_t, uint64_t, B>()};
+ISORT_WIDE_TABLES(16)
+ISORT_WIDE_TABLES(11)
+#undef ISORT_WIDE_TABLES
 
-int r16_variants(int key_bits, int val_bits, const LsdEntry** out) {
-  const LsdEntry* t = nullptr;
-  if (key_bits == 32) t = val_bits == 0 ? kR16None32 : val_bits == 32 ? kR16V32_32 : kR16V64_32;
-  if (key_bits == 64) t = val_bits == 0 ? kR16None64 : val_bits == 32 ? kR16V32_64 : kR16V64_64;
-  if (!t || (val_bits != 0 && val_bits != 32 && val_bits != 64)) return 0;
-  *out = t;
+int wide_variants(int key_bits, int val_bits, int radix_bits, const LsdEntry** out) {
+  if (val_bits != 0 && val_bits != 32 && val_bits != 64) return 0;
+  const int vi = val_bits == 0 ? 0 : val_bits == 32 ? 1 : 2;
+  const LsdEntry* t16[2][3] = {{kW16None32, kW16V32_32, kW16V64_32},
+                               {kW16None64, kW16V32_64, kW16V64_64}};
+  const LsdEntry* t11[2][3] = {{kW11None32, kW11V32_32, kW11V64_32},
+                               {kW11None64, kW11V32_64, kW11V64_64}};
+  if (key_bits != 32 && key_bits != 64) return 0;
+  const int ki = key_bits == 32 ? 0 : 1;
+  if (radix_bits == 16) *out = t16[ki][vi];
+  else if (radix_bits == 11) *out = t11[ki][vi];
+  else return 0;
   return 1;
 }
 

@@ -3,7 +3,7 @@ fastest, with a JSON cache keyed by GPU name, key/payload widths and size bucket
 
 What it tunes:
   * plain sorts: the radix-256 pass variant (threads x keys per thread) and the
-    radix width (8 or 16 bits) for (key_bits, val_bits, n-bucket);
+    radix width (8, 11 or 16 bits) for (key_bits, val_bits, n-bucket);
   * segmented sorts: the longest range that still takes the BTN network
     (btn_max) for (key_bits, val_bits).
 Measurement: CUDA events on the current stream around the library call, inputs
@@ -87,7 +87,8 @@ def tune_plain(n: int, key_bits: int = 32, val_bits: int = 0, reps: int = 5) -> 
         results.append({"radix_bits": 8, "variant": vi, "threads": threads, "kpt": kpt,
                         "ms": _time(run(8), restore, reps)})
     tune_set(key_bits, val_bits, 8, -1)
-    results.append({"radix_bits": 16, "variant": 0, "ms": _time(run(16), restore, reps)})
+    for rb in (11, 16):
+        results.append({"radix_bits": rb, "variant": 0, "ms": _time(run(rb), restore, reps)})
     best = min(results, key=lambda r: r["ms"])
     return {"best": best, "all": results, "n": n}
 

@@ -41,7 +41,7 @@ def test_argument_errors_need_no_gpu(lib):
     dummy = ctypes.c_void_p(256)
     assert lib.isort_keys(dummy, 10, 16, 8, None) == _lib.EINVAL        # bad key width
     assert lib.isort_keys(dummy, 10, 32, 7, None) == _lib.EUNSUPPORTED  # radix 2^7
-    assert lib.isort_keys(dummy, 10, 32, 11, None) == _lib.EUNSUPPORTED  # radix 2^11
+    assert lib.isort_keys(dummy, 10, 32, 12, None) == _lib.EUNSUPPORTED  # radix 2^12
     assert lib.isort_keys(dummy, 10, 32, 40, None) == _lib.EINVAL       # nonsense radix
     assert lib.isort_keys(dummy, -1, 32, 8, None) == _lib.EINVAL
     assert lib.isort_keys(dummy, (1 << 30) + 1, 32, 8, None) == _lib.EUNSUPPORTED
@@ -63,6 +63,9 @@ def test_workspace_size_and_tuning_tables(lib):
     assert isort.workspace_size(n, 64, 0, 8) >= n * 8
     assert isort.workspace_size(n, 32, 0, 16) >= n * 4 + 2 * 65536 * 4  # radix 65536: matrix
     assert len(isort.tune_variants(32, 0, 16)) == 1
+    # radix 2048: three passes (11, 11, 10 bits), a count matrix of 2^16-key rows
+    assert isort.workspace_size(n, 32, 0, 11) >= n * 4 + 2048 * 4 * (n >> 16)
+    assert len(isort.tune_variants(32, 0, 11)) == 1 and len(isort.tune_variants(64, 64, 11)) == 1
     v = isort.tune_variants(32, 0, 8)
     assert len(v) >= 2 and all(t % 32 == 0 and k > 0 for t, k in v)
     with pytest.raises(isort.IsortError):

@@ -199,6 +199,57 @@ def test_radix65536_edge_sizes():
         assert np.array_equal(gv, ov), n
 
 
+R11_BLOCK = 1 << 16  # keys per count-matrix row of the radix-2048 path
+
+
+@pytest.mark.parametrize("key_bits", [32, 64])
+@pytest.mark.parametrize("dist", inputs.DISTS)
+def test_radix2048_distributions(key_bits, dist):
+    """Radix 2048: 11-bit digits, the last one narrower (11, 11, 10 bits on
+    32-bit keys; five of 11 and one of 9 on 64-bit keys)."""
+    n = 1_234_567  # 19 count blocks, a ragged last block and sub-tile
+    k = inputs.keys(n, key_bits, dist, seed=14)
+    assert np.array_equal(gpu_sort(k, radix_bits=11), oracle.radix_sort(k, radix_bits=11))
+
+
+@pytest.mark.parametrize("key_bits,val_bits", [(32, 32), (32, 64), (64, 32), (64, 64)])
+@pytest.mark.parametrize("dist", ["uniform", "and4", "u16"])
+def test_radix2048_pairs_stable(key_bits, val_bits, dist):
+    n = 300_007
+    k = inputs.keys(n, key_bits, dist, seed=15)
+    v = inputs.iota(n, val_bits)
+    gk, gv = gpu_sort(k, v, radix_bits=11)
+    ok, ov = oracle.radix_sort(k, v, radix_bits=11)
+    assert np.array_equal(gk, ok)
+    assert np.array_equal(gv, ov)
+
+
+def test_radix2048_edge_sizes():
+    for n in sorted({0, 1, 2, 3, 4095, 4096, 4097, R11_BLOCK - 1, R11_BLOCK, R11_BLOCK + 1,
+                     3 * R11_BLOCK + 4097}):
+        k = inputs.keys(n, 32, "and4", seed=n + 5)
+        v = inputs.iota(n)
+        gk, gv = gpu_sort(k, v, radix_bits=11)
+        ok, ov = oracle.radix_sort(k, v, radix_bits=11)
+        assert np.array_equal(gk, ok), n
+        assert np.array_equal(gv, ov), n
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dist", ["uniform", "and4"])
+def test_full_size_2p28_u32_radix2048(dist):
+    """n = 2^28 u32 keys at radix 2048 (three passes), element by element."""
+    n = 1 << 28
+    t = inputs.device_keys(n, 32, dist, seed=1)
+    host_in = to_host(t)
+    isort.sort_keys(t, 11)
+    assert isort.stream_status() == _lib.OK
+    got = to_host(t)
+    del t
+    torch.cuda.empty_cache()
+    assert np.array_equal(got, oracle.radix_sort(host_in, radix_bits=11))
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("dist", inputs.DISTS)
 def test_full_size_2p28_u32_radix65536(dist):
