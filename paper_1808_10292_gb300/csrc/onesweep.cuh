@@ -72,6 +72,39 @@ struct HistShape {
   static constexpr size_t SMEM = sizeof(uint32_t) * (size_t)L::PASSES * L::R * LANES;
 };
 
+// Calls count(k) for every key of keys[0..n): thread `me` of `nth` takes the
+// unaligned head and tail one key at a time and the 16-byte-aligned middle as
+// 16-byte loads, U of them in flight.
+template <typename K, typename F>
+__device__ __forceinline__ void count_keys(const K* __restrict__ keys, int64_t n, int64_t me,
+                                           int64_t nth, F&& count) {
+  using V16 = Vec16<K>;
+  const uintptr_t addr = reinterpret_cast<uintptr_t>(keys);
+  int64_t head = (int64_t)(((16 - (addr & 15)) & 15) / sizeof(K));
+  if (head > n) head = n;
+  const int64_t nvec = (n - head) / V16::N;
+  const typename V16::T* vec = reinterpret_cast<const typename V16::T*>(keys + head);
+  if (me < head) count(keys[me]);
+  constexpr int U = 4;
+  int64_t i = me;
+  for (; i + (U - 1) * nth < nvec; i += U * nth) {
+    typename V16::T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = vec[i + u * nth];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int c = 0; c < V16::N; ++c) count(V16::get(v[u], c));
+  }
+  for (; i < nvec; i += nth) {
+    typename V16::T v = vec[i];
+#pragma unroll
+    for (int c = 0; c < V16::N; ++c) count(V16::get(v, c));
+  }
+  const int64_t tail0 = head + nvec * V16::N;
+  if (tail0 + me < n) count(keys[tail0 + me]);
+}
+
 template <typename K, int BITS, int THREADS, int LANES>
 __global__ void __launch_bounds__(THREADS) k_hist(const K* __restrict__ keys, int64_t n,
                                                   uint32_t* __restrict__ hist) {
@@ -88,34 +121,8 @@ __global__ void __launch_bounds__(THREADS) k_hist(const K* __restrict__ keys, in
       atomicAdd(&my[(p * R + digit_of(k, p * BITS, (1u << L::width(p)) - 1)) * LANES], 1u);
   };
 
-  using V16 = Vec16<K>;
-  const uintptr_t addr = reinterpret_cast<uintptr_t>(keys);
-  int64_t head = (int64_t)(((16 - (addr & 15)) & 15) / sizeof(K));
-  if (head > n) head = n;
-  const int64_t nvec = (n - head) / V16::N;
-  const typename V16::T* vec = reinterpret_cast<const typename V16::T*>(keys + head);
-  const int64_t gtid = blockIdx.x * (int64_t)THREADS + threadIdx.x;
-  const int64_t gsize = (int64_t)gridDim.x * THREADS;
-
-  if (gtid < head) count(keys[gtid]);
-  constexpr int U = 4;  // independent 16-byte loads in flight per thread
-  int64_t i = gtid;
-  for (; i + (U - 1) * gsize < nvec; i += U * gsize) {
-    typename V16::T v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) v[u] = vec[i + u * gsize];
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int c = 0; c < V16::N; ++c) count(V16::get(v[u], c));
-  }
-  for (; i < nvec; i += gsize) {
-    typename V16::T v = vec[i];
-#pragma unroll
-    for (int c = 0; c < V16::N; ++c) count(V16::get(v, c));
-  }
-  const int64_t tail0 = head + nvec * V16::N;
-  if (tail0 + gtid < n) count(keys[tail0 + gtid]);
+  count_keys(keys, n, blockIdx.x * (int64_t)THREADS + threadIdx.x, (int64_t)gridDim.x * THREADS,
+             count);
   __syncthreads();
   for (int j = threadIdx.x; j < P * R; j += THREADS) {
     uint32_t s = 0;
@@ -219,6 +226,8 @@ struct OnesweepShape {
   static constexpr size_t SMEM = HEADER_WORDS * 4 + STAGE_BYTES;
   static constexpr int DPT = R >= THREADS ? R / THREADS : 1;  // digits per owning thread
   static constexpr int DTHREADS = R >= THREADS ? THREADS : R;  // threads that own digits
+  static_assert(THREADS >= R || R % THREADS == 0,
+                "every digit needs exactly one owner thread: THREADS >= R or THREADS divides R");
 };
 
 // Decoupled look-back for digit d of tile `tile` (> 0): the sum of the counts of
@@ -447,32 +456,49 @@ __device__ __forceinline__ void tile_rank_place(const K (&key)[KPT], int shift, 
                                                 int tile_n, int wofs, uint32_t* my,
                                                 uint32_t* mm, K* s_keys,
                                                 uint32_t (&rank2)[(KPT + 1) / 2]) {
+  static_assert(MASK_BUFS == 3, "row r marks slot array r mod 3");
   const int lane = threadIdx.x & 31;
   const uint32_t ge = lanemask_ge();
   const uint32_t bit = 1u << lane;
-  uint32_t* slot1 = mm;
-  uint32_t* slot2 = mm;
-  bool lead1 = false, lead2 = false;
+  auto valid_row = [&](int i) { return FULL || wofs + i * 32 < tile_n; };
+  // Software-pipelined over rows: while row i's counter update is in flight,
+  // row i+1 is marked and its peer mask read. Row r marks array r mod 3; the
+  // slot of row i-1 is cleared in step i before the barrier that precedes any
+  // mark of row i+2 (its next user), after every lane has read it (all lanes
+  // passed the barrier of row i).
+  uint32_t d = digit_of(key[0], shift, mask);
+  uint32_t* slot = mm + d;
+  if (valid_row(0)) atomicOr(slot, bit);
+  __syncwarp();
+  uint32_t peers = valid_row(0) ? *slot : 0u;
+  uint32_t* slot_prev = mm;
+  bool lead_prev = false;
 #pragma unroll
   for (int i = 0; i < KPT; ++i) {
-    const bool valid = FULL || wofs + i * 32 < tile_n;
-    const uint32_t d = digit_of(key[i], shift, mask);
-    uint32_t* slot = mm + (i % MASK_BUFS) * R + d;
-    if (lead2) *slot2 = 0u;
-    if (valid) atomicOr(slot, bit);
-    __syncwarp();
-    const uint32_t peers = valid ? *slot : 0u;
+    const bool valid = valid_row(i);
     const bool leader = valid && (peers >> lane) == 1u;
-    uint32_t after = 0;
-    if (leader) after = atomicAdd(&my[d], __popc(peers)) + __popc(peers);
-    after = __shfl_sync(kFullMask, after, (31 - __clz(peers)) & 31);
+    if (i > 0 && lead_prev) *slot_prev = 0u;  // row i-1's slot, dead now
+    uint32_t old = 0;
+    if (leader) old = atomicAdd(&my[d], __popc(peers));
+    uint32_t d_next = 0, peers_next = 0;
+    uint32_t* slot_next = mm;
+    if (i + 1 < KPT) {
+      d_next = digit_of(key[i + 1], shift, mask);
+      slot_next = mm + ((i + 1) % MASK_BUFS) * R + d_next;
+      if (valid_row(i + 1)) atomicOr(slot_next, bit);
+      __syncwarp();
+      peers_next = valid_row(i + 1) ? *slot_next : 0u;
+    }
+    const uint32_t after =
+        __shfl_sync(kFullMask, old + __popc(peers), (31 - __clz(peers)) & 31);
     const uint32_t pos = after - __popc(peers & ge);
     if (valid) s_keys[pos] = key[i];
     rank2[i >> 1] = (i & 1) ? (rank2[i >> 1] | (pos << 16)) : pos;
-    slot2 = slot1;
-    lead2 = lead1;
-    slot1 = slot;
-    lead1 = leader;
+    slot_prev = slot;
+    lead_prev = leader;
+    slot = slot_next;
+    peers = peers_next;
+    d = d_next;
   }
 }
 
@@ -842,7 +868,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep_tma(PassParams p) {
   using S = OnesweepShape<K, NoVal, BITS, THREADS, KPT>;
   using T = TmaShape<K, BITS, THREADS, KPT>;
   constexpr int R = S::R, WARPS = S::WARPS, TILE = S::TILE;
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
   uint32_t* s_misc = s_wcnt + WARPS * R + R;
   uint32_t* s_stage = reinterpret_cast<uint32_t*>(smem + S::HEADER_WORDS * 4);

@@ -164,8 +164,10 @@ __global__ void __launch_bounds__(CTA) k_seg_btn(K* __restrict__ keys, V* __rest
 
 // ---------------------------------------------------------------------------
 // Digit histograms of the radix ranges: CTA c walks a contiguous run of tiles,
-// counting into shared memory and flushing into seg_hist when the range changes.
-template <typename K, int BITS, int TILE>
+// counting into shared memory and flushing into seg_hist when the range
+// changes. The counters are laid out as k_hist's, [p][d][lane % LANES], so one
+// warp's atomics fall in different banks; keys are read as 16-byte vectors.
+template <typename K, int BITS, int TILE, int LANES>
 __global__ void __launch_bounds__(1024) k_seg_hist(const K* __restrict__ keys,
                                                    const int64_t* __restrict__ off, int64_t nseg,
                                                    int64_t total, const int32_t* __restrict__ list,
@@ -174,28 +176,37 @@ __global__ void __launch_bounds__(1024) k_seg_hist(const K* __restrict__ keys,
                                                    const int32_t* __restrict__ tile_slot,
                                                    uint32_t* __restrict__ seg_hist) {
   using L = DigitLayout<K, BITS>;
-  constexpr int R = L::R, P = L::PASSES, SUBS = 4;
-  __shared__ uint32_t s_hist[SUBS][P * R];
-  for (int i = threadIdx.x; i < SUBS * P * R; i += 1024) (&s_hist[0][0])[i] = 0;
+  constexpr int R = L::R, P = L::PASSES;
+  extern __shared__ __align__(16) uint32_t s_cnt[];  // [P][R][LANES]
+  for (int i = threadIdx.x; i < P * R * LANES; i += 1024) s_cnt[i] = 0;
   const int64_t T = cnt[kCntTiles];
   const int64_t t0 = T * blockIdx.x / gridDim.x, t1 = T * (blockIdx.x + 1) / gridDim.x;
-  uint32_t* my = s_hist[(threadIdx.x >> 5) % SUBS];
+  uint32_t* my = s_cnt + (threadIdx.x & (LANES - 1));
+  auto count = [&](K k) {
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      atomicAdd(&my[(p * R + digit_of(k, p * BITS, (1u << L::width(p)) - 1)) * LANES], 1u);
+  };
   int32_t cur = -1;
   __syncthreads();
   auto flush = [&](int32_t slot) {
     __syncthreads();
     for (int j = threadIdx.x; j < P * R; j += 1024) {
       uint32_t s = 0;
-#pragma unroll
-      for (int b = 0; b < SUBS; ++b) {
-        s += s_hist[b][j];
-        s_hist[b][j] = 0;
+#pragma unroll 8
+      for (int b = 0; b < LANES; ++b) {
+        const int w = j * LANES + ((b + j) & (LANES - 1));
+        s += s_cnt[w];
+        s_cnt[w] = 0;
       }
       if (s) atomicAdd(&seg_hist[(size_t)slot * P * R + j], s);
     }
     __syncthreads();
   };
-  for (int64_t t = t0; t < t1; ++t) {
+  // A range's tiles have consecutive ids and cover consecutive keys, so each
+  // run of this CTA's tiles that belongs to one range is counted as one span
+  // (long spans keep many 16-byte loads in flight per thread).
+  for (int64_t t = t0; t < t1;) {
     const int32_t slot = tile_slot[t];
     if (slot != cur) {
       if (cur >= 0) flush(cur);
@@ -203,14 +214,12 @@ __global__ void __launch_bounds__(1024) k_seg_hist(const K* __restrict__ keys,
     }
     int64_t start, len;
     seg_range(off, list[(size_t)kSegRadix * nseg + slot], total, start, len);
-    const int64_t lo = start + (t - slot_first[slot]) * TILE;
-    const int64_t hi = min(start + len, lo + TILE);
-    for (int64_t i = lo + threadIdx.x; i < hi; i += 1024) {
-      const K k = keys[i];
-#pragma unroll
-      for (int p = 0; p < P; ++p)
-        atomicAdd(&my[p * R + digit_of(k, p * BITS, (1u << L::width(p)) - 1)], 1u);
-    }
+    const int64_t first = slot_first[slot];
+    const int64_t t_end = min(t1, first + (len + TILE - 1) / TILE);
+    const int64_t lo = start + (t - first) * TILE;
+    const int64_t hi = min(start + len, start + (t_end - first) * TILE);
+    count_keys(keys + lo, hi - lo, threadIdx.x, 1024, count);
+    t = t_end > t ? t_end : t + 1;
   }
   if (cur >= 0) flush(cur);
 }
@@ -340,9 +349,15 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
 
   // long ranges: histograms, bases, then the rounds over all their tiles
   timer_begin(a.timer, "k_seg_hist", st);
-  k_seg_hist<K, 8, TILE><<<a.num_sms, 1024, 0, st>>>(keys, a.offsets, a.nseg, a.total, a.lists,
-                                                     a.cnt, a.slot_first, a.tile_slot,
-                                                     a.seg_hist);
+  {
+    constexpr int LANES = sizeof(K) == 4 ? 32 : 16;  // 128 KiB of counters either way
+    constexpr size_t HSMEM = sizeof(uint32_t) * (size_t)P * R * LANES;
+    auto hk = k_seg_hist<K, 8, TILE, LANES>;
+    if ((e = cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HSMEM)))
+      return e;
+    hk<<<a.num_sms, 1024, HSMEM, st>>>(keys, a.offsets, a.nseg, a.total, a.lists, a.cnt,
+                                       a.slot_first, a.tile_slot, a.seg_hist);
+  }
   timer_end(a.timer, st);
   timer_begin(a.timer, "k_seg_scan", st);
   k_seg_scan<8, P><<<(unsigned)nslots, R, 0, st>>>(a.cnt, a.seg_hist, a.seg_base);

@@ -5,8 +5,8 @@ namespace isort {
 
 // <K, V, warp M, mid M, CTA M, radix threads, keys per thread, min CTAs per SM>
 static const SegConfig kSeg32[] = {
-    seg_config<uint32_t, NoVal, 4, 8, 16, 384, 32, 2>(),
-    seg_config<uint32_t, uint32_t, 4, 8, 16, 384, 16, 2>(),
+    seg_config<uint32_t, NoVal, 4, 8, 16, 256, 32, 3>(),
+    seg_config<uint32_t, uint32_t, 4, 8, 16, 256, 20, 3>(),
     seg_config<uint32_t, uint64_t, 4, 8, 16, 256, 16, 2>(),
 };
 

@@ -5,7 +5,7 @@ namespace isort {
 
 // <K, V, warp M, mid M, CTA M, radix threads, keys per thread, min CTAs per SM>
 static const SegConfig kSeg64[] = {
-    seg_config<uint64_t, NoVal, 4, 8, 8, 384, 16, 2>(),
+    seg_config<uint64_t, NoVal, 4, 8, 8, 256, 20, 3>(),
     seg_config<uint64_t, uint32_t, 4, 8, 8, 256, 16, 2>(),
     seg_config<uint64_t, uint64_t, 4, 8, 8, 256, 12, 2>(),
 };

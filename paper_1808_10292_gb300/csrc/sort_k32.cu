@@ -8,26 +8,32 @@ namespace isort {
 // lsd_entry<K, V, radix bits, threads, keys per thread, min CTAs per SM,
 //           cluster CTAs, TMA loads, early counts>
 static const LsdEntry kK32None8[] = {
-    lsd_entry<uint32_t, NoVal, 8, 384, 32, 2, 1, false, true>(),  // 12288-key tiles
     lsd_entry<uint32_t, NoVal, 8, 256, 32, 3, 1, false, true>(),  // 8192-key tiles, 3 CTAs/SM
+    lsd_entry<uint32_t, NoVal, 8, 384, 32, 2, 1, false, true>(),  // 12288-key tiles
+    lsd_entry<uint32_t, NoVal, 8, 256, 20, 4, 1, false, true>(),  // 4 CTAs/SM
+    lsd_entry<uint32_t, NoVal, 8, 256, 24, 4, 1, false, true>(),
     lsd_entry<uint32_t, NoVal, 8, 512, 20, 2, 1, false, true>(),
     lsd_entry<uint32_t, NoVal, 8, 384, 24, 2, 1, false, true>(),
-    lsd_entry<uint32_t, NoVal, 8, 256, 16, 4, 1, false, true>(),  // 4096-key tiles
+    lsd_entry<uint32_t, NoVal, 8, 128, 32, 6, 1, false, true>(),  // 6 CTAs/SM
     lsd_entry<uint32_t, NoVal, 8, 512, 24, 2>(),                  // rank, then reorder
     lsd_entry<uint32_t, NoVal, 8, 256, 16, 4>(),
     lsd_entry<uint32_t, NoVal, 8, 256, 16, 4, 8>(),               // 8-CTA cluster super-tiles
     lsd_entry<uint32_t, NoVal, 8, 256, 32, 3, 1, true>(),         // TMA tile loads
 };
 static const LsdEntry kK32V32_8[] = {
+    lsd_entry<uint32_t, uint32_t, 8, 256, 20, 3, 1, false, true>(),
     lsd_entry<uint32_t, uint32_t, 8, 384, 16, 2, 1, false, true>(),
     lsd_entry<uint32_t, uint32_t, 8, 256, 16, 3, 1, false, true>(),
     lsd_entry<uint32_t, uint32_t, 8, 256, 24, 2, 1, false, true>(),
+    lsd_entry<uint32_t, uint32_t, 8, 256, 16, 4, 1, false, true>(),
     lsd_entry<uint32_t, uint32_t, 8, 256, 12, 3>(),
     lsd_entry<uint32_t, uint32_t, 8, 512, 12, 2>(),
     lsd_entry<uint32_t, uint32_t, 8, 256, 12, 3, 8>(),
 };
 static const LsdEntry kK32V64_8[] = {
     lsd_entry<uint32_t, uint64_t, 8, 256, 16, 2, 1, false, true>(),
+    lsd_entry<uint32_t, uint64_t, 8, 256, 16, 3, 1, false, true>(),
+    lsd_entry<uint32_t, uint64_t, 8, 256, 12, 3, 1, false, true>(),
     lsd_entry<uint32_t, uint64_t, 8, 256, 12, 2>(),
 };
 

@@ -15,9 +15,10 @@ from paper_1808_10292_gb300 import _lib
 pytestmark = pytest.mark.gpu
 
 # lengths around every class edge: warp BTN (<= 128), 64-thread BTN (<= 512),
-# 256-thread BTN (<= 4096 for 32-bit keys, 2048 for 64-bit), radix tiles (12288 / 3072 keys)
-EDGE_LENGTHS = [0, 1, 2, 3, 31, 32, 33, 127, 128, 129, 511, 512, 513, 2047, 2048, 2049, 3071, 12287,
-                12288, 12289, 24577,
+# 256-thread BTN (<= 4096 for 32-bit keys, 2048 for 64-bit), radix tiles (8192 keys for
+# 32-bit keys alone, 5120 with 32-bit payloads or for 64-bit keys, 4096 / 3072 for the rest)
+EDGE_LENGTHS = [0, 1, 2, 3, 31, 32, 33, 127, 128, 129, 511, 512, 513, 2047, 2048, 2049, 3071, 5119,
+                5120, 5121, 8192, 10241, 12287, 12288, 12289, 16385, 24577,
                 3072, 3073, 4095, 4096, 4097, 8191, 8193, 12289, 100_000, 0, 1, 5]
 
 
