@@ -45,13 +45,14 @@ WORKLOADS = {
     # n is the total over 20,000 ranges with log-uniform lengths in [1, 2^20]
     "segmented_20000": (0, 32, 0, 8, "batched segmented sort, 20,000 ranges, lengths "
                                      "log-uniform in [1, 2^20], uniform uint32 keys"),
+    "short_ranges": (1 << 26, 32, 0, 8, "short ranges (32 .. 4096 keys), BTN vs OET networks"),
     "serve_poisson": (0, 32, 32, 8, "serving loop: Poisson arrivals at 2,000 req/s, sizes "
                                     "log-uniform in [2^10, 2^24] uint32 keys, half with "
                                     "uint32 payloads, 40 GB admission budget"),
 }
 ALIASES = {"r16": "u32_2p28_r65536", "r11": "u32_2p28_r2048", "pairs": "pairs_2p27", "u64": "u64_2p26",
            "paper128m": "u32_128M_paper", "default": "u32_2p28_r256",
-           "segmented": "segmented_20000", "serve": "serve_poisson"}
+           "segmented": "segmented_20000", "serve": "serve_poisson", "networks": "short_ranges"}
 
 
 def parse():
@@ -674,6 +675,82 @@ def run_ours_segmented(a):
     return 0
 
 
+def run_ours_short_ranges(a):
+    """The two short-range networks of the paper (BTN, OET) on batches of equal
+    ranges: for each range length L, 2^26 / L ranges of uint32 keys sorted with
+    one isort_segmented call; CUDA events per call, keys restored and L2
+    flushed outside the event pair, median of the timed steps."""
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    import inputs
+    import paper_1808_10292_gb300 as isort
+    from paper_1808_10292_gb300 import _lib
+    n = 1 << 26
+    stream = torch.cuda.current_stream()
+    pristine = inputs.device_keys(n, 32, a.dist, a.seed)
+    keys = torch.empty_like(pristine)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda").view(torch.int32)
+    flush.zero_()
+    clocks = ClockSampler(local)
+    clocks.start()
+    table, launches = {}, 0
+    isort.debug_set(_lib.DEBUG_KERNEL_TIMING, 1)  # to count the library's launches
+    t_wall0 = time.perf_counter()
+    for L in (32, 128, 512, 2048, 4096):
+        off = torch.arange(0, n + 1, L, dtype=torch.int64, device="cuda")
+        table[L] = {}
+        for net in ("btn", "oet"):
+            isort.tune_segmented_network(32, 0, net)
+            ms = []
+            for i in range(a.warmup + a.steps):
+                keys.copy_(pristine)
+                flush.sum()
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+                isort.sort_segmented(keys, off)
+                s1.record(stream)
+                s1.synchronize()
+                kt = isort.kernel_times()
+                if i >= a.warmup:
+                    ms.append(s0.elapsed_time(s1))
+                    launches += len(kt)
+            if isort.stream_status() != _lib.OK:
+                raise RuntimeError("device error in the short-range benchmark")
+            sk = keys.view(torch.int32) ^ (-(1 << 31))
+            srt = (sk.view(-1, L)[:, 1:] >= sk.view(-1, L)[:, :-1]).all().item()
+            if not srt:
+                raise RuntimeError(f"ranges of {L} keys not sorted ({net})")
+            q = 32 if L <= 128 else 64 if L <= 512 else 256
+            table[L][net] = {"keys_per_s": n / (statistics.median(ms) / 1000.0),
+                             "ms": statistics.median(ms), "q_threads": q,
+                             "network_steps": (q.bit_length() - 1) * q.bit_length() // 2
+                             if net == "btn" else q}
+    isort.tune_segmented_network(32, 0, "btn")
+    isort.debug_set(_lib.DEBUG_KERNEL_TIMING, 0)
+    clocks.window(t_wall0, time.perf_counter())
+    clk = clocks.stop()
+    tot_btn = sum(table[L]["btn"]["ms"] for L in table)
+    line = {
+        "metric": "short-range keys/s (equal ranges of 32..4096 uint32 keys, BTN network)",
+        "value": n * len(table) / (tot_btn / 1000.0),
+        "unit": "keys/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": tot_btn, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": a.workload, "keys_per_length": n, "dist": a.dist, "seed": a.seed,
+                   "l2": "256 MiB of keys per call, restored and L2 flushed before each call"},
+        "networks": {str(L): v for L, v in table.items()},
+        "oet_over_btn_time": {str(L): table[L]["oet"]["ms"] / table[L]["btn"]["ms"]
+                              for L in table},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours_serve(a):
     """Served (continuous batching) vs sequential plain sorts on one Poisson trace;
     then both arms on a backlog (every request queued at once) for capacity."""
@@ -764,6 +841,12 @@ def main():
         if a.impl == "reference":
             return run_reference_segmented(a)
         return run_ours_segmented(a)
+    if a.workload == "short_ranges":
+        if a.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "network comparison only; "
+                              "the oracle arm is timed on the plain and segmented workloads"}))
+            return 0
+        return run_ours_short_ranges(a)
     if a.impl == "reference":
         return run_reference(a)
     return run_ours(a)

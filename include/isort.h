@@ -102,6 +102,15 @@ isort_status isort_keys_noalloc(void *keys, int64_t n, uint32_t *err_out, void *
  * keys for 32-bit keys, 2048 for 64-bit; < 0 restores the default). */
 isort_status isort_tune_segmented(int key_bits, int val_bits, int64_t btn_max_keys);
 
+/* Network for the short ranges of a segmented sort (the paper compares both,
+ * Section "Related work", Eqs. Tb and To; Tables 1-4):
+ *   ISORT_NET_BTN (default): bitonic merge-split over q runs, lg q (lg q + 1) / 2 stages;
+ *   ISORT_NET_OET: odd-even transposition merge-split over q runs, q rounds.
+ * Both give the same (stable) result. Other values return ISORT_EINVAL. */
+#define ISORT_NET_BTN 0
+#define ISORT_NET_OET 1
+isort_status isort_tune_segmented_network(int key_bits, int val_bits, int network);
+
 /* Bytes of workspace one isort_segmented call with these arguments needs. */
 isort_status isort_segmented_workspace_size(int64_t num_segments, int64_t total_keys, int key_bits,
                                             int val_bits, size_t *bytes);

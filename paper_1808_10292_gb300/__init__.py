@@ -141,6 +141,13 @@ def tune_segmented(key_bits: int = 32, val_bits: int = 0, btn_max_keys: int = -1
     check(load().isort_tune_segmented(key_bits, val_bits, btn_max_keys), "isort_tune_segmented")
 
 
+def tune_segmented_network(key_bits: int = 32, val_bits: int = 0, network: str = "btn"):
+    """Network of the short ranges of a segmented sort: "btn" (default) or "oet"."""
+    net = {"btn": _lib.NET_BTN, "oet": _lib.NET_OET}[network]
+    check(load().isort_tune_segmented_network(key_bits, val_bits, net),
+          "isort_tune_segmented_network")
+
+
 def segmented_workspace_size(num_segments: int, total_keys: int, key_bits: int = 32,
                              val_bits: int = 0) -> int:
     out = ctypes.c_size_t(0)

@@ -19,6 +19,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
 DEBUG_SPIN_LIMIT, DEBUG_STALL_TILE, DEBUG_KERNEL_TIMING = 1, 2, 3
 DEBUG_TRACE_PTR, DEBUG_TRACE_PASS, DEBUG_PREFETCH_TILES = 4, 5, 6
 NOALLOC_MAX_KEYS = 1 << 20
+NET_BTN, NET_OET = 0, 1
 
 _lib = None
 
@@ -45,6 +46,7 @@ def _sig(lib):
         "isort_debug_set": [i32, i64],
         "isort_keys_noalloc": [vp, i64, vp, vp],
         "isort_tune_segmented": [i32, i32, i64],
+        "isort_tune_segmented_network": [i32, i32, i32],
         "isort_segmented_workspace_size": [i64, i64, i32, i32, ctypes.POINTER(sz)],
     }
     for name, args in sigs.items():

@@ -125,6 +125,7 @@ bool aligned(const void* p, int bytes) { return (reinterpret_cast<uintptr_t>(p) 
 
 // ---- segmented sort workspace ----
 std::map<std::pair<int, int>, int64_t> g_seg_btn_max;  // (key_bits, val_bits) -> threshold
+std::map<std::pair<int, int>, int> g_seg_network;      // (key_bits, val_bits) -> ISORT_NET_*
 
 // Longest range that takes the BTN path: the tuned threshold, capped by the
 // capacity of the 256-thread BTN class (256 threads x cta_m keys).
@@ -302,6 +303,10 @@ isort_status isort_segmented(void* keys, void* vals, const int64_t* offsets, int
   a.nseg = num_segments;
   a.total = total_keys;
   a.btn_max = seg_btn_max(*c);
+  {
+    auto it = g_seg_network.find({key_bits, c->val_bits});
+    a.network = it == g_seg_network.end() ? ISORT_NET_BTN : it->second;
+  }
   a.max_tiles = L.max_tiles;
   a.lists = reinterpret_cast<int32_t*>(b + L.lists);
   a.cnt = reinterpret_cast<uint32_t*>(b + L.cnt);
@@ -335,6 +340,15 @@ isort_status isort_tune_segmented(int key_bits, int val_bits, int64_t btn_max_ke
     return ISORT_OK;
   }
   g_seg_btn_max[{key_bits, val_bits}] = btn_max_keys;
+  return ISORT_OK;
+}
+
+isort_status isort_tune_segmented_network(int key_bits, int val_bits, int network) {
+  if (key_bits != 32 && key_bits != 64) return ISORT_EINVAL;
+  if (val_bits != 0 && val_bits != 32 && val_bits != 64) return ISORT_EINVAL;
+  if (network != ISORT_NET_BTN && network != ISORT_NET_OET) return ISORT_EINVAL;
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_seg_network[{key_bits, val_bits}] = network;
   return ISORT_OK;
 }
 

@@ -139,4 +139,52 @@ __device__ __forceinline__ void btn_network(BtnItem<K, STABLE> (&x)[M], int t, K
   }
 }
 
+// OET: the paper's p-wide odd-even transposition sort ("Algorithm OET",
+// Section "Related work", cost Eq. To) over the same runs. Q rounds; in an
+// even round threads (2i, 2i+1) merge-split, in an odd round (2i+1, 2i+2); the
+// lower-indexed thread of a pair keeps the M smallest items. After Q rounds
+// the runs, concatenated in thread order, are sorted (odd-even transposition
+// sorts Q "keys" in Q rounds, and a merge-split is a comparator on runs).
+// Partners are neighbours: even rounds stay within a warp (shuffles); odd
+// rounds cross warp boundaries when Q > 32 and then go through sk/si.
+// Contains __syncthreads when Q > 32 (all Q threads must call it).
+template <bool STABLE, typename K, int M, int Q>
+__device__ __forceinline__ void oet_network(BtnItem<K, STABLE> (&x)[M], int t, K* sk,
+                                            uint32_t* si) {
+  BtnItem<K, STABLE> b[M];
+  const int lane = t & 31;
+#pragma unroll 1
+  for (int r = 0; r < Q; ++r) {
+    const bool odd = r & 1;
+    // partner: t ^ 1 in even rounds; t + 1 (t odd) or t - 1 (t even) in odd rounds
+    const int u = odd ? ((t & 1) ? t + 1 : t - 1) : (t ^ 1);
+    const bool active = u >= 0 && u < Q;
+    if (!odd || Q == 32) {
+      // within the warp: lane u & 31 (idle lanes read something and ignore it)
+      const int src = active ? (u & 31) : lane;
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        b[i].k = __shfl_sync(kFullMask, x[i].k, src);
+        if constexpr (STABLE) b[i].i = __shfl_sync(kFullMask, x[i].i, src);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        sk[i * Q + t] = x[i].k;
+        if constexpr (STABLE) si[i * Q + t] = x[i].i;
+      }
+      __syncthreads();
+      if (active) {
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+          b[i].k = sk[i * Q + u];
+          if constexpr (STABLE) b[i].i = si[i * Q + u];
+        }
+      }
+      __syncthreads();
+    }
+    if (active) btn_merge_split<STABLE>(x, b, t < u);
+  }
+}
+
 }  // namespace isort

@@ -85,6 +85,7 @@ struct SegArgs {
   int64_t nseg;
   int64_t total;
   int64_t btn_max;       // ranges longer than this take the radix path
+  int network;           // short-range network: 0 = BTN, 1 = OET
   int64_t max_tiles;     // upper bound on tiles of the radix ranges
   int32_t* lists;        // [4][nseg]
   uint32_t* cnt;         // [kCntWords]

@@ -12,7 +12,8 @@
 //                   BTN, radix) and gives each radix range a block of tile ids.
 //   k_seg_fill      tile id -> radix range.
 //   k_seg_btn<Q,M>  persistent: Q threads with M keys each sort one range at a
-//                   time, popped from the class list (Q = 32: one range per warp).
+//                   time, popped from the class list (Q = 32: one range per warp),
+//                   with the BTN network or, if chosen, the OET network.
 //   k_seg_hist      digit histograms of every radix range, all passes, one read.
 //   k_seg_scan      per range and pass, exclusive digit bases.
 //   k_seg_onesweep  one count-sort round over the tiles of ALL radix ranges; the
@@ -94,7 +95,7 @@ struct BtnShape {
                                  (HV ? sizeof(VS) * (size_t)CAP * GROUPS : 0) + 16;
 };
 
-template <typename K, typename V, int Q, int M, int CTA>
+template <typename K, typename V, int Q, int M, int CTA, bool OET = false>
 __global__ void __launch_bounds__(CTA) k_seg_btn(K* __restrict__ keys, V* __restrict__ vals,
                                                  const int64_t* __restrict__ off, int64_t nseg,
                                                  int64_t total, const int32_t* __restrict__ list,
@@ -140,7 +141,10 @@ __global__ void __launch_bounds__(CTA) k_seg_btn(K* __restrict__ keys, V* __rest
       }
     }
     btn_local_sort<STABLE>(x);
-    btn_network<STABLE, K, M, Q>(x, t, sk, si);
+    if constexpr (OET)
+      oet_network<STABLE, K, M, Q>(x, t, sk, si);
+    else
+      btn_network<STABLE, K, M, Q>(x, t, sk, si);
     if constexpr (HV) {
       if constexpr (Q == 32)
         __syncwarp();
@@ -321,16 +325,17 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
                                                      a.slot_first, a.tile_slot);
   timer_end(a.timer, st);
 
-  // short ranges: the three BTN classes, persistent grids
+  // short ranges: the three network classes, persistent grids
   K* keys = static_cast<K*>(a.keys);
   V* vals = static_cast<V*>(a.vals);
   {
+    const bool oet = a.network == 1;
     using B0 = BtnShape<K, V, 32, WM, 256>;
-    auto k0 = k_seg_btn<K, V, 32, WM, 256>;
+    auto k0 = oet ? k_seg_btn<K, V, 32, WM, 256, true> : k_seg_btn<K, V, 32, WM, 256>;
     using B1 = BtnShape<K, V, 64, MM, 64>;
-    auto k1 = k_seg_btn<K, V, 64, MM, 64>;
+    auto k1 = oet ? k_seg_btn<K, V, 64, MM, 64, true> : k_seg_btn<K, V, 64, MM, 64>;
     using B2 = BtnShape<K, V, 256, CM, 256>;
-    auto k2 = k_seg_btn<K, V, 256, CM, 256>;
+    auto k2 = oet ? k_seg_btn<K, V, 256, CM, 256, true> : k_seg_btn<K, V, 256, CM, 256>;
     if ((e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B2::SMEM)))
       return e;
     timer_begin(a.timer, "k_seg_btn_warp", st);

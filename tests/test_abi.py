@@ -52,6 +52,9 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.isort_pairs(dummy, None, 10, 32, 32, 8, None) == _lib.EINVAL
     assert lib.isort_pairs(dummy, dummy, 10, 32, 16, 8, None) == _lib.EINVAL
     assert lib.isort_debug_set(99, 0) == _lib.EINVAL
+    assert lib.isort_tune_segmented_network(32, 0, 2) == _lib.EINVAL    # no such network
+    assert lib.isort_tune_segmented_network(16, 0, _lib.NET_OET) == _lib.EINVAL
+    assert lib.isort_tune_segmented_network(32, 0, _lib.NET_BTN) == _lib.OK
     assert lib.isort_strerror(_lib.ETIMEOUT) == b"bounded device wait gave up"
 
 

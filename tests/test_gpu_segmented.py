@@ -50,6 +50,30 @@ def test_class_edges(key_bits, val_bits, dist):
         assert np.array_equal(gv, ov)
 
 
+@pytest.mark.parametrize("key_bits,val_bits", [(32, 0), (32, 32), (64, 0), (64, 64)])
+@pytest.mark.parametrize("dist", ["uniform", "and4", "equal", "reverse"])
+def test_oet_network_class_edges(key_bits, val_bits, dist):
+    """The odd-even transposition network (Algorithm OET) on the short-range
+    classes gives the same stable result as BTN and the oracle."""
+    L = np.array(EDGE_LENGTHS, dtype=np.int64)
+    off = inputs.segment_offsets(L)
+    n = int(off[-1])
+    k = inputs.keys(n, key_bits, dist, seed=43)
+    v = inputs.iota(n, val_bits) if val_bits else None
+    try:
+        isort.tune_segmented_network(key_bits, val_bits, "oet")
+        st, gk, gv = run_segmented(k, off, v)
+    finally:
+        isort.tune_segmented_network(key_bits, val_bits, "btn")
+    assert st == _lib.OK
+    if v is None:
+        assert np.array_equal(gk, oracle.segmented_sort(k, off))
+    else:
+        ok, ov = oracle.segmented_sort(k, off, v)
+        assert np.array_equal(gk, ok)
+        assert np.array_equal(gv, ov)
+
+
 @pytest.mark.parametrize("key_bits", [32, 64])
 def test_log_uniform_lengths(key_bits):
     """The batched workload's recipe at reduced scale: 3000 ranges, lengths
