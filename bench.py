@@ -815,14 +815,21 @@ def run_ours_serve(a):
         srv.close()
         srv = serve.SortServer(budget_bytes=40 << 30, num_streams=4, max_batch_keys=1 << 27,
                                max_batch_requests=2048, batching=batching)
+        clocks = ClockSampler(local)
+        clocks.start()
+        l0 = isort.launch_count()
         t0 = time.perf_counter()
         reqs = serve.drive(srv, arr, sizes, payload, make_fill, duration_s=duration)
         srv.close()
         wall = time.perf_counter() - t0
+        launches = isort.launch_count() - l0
+        clocks.window(t0, t0 + wall)
+        clk = clocks.stop()
         if srv.errors:
             raise RuntimeError(f"serving errors: {srv.errors[:3]}")
         out = serve.latency_summary(reqs)
-        out.update({"batches": srv.batches, "rejected": len(srv.rejected), "wall_s": wall})
+        out.update({"batches": srv.batches, "rejected": len(srv.rejected), "wall_s": wall,
+                    "gpu_launches": launches, "clocks": clk})
         del srv
         torch.cuda.empty_cache()
         return out
@@ -855,6 +862,9 @@ def run_ours_serve(a):
         "sequential_plain_sorts": sequential,
         "capacity_backlog_4000": {"served": cap_served, "sequential": cap_seq,
                                   "speedup": cap_served["keys_per_s"] / cap_seq["keys_per_s"]},
+        "gpu_launches": served["gpu_launches"],
+        "clocks": served["clocks"],
+        "e2e": None,  # requests are generated on the device by their fill callbacks
     }
     print(json.dumps(line), flush=True)
     return 0

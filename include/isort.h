@@ -176,6 +176,11 @@ isort_status isort_debug_set(int what, int64_t value);
  * how many it wrote (-1.0 for a duration that could not be read). */
 int isort_debug_kernel_times(const char **names, float *ms, int max);
 
+/* Measurement hook: the number of kernels this library has enqueued since it
+ * was loaded (all streams and entry points; CUDA-graph replays of a captured
+ * call are not counted again). */
+int64_t isort_debug_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -141,6 +141,11 @@ def tune_segmented(key_bits: int = 32, val_bits: int = 0, btn_max_keys: int = -1
     check(load().isort_tune_segmented(key_bits, val_bits, btn_max_keys), "isort_tune_segmented")
 
 
+def launch_count() -> int:
+    """Kernels the library has enqueued since it was loaded (a measurement hook)."""
+    return int(load().isort_debug_launch_count())
+
+
 def tune_segmented_network(key_bits: int = 32, val_bits: int = 0, network: str = "btn"):
     """Network of the short ranges of a segmented sort: "btn" (default) or "oet"."""
     net = {"btn": _lib.NET_BTN, "oet": _lib.NET_OET}[network]

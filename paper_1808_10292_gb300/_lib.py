@@ -56,6 +56,8 @@ def _sig(lib):
     lib.isort_debug_kernel_times.argtypes = [ctypes.POINTER(ctypes.c_char_p),
                                              ctypes.POINTER(ctypes.c_float), i32]
     lib.isort_debug_kernel_times.restype = i32
+    lib.isort_debug_launch_count.argtypes = []
+    lib.isort_debug_launch_count.restype = ctypes.c_int64
     lib.isort_strerror.argtypes = [ctypes.c_int]
     lib.isort_strerror.restype = ctypes.c_char_p
     return lib

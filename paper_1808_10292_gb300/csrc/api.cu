@@ -2,6 +2,7 @@
 // family selection. Every step of a sort runs in the kernels of sort_k32.cu,
 // sort_k64.cu, radix_wide.cu and segmented.cu; this file only validates, carves
 // scratch memory and enqueues.
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -231,7 +232,10 @@ isort_status run_lsd(void* keys, void* vals, int64_t n, int key_bits, int val_bi
 
 namespace isort {
 
+std::atomic<int64_t> g_launch_count{0};  // every kernel the library enqueues
+
 void timer_begin(KernelTimer* t, const char* name, cudaStream_t st) {
+  g_launch_count.fetch_add(1, std::memory_order_relaxed);  // each launch is preceded by this call
   if (!t || t->count >= KernelTimer::kMax) return;
   t->name[t->count] = name;
   cudaEventRecord(t->ev[2 * t->count], st);
@@ -341,6 +345,10 @@ isort_status isort_tune_segmented(int key_bits, int val_bits, int64_t btn_max_ke
   }
   g_seg_btn_max[{key_bits, val_bits}] = btn_max_keys;
   return ISORT_OK;
+}
+
+int64_t isort_debug_launch_count(void) {
+  return isort::g_launch_count.load(std::memory_order_relaxed);
 }
 
 isort_status isort_tune_segmented_network(int key_bits, int val_bits, int network) {
