@@ -111,6 +111,28 @@ isort_status isort_tune_segmented(int key_bits, int val_bits, int64_t btn_max_ke
 #define ISORT_NET_OET 1
 isort_status isort_tune_segmented_network(int key_bits, int val_bits, int network);
 
+/* Sample sort: the paper's GVR (Algorithm 3, Section "Oversampling algorithms:
+ * GSD, GVR, GER") with the buckets sorted on this GPU. Sorts keys[0..n)
+ * ascending in place (stable with vals, which may be NULL):
+ *   1. s*p - 1 keys are drawn at random positions (SplitMix64, stream 30 of
+ *      `seed`; position = high 32 bits of the draw times n, shifted right 32)
+ *      and sorted with the BTN network;
+ *   2. the (i*s)-th smallest sampled keys, 1 <= i <= p-1, are the splitters;
+ *   3. one stable count-sort round moves every key to bucket j = the number of
+ *      splitters smaller than it;
+ *   4. each bucket is sorted independently (the segmented sort).
+ * buckets = p in 1..256, oversample = s >= 1 with p*s <= 4096 (else
+ * ISORT_EINVAL); n <= 2^30. bucket_counts: DEVICE array of p uint32 that
+ * receives the bucket sizes, or NULL. The result is the same as isort_keys /
+ * isort_pairs; the bucket sizes depend on the sample. */
+isort_status isort_sample_sort(void *keys, void *vals, int64_t n, int key_bits, int val_bits,
+                               int buckets, int oversample, uint64_t seed,
+                               uint32_t *bucket_counts, void *stream);
+
+/* Bytes of workspace one isort_sample_sort call with these arguments needs. */
+isort_status isort_sample_sort_workspace_size(int64_t n, int key_bits, int val_bits, int buckets,
+                                              int oversample, size_t *bytes);
+
 /* Bytes of workspace one isort_segmented call with these arguments needs. */
 isort_status isort_segmented_workspace_size(int64_t num_segments, int64_t total_keys, int key_bits,
                                             int val_bits, size_t *bytes);

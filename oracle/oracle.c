@@ -145,3 +145,100 @@ int oracle_segmented_sort(void *keys, void *vals, const int64_t *offsets, int64_
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * GVR, the paper's random-oversampling sample sort (Algorithm 3, Section
+ * "Oversampling algorithms: GSD, GVR, GER"), serially, in the algorithm's order:
+ *   1. Sample Selection: s*p - 1 keys at random positions, sorted;
+ *   2. Splitter Selection: the (i*s)-th smallest sampled keys, 1 <= i <= p-1;
+ *   3. Split input keys: each key's destination j = the number of splitters
+ *      smaller than it, then a count-sort by j (stable), so every key moves once;
+ *   4. LocalSorting: each destination sequence sorted by SR4 (radix 256).
+ * Random positions: SplitMix64 (Steele, Lea & Flood 2014), stream 30 of the
+ * seed: S = mix(seed*G ^ 30*C), draw m = mix(S + (m+1)*G), position = high 32
+ * bits of the draw times n, shifted right 32. Sorting the sample uses the C
+ * library's qsort (the paper sorts it with BTN; the sorted sample is the same).
+ */
+static uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static int cmp_u64(const void *a, const void *b) {
+  const uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+  return (x > y) - (x < y);
+}
+
+int oracle_gvr_sort(void *keys, void *vals, int64_t n, int key_bits, int val_bits, int p, int s,
+                    uint64_t seed, uint32_t *bucket_counts, uint64_t *splitters) {
+  if (n < 0 || (key_bits != 32 && key_bits != 64) ||
+      (val_bits != 0 && val_bits != 32 && val_bits != 64) || p < 1 || s < 1)
+    return 1;
+  const int kb = key_bits / 8, vb = val_bits / 8;
+  const int64_t ns = (int64_t)s * p - 1;
+  uint64_t *sample = malloc(sizeof(uint64_t) * (size_t)(ns > 0 ? ns : 1));
+  uint64_t *split = malloc(sizeof(uint64_t) * (size_t)(p > 1 ? p - 1 : 1));
+  int64_t *count = calloc((size_t)p + 1, sizeof(int64_t));
+  uint32_t *dest = malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+  void *kout = malloc((size_t)(n > 0 ? n : 1) * kb);
+  void *vout = vb ? malloc((size_t)(n > 0 ? n : 1) * vb) : NULL;
+  int rc = 0;
+  if (!sample || !split || !count || !dest || !kout || (vb && !vout)) {
+    rc = 2;
+    goto done;
+  }
+  /* 1. Sample Selection */
+  if (n > 0) {
+    const uint64_t G = 0x9E3779B97F4A7C15ull, C = 0xD1B54A32D192ED03ull;
+    const uint64_t S = sm64_mix(seed * G ^ 30ull * C);
+    for (int64_t m = 0; m < ns; ++m) {
+      const uint64_t d = sm64_mix(S + (uint64_t)(m + 1) * G);
+      const int64_t pos = (int64_t)(((d >> 32) * (uint64_t)n) >> 32);
+      sample[m] = get_key(keys, pos, kb);
+    }
+    qsort(sample, (size_t)ns, sizeof(uint64_t), cmp_u64);
+  }
+  /* 2. Splitter Selection: split[i-1] = the (i*s)-th smallest, 1 <= i <= p-1 */
+  for (int i = 1; i <= p - 1; ++i) split[i - 1] = n > 0 ? sample[(int64_t)i * s - 1] : 0;
+  /* 3. Split input keys: destinations, their counts, then the count-sort by destination */
+  for (int64_t i = 0; i < n; ++i) {
+    const uint64_t k = get_key(keys, i, kb);
+    uint32_t j = 0;
+    while ((int)j < p - 1 && split[j] < k) ++j;  /* splitters ascending: count those below k */
+    dest[i] = j;
+    ++count[j + 1];
+  }
+  for (int j = 0; j < p; ++j) count[j + 1] += count[j]; /* count[j] = first slot of j */
+  {
+    int64_t *next = malloc(sizeof(int64_t) * (size_t)p);
+    if (!next) {
+      rc = 2;
+      goto done;
+    }
+    memcpy(next, count, sizeof(int64_t) * (size_t)p);
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t o = next[dest[i]]++;
+      put_key(kout, o, get_key(keys, i, kb), kb);
+      if (vb) copy_val(vout, o, vals, i, vb);
+    }
+    free(next);
+  }
+  /* 4. LocalSorting of each destination sequence (SR4), then the concatenation */
+  rc = oracle_segmented_sort(kout, vout, count, p, key_bits, val_bits, 8);
+  if (rc) goto done;
+  memcpy(keys, kout, (size_t)n * kb);
+  if (vb) memcpy(vals, vout, (size_t)n * vb);
+  if (bucket_counts)
+    for (int j = 0; j < p; ++j) bucket_counts[j] = (uint32_t)(count[j + 1] - count[j]);
+  if (splitters)
+    for (int i = 0; i < p - 1; ++i) splitters[i] = split[i];
+done:
+  free(sample);
+  free(split);
+  free(count);
+  free(dest);
+  free(kout);
+  free(vout);
+  return rc;
+}

@@ -34,6 +34,14 @@ int oracle_radix_sort(void *keys, void *vals, int64_t n, int key_bits, int val_b
 int oracle_segmented_sort(void *keys, void *vals, const int64_t *offsets, int64_t num_segments,
                           int key_bits, int val_bits, int radix_bits);
 
+/* GVR sample sort (Algorithm 3): sample s*p - 1 keys at SplitMix64 positions
+ * (stream 30 of seed), splitters = the (i*s)-th smallest sampled keys, stable
+ * count-sort by destination (number of splitters below the key), SR4 on each
+ * destination sequence. Sorts in place; bucket_counts (p entries) and
+ * splitters (p - 1 entries) receive the intermediates when not NULL. */
+int oracle_gvr_sort(void *keys, void *vals, int64_t n, int key_bits, int val_bits, int p, int s,
+                    uint64_t seed, uint32_t *bucket_counts, uint64_t *splitters);
+
 #ifdef __cplusplus
 }
 #endif

@@ -98,6 +98,39 @@ def sort_segmented(keys, offsets, vals=None, radix_bits: int = 0, stream=None):
     return keys if vals is None else (keys, vals)
 
 
+def sample_sort(keys, vals=None, buckets: int = 256, oversample: int = 16, seed: int = 1,
+                bucket_counts=None, stream=None):
+    """The paper's GVR sample sort (Algorithm 3), in place: s*p - 1 sampled keys
+    sorted, p - 1 splitters, one stable count-sort round by bucket, then the
+    buckets sorted independently. bucket_counts: optional CUDA uint32 tensor of
+    at least `buckets` entries that receives the bucket sizes."""
+    _dev(keys, "keys")
+    vb, vptr = 0, None
+    if vals is not None:
+        _dev(vals, "vals")
+        if vals.numel() != keys.numel():
+            raise ValueError("keys and vals differ in length")
+        vb, vptr = _bits(vals), vals.data_ptr()
+    cptr = None
+    if bucket_counts is not None:
+        _dev(bucket_counts, "bucket_counts")
+        if _bits(bucket_counts) != 32 or bucket_counts.numel() < buckets:
+            raise ValueError("bucket_counts must be uint32 with at least `buckets` entries")
+        cptr = bucket_counts.data_ptr()
+    check(load().isort_sample_sort(keys.data_ptr(), vptr, keys.numel(), _bits(keys), vb, buckets,
+                                   oversample, seed, cptr, _stream(stream)), "isort_sample_sort")
+    return keys if vals is None else (keys, vals)
+
+
+def sample_sort_workspace_size(n: int, key_bits: int = 32, val_bits: int = 0, buckets: int = 256,
+                               oversample: int = 16) -> int:
+    out = ctypes.c_size_t(0)
+    check(load().isort_sample_sort_workspace_size(n, key_bits, val_bits, buckets, oversample,
+                                                  ctypes.byref(out)),
+          "isort_sample_sort_workspace_size")
+    return out.value
+
+
 def workspace_size(n: int, key_bits: int = 32, val_bits: int = 0, radix_bits: int = 0) -> int:
     out = ctypes.c_size_t(0)
     check(load().isort_workspace_size(n, key_bits, val_bits, radix_bits, ctypes.byref(out)),

@@ -48,6 +48,8 @@ def _sig(lib):
         "isort_tune_segmented": [i32, i32, i64],
         "isort_tune_segmented_network": [i32, i32, i32],
         "isort_segmented_workspace_size": [i64, i64, i32, i32, ctypes.POINTER(sz)],
+        "isort_sample_sort": [vp, vp, i64, i32, i32, i32, i32, ctypes.c_uint64, vp, vp],
+        "isort_sample_sort_workspace_size": [i64, i32, i32, i32, i32, ctypes.POINTER(sz)],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)

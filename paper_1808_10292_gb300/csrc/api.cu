@@ -249,6 +249,86 @@ void timer_end(KernelTimer* t, cudaStream_t st) {
 
 }  // namespace isort
 
+namespace {
+
+// Segmented-sort arguments over workspace b laid out by L (caller holds g_mu).
+SegArgs seg_args(const SegConfig& c, const SegLayout& L, char* b, void* keys, void* vals,
+                 const int64_t* offsets, int64_t nseg, int64_t total) {
+  SegArgs a;
+  a.keys = keys;
+  a.vals = vals;
+  a.alt_keys = b + L.alt_k;
+  a.alt_vals = vals ? b + L.alt_v : nullptr;
+  a.offsets = offsets;
+  a.nseg = nseg;
+  a.total = total;
+  a.btn_max = seg_btn_max(c);
+  {
+    auto it = g_seg_network.find({c.key_bits, c.val_bits});
+    a.network = it == g_seg_network.end() ? ISORT_NET_BTN : it->second;
+  }
+  a.max_tiles = L.max_tiles;
+  a.lists = reinterpret_cast<int32_t*>(b + L.lists);
+  a.cnt = reinterpret_cast<uint32_t*>(b + L.cnt);
+  a.slot_first = reinterpret_cast<uint32_t*>(b + L.slot_first);
+  a.tile_slot = reinterpret_cast<int32_t*>(b + L.tile_slot);
+  a.seg_hist = reinterpret_cast<uint32_t*>(b + L.seg_hist);
+  a.seg_base = reinterpret_cast<uint32_t*>(b + L.seg_base);
+  a.status[0] = reinterpret_cast<uint32_t*>(b + L.status0);
+  a.status[1] = reinterpret_cast<uint32_t*>(b + L.status1);
+  a.err = reinterpret_cast<uint32_t*>(b + L.err);
+  a.spin_limit = g_spin_limit;
+  a.num_sms = num_sms();
+  a.timer = nullptr;
+  if (g_timing) {
+    if (!g_timer.ready) {
+      for (int i = 0; i < 2 * KernelTimer::kMax; ++i) cudaEventCreate(&g_timer.ev[i]);
+      g_timer.ready = true;
+    }
+    g_timer.count = 0;
+    a.timer = &g_timer;
+  }
+  return a;
+}
+
+// Sample-sort workspace: the segmented-sort layout of the p buckets (error word
+// at offset 0), then the bucketed copy of the input and the split round's arrays.
+struct GvrLayout {
+  SegLayout seg;
+  size_t out_k, out_v, split, hist, base, skip, counter, status, offsets, total;
+};
+
+GvrLayout gvr_layout(const SegConfig& c, int64_t n, int buckets) {
+  GvrLayout G;
+  G.seg = seg_layout(c, buckets, n, seg_btn_max(c));
+  const int64_t tiles = (n + gvr_tile(c.key_bits, c.val_bits) - 1) / gvr_tile(c.key_bits, c.val_bits);
+  size_t off = G.seg.total;
+  G.out_k = off;    off = align256(off + (size_t)n * (c.key_bits / 8));
+  G.out_v = off;    off = align256(off + (size_t)n * (c.val_bits / 8));
+  G.split = off;    off = align256(off + 255 * sizeof(uint64_t));
+  G.hist = off;     off = align256(off + 256 * sizeof(uint32_t));
+  G.base = off;     off = align256(off + 256 * sizeof(uint32_t));
+  G.skip = off;     off = align256(off + sizeof(uint32_t));
+  G.counter = off;  off = align256(off + sizeof(uint32_t));
+  G.status = off;   off = align256(off + sizeof(uint32_t) * 256 * (size_t)tiles);
+  G.offsets = off;  off = align256(off + sizeof(int64_t) * (size_t)(buckets + 1));
+  G.total = off;
+  return G;
+}
+
+isort_status check_sample_args(int64_t n, int key_bits, int val_bits, bool pairs, int buckets,
+                               int oversample) {
+  isort_status s = check_widths(key_bits, val_bits, pairs);
+  if (s != ISORT_OK) return s;
+  if (n < 0 || buckets < 1 || buckets > 256 || oversample < 1 ||
+      (int64_t)buckets * oversample > 4096)
+    return ISORT_EINVAL;
+  if (n > (int64_t(1) << 30)) return ISORT_EUNSUPPORTED;
+  return ISORT_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 isort_status isort_keys(void* keys, int64_t n, int key_bits, int radix_bits, void* stream) {
@@ -277,6 +357,71 @@ isort_status isort_pairs(void* keys, void* vals, int64_t n, int key_bits, int va
   return run_lsd(keys, vals, n, key_bits, val_bits, rb, static_cast<cudaStream_t>(stream));
 }
 
+isort_status isort_sample_sort(void* keys, void* vals, int64_t n, int key_bits, int val_bits,
+                               int buckets, int oversample, uint64_t seed,
+                               uint32_t* bucket_counts, void* stream) {
+  if (!vals) val_bits = 0;
+  isort_status s = check_sample_args(n, key_bits, val_bits, vals != nullptr, buckets, oversample);
+  if (s != ISORT_OK) return s;
+  if (n == 0) return ISORT_OK;
+  if (!keys || !aligned(keys, key_bits / 8) || (vals && !aligned(vals, val_bits / 8)) ||
+      (bucket_counts && !aligned(bucket_counts, 4)))
+    return ISORT_EINVAL;
+  const SegConfig* c = key_bits == 32 ? seg_config_k32(val_bits) : seg_config_k64(val_bits);
+  if (!c) return ISORT_EUNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lock(g_mu);
+  const GvrLayout G = gvr_layout(*c, n, buckets);
+  void* ws = nullptr;
+  if ((s = acquire(st, G.total, &ws)) != ISORT_OK) return s;
+  char* b = static_cast<char*>(ws);
+  SegArgs sa = seg_args(*c, G.seg, b, b + G.out_k, vals ? b + G.out_v : nullptr,
+                        reinterpret_cast<const int64_t*>(b + G.offsets), buckets, n);
+  GvrArgs g;
+  g.keys = keys;
+  g.vals = vals;
+  g.out_keys = b + G.out_k;
+  g.out_vals = vals ? b + G.out_v : nullptr;
+  g.n = n;
+  g.buckets = buckets;
+  g.oversample = oversample;
+  g.seed = seed;
+  g.split = b + G.split;
+  g.hist = reinterpret_cast<uint32_t*>(b + G.hist);
+  g.base = reinterpret_cast<uint32_t*>(b + G.base);
+  g.skip = reinterpret_cast<uint32_t*>(b + G.skip);
+  g.counter = reinterpret_cast<uint32_t*>(b + G.counter);
+  g.status = reinterpret_cast<uint32_t*>(b + G.status);
+  g.offsets = reinterpret_cast<int64_t*>(b + G.offsets);
+  g.counts_out = bucket_counts;
+  g.err = sa.err;
+  g.spin_limit = g_spin_limit;
+  g.num_sms = sa.num_sms;
+  g.timer = sa.timer;
+  if (gvr_split_launch(key_bits, val_bits, g, st) != cudaSuccess) return ISORT_ECUDA;
+  // the buckets, each sorted independently, in place in the workspace copy
+  if (c->launch(sa, st) != cudaSuccess) return ISORT_ECUDA;
+  if (cudaMemcpyAsync(keys, g.out_keys, (size_t)n * (key_bits / 8), cudaMemcpyDeviceToDevice,
+                      st) != cudaSuccess)
+    return ISORT_ECUDA;
+  if (vals && cudaMemcpyAsync(vals, g.out_vals, (size_t)n * (val_bits / 8),
+                              cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return ISORT_ECUDA;
+  return ISORT_OK;
+}
+
+isort_status isort_sample_sort_workspace_size(int64_t n, int key_bits, int val_bits, int buckets,
+                                              int oversample, size_t* bytes) {
+  if (!bytes) return ISORT_EINVAL;
+  isort_status s = check_sample_args(n, key_bits, val_bits, val_bits != 0, buckets, oversample);
+  if (s != ISORT_OK) return s;
+  const SegConfig* c = key_bits == 32 ? seg_config_k32(val_bits) : seg_config_k64(val_bits);
+  if (!c) return ISORT_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_mu);
+  *bytes = gvr_layout(*c, n, buckets).total;
+  return ISORT_OK;
+}
+
 isort_status isort_segmented(void* keys, void* vals, const int64_t* offsets, int64_t num_segments,
                              int64_t total_keys, int key_bits, int val_bits, int radix_bits,
                              void* stream) {
@@ -297,41 +442,8 @@ isort_status isort_segmented(void* keys, void* vals, const int64_t* offsets, int
   SegLayout L = seg_layout(*c, num_segments, total_keys, seg_btn_max(*c));
   void* ws = nullptr;
   if ((s = acquire(st, L.total, &ws)) != ISORT_OK) return s;
-  char* b = static_cast<char*>(ws);
-  SegArgs a;
-  a.keys = keys;
-  a.vals = vals;
-  a.alt_keys = b + L.alt_k;
-  a.alt_vals = vals ? b + L.alt_v : nullptr;
-  a.offsets = offsets;
-  a.nseg = num_segments;
-  a.total = total_keys;
-  a.btn_max = seg_btn_max(*c);
-  {
-    auto it = g_seg_network.find({key_bits, c->val_bits});
-    a.network = it == g_seg_network.end() ? ISORT_NET_BTN : it->second;
-  }
-  a.max_tiles = L.max_tiles;
-  a.lists = reinterpret_cast<int32_t*>(b + L.lists);
-  a.cnt = reinterpret_cast<uint32_t*>(b + L.cnt);
-  a.slot_first = reinterpret_cast<uint32_t*>(b + L.slot_first);
-  a.tile_slot = reinterpret_cast<int32_t*>(b + L.tile_slot);
-  a.seg_hist = reinterpret_cast<uint32_t*>(b + L.seg_hist);
-  a.seg_base = reinterpret_cast<uint32_t*>(b + L.seg_base);
-  a.status[0] = reinterpret_cast<uint32_t*>(b + L.status0);
-  a.status[1] = reinterpret_cast<uint32_t*>(b + L.status1);
-  a.err = reinterpret_cast<uint32_t*>(b + L.err);
-  a.spin_limit = g_spin_limit;
-  a.num_sms = num_sms();
-  a.timer = nullptr;
-  if (g_timing) {
-    if (!g_timer.ready) {
-      for (int i = 0; i < 2 * KernelTimer::kMax; ++i) cudaEventCreate(&g_timer.ev[i]);
-      g_timer.ready = true;
-    }
-    g_timer.count = 0;
-    a.timer = &g_timer;
-  }
+  SegArgs a = seg_args(*c, L, static_cast<char*>(ws), keys, vals, offsets, num_segments,
+                       total_keys);
   return c->launch(a, st) == cudaSuccess ? ISORT_OK : ISORT_ECUDA;
 }
 

@@ -109,6 +109,34 @@ struct SegConfig {
   cudaError_t (*launch)(const SegArgs&, cudaStream_t);
 };
 
+// The splitter partition round of the sample sort (sample_sort.cu): sample,
+// splitters, bucket counts and offsets, and one count-sort round by bucket
+// from keys/vals into out_keys/out_vals.
+struct GvrArgs {
+  const void* keys;      // caller's keys (input of the round)
+  const void* vals;      // caller's payloads or nullptr
+  void* out_keys;        // workspace: keys grouped by bucket
+  void* out_vals;        // workspace: payloads (when vals != nullptr)
+  int64_t n;
+  int buckets;           // p, 1..256
+  int oversample;        // s, p * s <= 4096
+  uint64_t seed;
+  void* split;           // [255] keys: splitters, then padding
+  uint32_t* hist;        // [256] bucket counts
+  uint32_t* base;        // [256] bucket bases
+  uint32_t* skip;        // [1]
+  uint32_t* counter;     // [1] tile-id counter
+  uint32_t* status;      // [tiles][256] look-back words
+  int64_t* offsets;      // [buckets + 1] bucket offsets for the segmented sort
+  uint32_t* counts_out;  // [buckets] caller's copy of the bucket counts, or nullptr
+  uint32_t* err;
+  uint32_t spin_limit;
+  int num_sms;
+  KernelTimer* timer;
+};
+int64_t gvr_tile(int key_bits, int val_bits);  // keys per tile of the round
+cudaError_t gvr_split_launch(int key_bits, int val_bits, const GvrArgs& a, cudaStream_t st);
+
 // Segmented sort families (segmented_k32.cu, segmented_k64.cu).
 const SegConfig* seg_config_k32(int val_bits);
 const SegConfig* seg_config_k64(int val_bits);

@@ -191,6 +191,18 @@ struct PassParams {
   int64_t prefetch_tiles;     // L2-prefetch the input of the tile this many ids ahead (0: off)
 };
 
+// The digit of a key in one round: bits [shift, shift + width) of the key. The
+// early-counts tile functions take the digit as a function object, so a round
+// can also distribute keys by another rule (a splitter bucket, for instance).
+struct RadixDigit {
+  int shift;
+  uint32_t mask;
+  template <typename K>
+  __device__ __forceinline__ uint32_t operator()(K k) const {
+    return digit_of(k, shift, mask);
+  }
+};
+
 // Keep DRAM busy while tiles are ranking: one thread of the CTA asks the copy
 // engine to bring the input of a tile about one wave ahead into L2, so that
 // tile's loads hit L2. Skipped when the range is not 16-byte aligned.
@@ -399,11 +411,11 @@ __device__ __forceinline__ void tile_reorder(const K (&key)[KPT], uint32_t (&ran
 // Write out: consecutive threads take consecutive tile slots, so each digit's
 // run lands on consecutive global addresses; every index is bounds-checked.
 // With payloads the staging area is reused for them (contains __syncthreads).
-template <typename K, typename V, int THREADS, int KPT, bool FULL>
+template <typename K, typename V, int THREADS, int KPT, bool FULL, typename DS>
 __device__ __forceinline__ void tile_scatter(const K* s_keys, V* s_vals, const uint32_t* s_adj,
                                              const V (&val)[HasVal<V>::value ? KPT : 1],
-                                             const uint32_t (&rank2)[(KPT + 1) / 2], int shift,
-                                             uint32_t mask, int tile_n, int wofs, K* kout,
+                                             const uint32_t (&rank2)[(KPT + 1) / 2],
+                                             const DS& dig, int tile_n, int wofs, K* kout,
                                              V* vout, uint32_t bound, uint32_t* err) {
   constexpr bool HV = HasVal<V>::value;
   const int tid = threadIdx.x;
@@ -413,7 +425,7 @@ __device__ __forceinline__ void tile_scatter(const K* s_keys, V* s_vals, const u
     const int j = k * THREADS + tid;
     if (FULL || j < tile_n) {
       const K kk = s_keys[j];
-      const uint32_t g = s_adj[digit_of(kk, shift, mask)] + (uint32_t)j;
+      const uint32_t g = s_adj[dig(kk)] + (uint32_t)j;
       if (g < bound)
         kout[g] = kk;
       else
@@ -438,12 +450,12 @@ __device__ __forceinline__ void tile_scatter(const K* s_keys, V* s_vals, const u
 
 // Early counts: each warp counts the digits of its keys into its private row of
 // s_wcnt (one shared atomic add per key, order irrelevant).
-template <typename K, int R, int KPT, bool FULL>
-__device__ __forceinline__ void tile_count(const K (&key)[KPT], int shift, uint32_t mask,
-                                           int tile_n, int wofs, uint32_t* my) {
+template <typename K, int R, int KPT, bool FULL, typename DS>
+__device__ __forceinline__ void tile_count(const K (&key)[KPT], const DS& dig, int tile_n,
+                                           int wofs, uint32_t* my) {
 #pragma unroll
   for (int i = 0; i < KPT; ++i)
-    if (FULL || wofs + i * 32 < tile_n) atomicAdd(&my[digit_of(key[i], shift, mask)], 1u);
+    if (FULL || wofs + i * 32 < tile_n) atomicAdd(&my[dig(key[i])], 1u);
 }
 
 // Rank and reorder in one sweep: the warp's counters already hold, per digit,
@@ -451,9 +463,9 @@ __device__ __forceinline__ void tile_count(const K (&key)[KPT], int shift, uint3
 // key (peer masks, as in tile_rank) is its final tile position and the key is
 // written straight into the staging area. The masks live in a separate area
 // (the staging area is being filled). rank2 receives the positions.
-template <typename K, int R, int KPT, int MASK_BUFS, bool FULL>
-__device__ __forceinline__ void tile_rank_place(const K (&key)[KPT], int shift, uint32_t mask,
-                                                int tile_n, int wofs, uint32_t* my,
+template <typename K, int R, int KPT, int MASK_BUFS, bool FULL, typename DS>
+__device__ __forceinline__ void tile_rank_place(const K (&key)[KPT], const DS& dig, int tile_n,
+                                                int wofs, uint32_t* my,
                                                 uint32_t* mm, K* s_keys,
                                                 uint32_t (&rank2)[(KPT + 1) / 2]) {
   static_assert(MASK_BUFS == 3, "row r marks slot array r mod 3");
@@ -466,7 +478,7 @@ __device__ __forceinline__ void tile_rank_place(const K (&key)[KPT], int shift, 
   // slot of row i-1 is cleared in step i before the barrier that precedes any
   // mark of row i+2 (its next user), after every lane has read it (all lanes
   // passed the barrier of row i).
-  uint32_t d = digit_of(key[0], shift, mask);
+  uint32_t d = dig(key[0]);
   uint32_t* slot = mm + d;
   if (valid_row(0)) atomicOr(slot, bit);
   __syncwarp();
@@ -483,7 +495,7 @@ __device__ __forceinline__ void tile_rank_place(const K (&key)[KPT], int shift, 
     uint32_t d_next = 0, peers_next = 0;
     uint32_t* slot_next = mm;
     if (i + 1 < KPT) {
-      d_next = digit_of(key[i + 1], shift, mask);
+      d_next = dig(key[i + 1]);
       slot_next = mm + ((i + 1) % MASK_BUFS) * R + d_next;
       if (valid_row(i + 1)) atomicOr(slot_next, bit);
       __syncwarp();
@@ -515,13 +527,15 @@ struct EarlyShape {
 // One tile of one count-sort round, early-counts form: count, publish the
 // tile's counts, scan, rank straight into the reordered tile, look back,
 // publish the inclusive counts, write out.
-template <typename K, typename V, int BITS, int THREADS, int KPT, bool FULL>
+// dig: the key -> digit rule of this round (RadixDigit for a radix round).
+template <typename K, typename V, int BITS, int THREADS, int KPT, bool FULL,
+          typename DS = RadixDigit>
 __device__ __forceinline__ void onesweep_tile_early(const PassParams& p, uint32_t tile, bool first,
                                                     int64_t tile_base, int tile_n,
                                                     const K* __restrict__ kin,
                                                     K* __restrict__ kout, const V* vin, V* vout,
                                                     const uint32_t* base, uint32_t bound,
-                                                    unsigned char* smem) {
+                                                    unsigned char* smem, const DS& dig) {
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
   using E = EarlyShape<K, V, BITS, THREADS, KPT>;
   constexpr int R = S::R, WARPS = S::WARPS, DPT = S::DPT;
@@ -539,7 +553,7 @@ __device__ __forceinline__ void onesweep_tile_early(const PassParams& p, uint32_
   K key[KPT];
   V val[HV ? KPT : 1];
   tile_load<K, V, KPT, FULL>(kin, vin, tile_base, tile_n, wofs, key, val);
-  tile_count<K, R, KPT, FULL>(key, p.shift, p.mask, tile_n, wofs, s_wcnt + warp * R);
+  tile_count<K, R, KPT, FULL>(key, dig, tile_n, wofs, s_wcnt + warp * R);
   __syncthreads();
   if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 1] = globaltimer();
 
@@ -570,7 +584,7 @@ __device__ __forceinline__ void onesweep_tile_early(const PassParams& p, uint32_
   }
   __syncthreads();
   uint32_t rank2[(KPT + 1) / 2];
-  tile_rank_place<K, R, KPT, S::MASK_BUFS, FULL>(key, p.shift, p.mask, tile_n, wofs,
+  tile_rank_place<K, R, KPT, S::MASK_BUFS, FULL>(key, dig, tile_n, wofs,
                                                  s_wcnt + warp * R,
                                                  s_masks + warp * S::MASK_BUFS * R, s_keys,
                                                  rank2);
@@ -597,8 +611,8 @@ __device__ __forceinline__ void onesweep_tile_early(const PassParams& p, uint32_
     p.trace[(size_t)tile * 8 + 3] = globaltimer();
     p.trace[(size_t)tile * 8 + 4] = globaltimer();
   }
-  tile_scatter<K, V, THREADS, KPT, FULL>(s_keys, s_vals, s_adj, val, rank2, p.shift, p.mask,
-                                         tile_n, wofs, kout, vout, bound, p.err);
+  tile_scatter<K, V, THREADS, KPT, FULL>(s_keys, s_vals, s_adj, val, rank2, dig, tile_n, wofs,
+                                         kout, vout, bound, p.err);
   if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 5] = globaltimer();
 }
 
@@ -682,8 +696,9 @@ __device__ __forceinline__ void onesweep_tile(const PassParams& p, uint32_t tile
   __syncthreads();
   if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 4] = globaltimer();
 
-  tile_scatter<K, V, THREADS, KPT, FULL>(s_keys, s_vals, s_adj, val, rank2, p.shift, p.mask,
-                                         tile_n, wofs, kout, vout, bound, p.err);
+  tile_scatter<K, V, THREADS, KPT, FULL>(s_keys, s_vals, s_adj, val, rank2,
+                                         RadixDigit{p.shift, p.mask}, tile_n, wofs, kout, vout,
+                                         bound, p.err);
   if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 5] = globaltimer();
 }
 
@@ -734,11 +749,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
     if (tile_n == TILE)
       onesweep_tile_early<K, V, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n,
                                                           kin, kout, vin, vout, p.base,
-                                                          (uint32_t)p.n, smem);
+                                                          (uint32_t)p.n, smem,
+                                                          RadixDigit{p.shift, p.mask});
     else
       onesweep_tile_early<K, V, BITS, THREADS, KPT, false>(p, tile, tile == 0, tile_base,
                                                            tile_n, kin, kout, vin, vout, p.base,
-                                                           (uint32_t)p.n, smem);
+                                                           (uint32_t)p.n, smem,
+                                                           RadixDigit{p.shift, p.mask});
   } else {
     if (tile_n == TILE)
       onesweep_tile<K, V, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n, kin,
@@ -859,8 +876,9 @@ __device__ __forceinline__ void onesweep_tile_tma(const PassParams& p, uint32_t 
   }
   __syncthreads();
   const NoVal nv[1] = {};
-  tile_scatter<K, NoVal, THREADS, KPT, FULL>(s_keys, nullptr, s_adj, nv, rank2, p.shift, p.mask,
-                                             tile_n, wofs, kout, nullptr, (uint32_t)p.n, p.err);
+  tile_scatter<K, NoVal, THREADS, KPT, FULL>(s_keys, nullptr, s_adj, nv, rank2,
+                                             RadixDigit{p.shift, p.mask}, tile_n, wofs, kout,
+                                             nullptr, (uint32_t)p.n, p.err);
 }
 
 template <typename K, int BITS, int THREADS, int KPT, int MINB>
@@ -1047,8 +1065,9 @@ __device__ __forceinline__ void onesweep_cluster_tile(const PassParams& p, uint3
     }
   }
   __syncthreads();
-  tile_scatter<K, V, THREADS, KPT, FULL>(s_keys, s_vals, s_adj, val, rank2, p.shift, p.mask,
-                                         tile_n, wofs, kout, vout, (uint32_t)p.n, p.err);
+  tile_scatter<K, V, THREADS, KPT, FULL>(s_keys, s_vals, s_adj, val, rank2,
+                                         RadixDigit{p.shift, p.mask}, tile_n, wofs, kout, vout,
+                                         (uint32_t)p.n, p.err);
 }
 
 template <typename K, typename V, int BITS, int THREADS, int KPT, int CL, int MINB>

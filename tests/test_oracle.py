@@ -162,6 +162,40 @@ def test_bad_arguments_rejected():
     assert oracle.num_passes(32, 16) == 2 and oracle.num_passes(64, 8) == 8
 
 
+# ---- GVR sample sort (Algorithm 3) ------------------------------------------
+def gvr_definition(k, p, s, seed):
+    """Splitters and bucket sizes recomputed with numpy from the algorithm's
+    definitions: sample positions from the inputs module's SplitMix64 (stream
+    30), splitters = the (i*s)-th smallest sampled keys, bucket j = the keys
+    above splitter j-1 and at most splitter j."""
+    n = k.size
+    if n == 0:
+        return np.zeros(max(p - 1, 0), np.uint64), np.zeros(p, np.int64)
+    d = inputs.draws_u64(seed, 30, 0, s * p - 1)
+    pos = ((d >> np.uint64(32)) * np.uint64(n)) >> np.uint64(32)
+    sample = np.sort(k[pos.astype(np.int64)].astype(np.uint64))
+    split = sample[np.arange(1, p) * s - 1]
+    srt = np.sort(k).astype(np.uint64)
+    edges = np.concatenate([[0], np.searchsorted(srt, split, side="right"), [n]])
+    return split, np.diff(edges)
+
+
+@pytest.mark.parametrize("key_bits", [32, 64])
+@pytest.mark.parametrize("dist", inputs.DISTS)
+@pytest.mark.parametrize("p,s", [(1, 1), (2, 3), (16, 8), (256, 16)])
+def test_gvr_sorts_stably_and_its_intermediates_follow_the_definition(key_bits, dist, p, s):
+    for n in (0, 1, 5, 1000, 20_011):
+        k = inputs.keys(n, key_bits, dist, seed=n + 7)
+        v = inputs.iota(n)
+        ks, vs, counts, split = oracle.gvr_sort(k, v, buckets=p, oversample=s, seed=9)
+        order = np.argsort(k, kind="stable")  # a library routine: the stable order
+        assert np.array_equal(ks, k[order]) and np.array_equal(vs, v[order]), n
+        want_split, want_counts = gvr_definition(k, p, s, 9)
+        assert np.array_equal(counts.astype(np.int64), want_counts), n
+        if n:
+            assert np.array_equal(split, want_split), n
+
+
 # ---- planted mistakes -------------------------------------------------------
 # Each mutant is a textual edit of oracle.c that a plausible bug would make. None
 # writes out of bounds (every output slot stays in [0, n)), so running it is safe.
@@ -178,6 +212,11 @@ MUTANTS = {
                           "if (vb) copy_val(vals_out, i, vals_in, i, vb);"),
     "narrow_mask": ("const uint64_t mask = (uint64_t)r - 1;",
                     "const uint64_t mask = ((uint64_t)r - 1) >> 1;"),
+    "gvr_bucket_takes_equal_keys_up": ("split[j] < k) ++j;", "split[j] <= k) ++j;"),
+    "gvr_splitter_rank_off_by_one": ("sample[(int64_t)i * s - 1]", "sample[(int64_t)i * s]"),
+    "gvr_split_round_backwards": (
+        "for (int64_t i = 0; i < n; ++i) {\n      const int64_t o = next[dest[i]]++;",
+        "for (int64_t i = n - 1; i >= 0; --i) {\n      const int64_t o = next[dest[i]]++;"),
 }
 
 
@@ -195,6 +234,20 @@ def _pins_pass(lib):
                 bk, bv = brute_force_stable(k, v)
                 if not (np.array_equal(ks, bk) and np.array_equal(vs, bv)):
                     return False
+    for dist in ("uniform", "u16", "and4", "equal"):
+        k = inputs.keys(3000, 32, dist, seed=4)
+        v = inputs.iota(3000)
+        try:
+            ks, vs, counts, split = oracle.gvr_sort(k, v, buckets=16, oversample=4, seed=7,
+                                                    lib=lib)
+        except RuntimeError:
+            return False
+        order = np.argsort(k, kind="stable")
+        want_split, want_counts = gvr_definition(k, 16, 4, 7)
+        if not (np.array_equal(ks, k[order]) and np.array_equal(vs, v[order]) and
+                np.array_equal(counts.astype(np.int64), want_counts) and
+                np.array_equal(split, want_split)):
+            return False
     for c in load_golden():
         dt = np.uint32 if c["key_bits"] == 32 else np.uint64
         ko, vo = oracle.count_sort_round(np.array(c["keys_in"], dt), c["shift"], c["bits"],
