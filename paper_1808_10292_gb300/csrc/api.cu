@@ -295,7 +295,7 @@ SegArgs seg_args(const SegConfig& c, const SegLayout& L, char* b, void* keys, vo
 // at offset 0), then the bucketed copy of the input and the split round's arrays.
 struct GvrLayout {
   SegLayout seg;
-  size_t out_k, out_v, split, hist, base, skip, counter, status, offsets, total;
+  size_t out_k, out_v, split, cell, hist, base, skip, counter, status, offsets, total;
 };
 
 GvrLayout gvr_layout(const SegConfig& c, int64_t n, int buckets) {
@@ -306,6 +306,7 @@ GvrLayout gvr_layout(const SegConfig& c, int64_t n, int buckets) {
   G.out_k = off;    off = align256(off + (size_t)n * (c.key_bits / 8));
   G.out_v = off;    off = align256(off + (size_t)n * (c.val_bits / 8));
   G.split = off;    off = align256(off + 255 * sizeof(uint64_t));
+  G.cell = off;     off = align256(off + 1024 * sizeof(uint16_t));
   G.hist = off;     off = align256(off + 256 * sizeof(uint32_t));
   G.base = off;     off = align256(off + 256 * sizeof(uint32_t));
   G.skip = off;     off = align256(off + sizeof(uint32_t));
@@ -387,6 +388,7 @@ isort_status isort_sample_sort(void* keys, void* vals, int64_t n, int key_bits, 
   g.oversample = oversample;
   g.seed = seed;
   g.split = b + G.split;
+  g.cell = b + G.cell;
   g.hist = reinterpret_cast<uint32_t*>(b + G.hist);
   g.base = reinterpret_cast<uint32_t*>(b + G.base);
   g.skip = reinterpret_cast<uint32_t*>(b + G.skip);

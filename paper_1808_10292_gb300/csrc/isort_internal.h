@@ -122,6 +122,7 @@ struct GvrArgs {
   int oversample;        // s, p * s <= 4096
   uint64_t seed;
   void* split;           // [255] keys: splitters, then padding
+  void* cell;            // [1024] uint16: bucket range of each top-10-bit key cell
   uint32_t* hist;        // [256] bucket counts
   uint32_t* base;        // [256] bucket bases
   uint32_t* skip;        // [1]

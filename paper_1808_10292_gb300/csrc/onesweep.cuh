@@ -194,11 +194,28 @@ struct PassParams {
 // The digit of a key in one round: bits [shift, shift + width) of the key. The
 // early-counts tile functions take the digit as a function object, so a round
 // can also distribute keys by another rule (a splitter bucket, for instance).
+// The tile code asks for digits through four calls, so a rule whose digits are
+// costly can compute each once (prepare) and hand back the stored value:
+//   prepare(key)  after the tile's keys are loaded into registers;
+//   of(k, i)      the digit of this thread's key i (k = key[i]);
+//   keep(pos, d)  the key with digit d was placed at tile slot pos;
+//   staged(k, j)  the digit of the key at tile slot j (k = that key).
 struct RadixDigit {
   int shift;
   uint32_t mask;
   template <typename K>
   __device__ __forceinline__ uint32_t operator()(K k) const {
+    return digit_of(k, shift, mask);
+  }
+  template <typename K, int KPT>
+  __device__ __forceinline__ void prepare(const K (&)[KPT]) {}
+  template <typename K>
+  __device__ __forceinline__ uint32_t of(K k, int) const {
+    return digit_of(k, shift, mask);
+  }
+  __device__ __forceinline__ void keep(uint32_t, uint32_t) const {}
+  template <typename K>
+  __device__ __forceinline__ uint32_t staged(K k, int) const {
     return digit_of(k, shift, mask);
   }
 };
@@ -425,7 +442,7 @@ __device__ __forceinline__ void tile_scatter(const K* s_keys, V* s_vals, const u
     const int j = k * THREADS + tid;
     if (FULL || j < tile_n) {
       const K kk = s_keys[j];
-      const uint32_t g = s_adj[dig(kk)] + (uint32_t)j;
+      const uint32_t g = s_adj[dig.staged(kk, j)] + (uint32_t)j;
       if (g < bound)
         kout[g] = kk;
       else
@@ -455,7 +472,7 @@ __device__ __forceinline__ void tile_count(const K (&key)[KPT], const DS& dig, i
                                            int wofs, uint32_t* my) {
 #pragma unroll
   for (int i = 0; i < KPT; ++i)
-    if (FULL || wofs + i * 32 < tile_n) atomicAdd(&my[dig(key[i])], 1u);
+    if (FULL || wofs + i * 32 < tile_n) atomicAdd(&my[dig.of(key[i], i)], 1u);
 }
 
 // Rank and reorder in one sweep: the warp's counters already hold, per digit,
@@ -478,7 +495,7 @@ __device__ __forceinline__ void tile_rank_place(const K (&key)[KPT], const DS& d
   // slot of row i-1 is cleared in step i before the barrier that precedes any
   // mark of row i+2 (its next user), after every lane has read it (all lanes
   // passed the barrier of row i).
-  uint32_t d = dig(key[0]);
+  uint32_t d = dig.of(key[0], 0);
   uint32_t* slot = mm + d;
   if (valid_row(0)) atomicOr(slot, bit);
   __syncwarp();
@@ -495,7 +512,7 @@ __device__ __forceinline__ void tile_rank_place(const K (&key)[KPT], const DS& d
     uint32_t d_next = 0, peers_next = 0;
     uint32_t* slot_next = mm;
     if (i + 1 < KPT) {
-      d_next = dig(key[i + 1]);
+      d_next = dig.of(key[i + 1], i + 1);
       slot_next = mm + ((i + 1) % MASK_BUFS) * R + d_next;
       if (valid_row(i + 1)) atomicOr(slot_next, bit);
       __syncwarp();
@@ -504,7 +521,10 @@ __device__ __forceinline__ void tile_rank_place(const K (&key)[KPT], const DS& d
     const uint32_t after =
         __shfl_sync(kFullMask, old + __popc(peers), (31 - __clz(peers)) & 31);
     const uint32_t pos = after - __popc(peers & ge);
-    if (valid) s_keys[pos] = key[i];
+    if (valid) {
+      s_keys[pos] = key[i];
+      dig.keep(pos, d);
+    }
     rank2[i >> 1] = (i & 1) ? (rank2[i >> 1] | (pos << 16)) : pos;
     slot_prev = slot;
     lead_prev = leader;
@@ -535,7 +555,7 @@ __device__ __forceinline__ void onesweep_tile_early(const PassParams& p, uint32_
                                                     const K* __restrict__ kin,
                                                     K* __restrict__ kout, const V* vin, V* vout,
                                                     const uint32_t* base, uint32_t bound,
-                                                    unsigned char* smem, const DS& dig) {
+                                                    unsigned char* smem, DS& dig) {
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
   using E = EarlyShape<K, V, BITS, THREADS, KPT>;
   constexpr int R = S::R, WARPS = S::WARPS, DPT = S::DPT;
@@ -553,6 +573,7 @@ __device__ __forceinline__ void onesweep_tile_early(const PassParams& p, uint32_
   K key[KPT];
   V val[HV ? KPT : 1];
   tile_load<K, V, KPT, FULL>(kin, vin, tile_base, tile_n, wofs, key, val);
+  dig.prepare(key);
   tile_count<K, R, KPT, FULL>(key, dig, tile_n, wofs, s_wcnt + warp * R);
   __syncthreads();
   if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 1] = globaltimer();
@@ -746,16 +767,15 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
   V* vout = static_cast<V*>(src ? p.vals[0] : p.vals[1]);
   const int64_t tile_base = (int64_t)tile * TILE;
   if constexpr (EARLY) {
+    RadixDigit dig{p.shift, p.mask};
     if (tile_n == TILE)
       onesweep_tile_early<K, V, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n,
                                                           kin, kout, vin, vout, p.base,
-                                                          (uint32_t)p.n, smem,
-                                                          RadixDigit{p.shift, p.mask});
+                                                          (uint32_t)p.n, smem, dig);
     else
       onesweep_tile_early<K, V, BITS, THREADS, KPT, false>(p, tile, tile == 0, tile_base,
                                                            tile_n, kin, kout, vin, vout, p.base,
-                                                           (uint32_t)p.n, smem,
-                                                           RadixDigit{p.shift, p.mask});
+                                                           (uint32_t)p.n, smem, dig);
   } else {
     if (tile_n == TILE)
       onesweep_tile<K, V, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n, kin,

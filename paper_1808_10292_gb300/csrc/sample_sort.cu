@@ -48,23 +48,79 @@ constexpr int kMaxSplit = 255;    // p <= 256 buckets
 // splitters ascending followed by copies of the largest key value, 255 in
 // all; eight halving steps over those 255 entries.
 template <typename K>
+__device__ __forceinline__ uint32_t bucket_of(const K* s, K k) {
+  uint32_t pos = 0;
+#pragma unroll
+  for (uint32_t step = 128; step; step >>= 1)
+    if (s[pos + step - 1] < k) pos += step;
+  return pos;
+}
+
+// A key's bucket lies between the buckets of the smallest and the largest key
+// with the same top kCellBits bits: cell[c] = lo | hi << 8 for cell c. The
+// search then runs over [lo, hi] only, often a single splitter or none.
+constexpr int kCellBits = 10;
+constexpr int kCells = 1 << kCellBits;
+
+template <typename K>
+__device__ __forceinline__ uint32_t cell_of(K k) {
+  return (uint32_t)(k >> (8 * sizeof(K) - kCellBits));
+}
+
+template <typename K>
+__device__ __forceinline__ uint32_t bucket_in_cell(const K* s, const uint16_t* cell, K k) {
+  const uint32_t e = cell[cell_of(k)];
+  uint32_t lo = e & 0xffu, hi = e >> 8;  // s[lo - 1] < k <= s[hi] (where they exist)
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (s[mid] < k)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+template <typename K>
 struct SplitDigit {
   const K* s;
-  __device__ __forceinline__ uint32_t operator()(K k) const {
-    uint32_t pos = 0;
+  const uint16_t* cell;
+  __device__ __forceinline__ uint32_t operator()(K k) const { return bucket_in_cell(s, cell, k); }
+};
+
+// The split round's digit rule: each key's bucket is searched once, right
+// after the tile is loaded, and kept as a byte (four per register); the
+// ranking records the bucket of every slot of the reordered tile in s_slot,
+// which the write-out reads back.
+template <typename K, int KPT>
+struct CachedSplitDigit {
+  const K* s;
+  const uint16_t* cell;
+  uint8_t* s_slot;  // [tile] bucket of each slot of the reordered tile
+  uint32_t packed[(KPT + 3) / 4];
+  __device__ __forceinline__ void prepare(const K (&key)[KPT]) {
 #pragma unroll
-    for (uint32_t step = 128; step; step >>= 1)
-      if (s[pos + step - 1] < k) pos += step;
-    return pos;
+    for (int i = 0; i < (KPT + 3) / 4; ++i) packed[i] = 0;
+#pragma unroll
+    for (int i = 0; i < KPT; ++i)
+      packed[i >> 2] |= bucket_in_cell(s, cell, key[i]) << ((i & 3) * 8);
   }
+  __device__ __forceinline__ uint32_t of(K, int i) const {
+    return (packed[i >> 2] >> ((i & 3) * 8)) & 0xffu;
+  }
+  __device__ __forceinline__ void keep(uint32_t pos, uint32_t d) const {
+    s_slot[pos] = (uint8_t)d;
+  }
+  __device__ __forceinline__ uint32_t staged(K, int j) const { return s_slot[j]; }
 };
 
 template <typename K>
 __global__ void __launch_bounds__(kSampleThreads)
     k_gvr_sample(const K* __restrict__ keys, int64_t n, int buckets, int oversample, uint64_t seed,
-                 K* __restrict__ split) {
+                 K* __restrict__ split, uint16_t* __restrict__ cell) {
   constexpr int Q = kSampleThreads, M = kSampleItems;
   __shared__ K sk[M * Q];
+  __shared__ K s_split[kMaxSplit];
   const int t = threadIdx.x;
   const int ns = buckets * oversample - 1;  // sample size s*p - 1 <= 4095
   BtnItem<K, false> x[M];
@@ -81,10 +137,19 @@ __global__ void __launch_bounds__(kSampleThreads)
     const int r = t * M + i;
     if ((r + 1) % oversample == 0) {
       const int j = (r + 1) / oversample;
-      if (j >= 1 && j <= buckets - 1) split[j - 1] = x[i].k;
+      if (j >= 1 && j <= buckets - 1) s_split[j - 1] = x[i].k;
     }
   }
-  if (t < kMaxSplit && t >= buckets - 1) split[t] = ~K(0);
+  if (t < kMaxSplit && t >= buckets - 1) s_split[t] = ~K(0);
+  __syncthreads();
+  if (t < kMaxSplit) split[t] = s_split[t];
+  // cell c holds the keys c << low .. ((c + 1) << low) - 1
+  constexpr int LOW = 8 * sizeof(K) - kCellBits;
+  for (int c = t; c < kCells; c += Q) {
+    const K first = (K)c << LOW;
+    const K last = first | (((K)1 << LOW) - 1);
+    cell[c] = (uint16_t)(bucket_of(s_split, first) | (bucket_of(s_split, last) << 8));
+  }
 }
 
 // Bucket counts: lane-private counter columns [bucket][lane] in shared memory
@@ -92,13 +157,16 @@ __global__ void __launch_bounds__(kSampleThreads)
 template <typename K>
 __global__ void __launch_bounds__(1024) k_gvr_hist(const K* __restrict__ keys, int64_t n,
                                                    const K* __restrict__ split,
+                                                   const uint16_t* __restrict__ cell,
                                                    uint32_t* __restrict__ hist) {
   __shared__ K s_split[kMaxSplit];
+  __shared__ uint16_t s_cell[kCells];
   __shared__ uint32_t s_cnt[256 * 32];
   for (int i = threadIdx.x; i < kMaxSplit; i += 1024) s_split[i] = split[i];
+  for (int i = threadIdx.x; i < kCells; i += 1024) s_cell[i] = cell[i];
   for (int i = threadIdx.x; i < 256 * 32; i += 1024) s_cnt[i] = 0;
   __syncthreads();
-  const SplitDigit<K> dig{s_split};
+  const SplitDigit<K> dig{s_split, s_cell};
   uint32_t* my = s_cnt + (threadIdx.x & 31);
   count_keys(keys, n, blockIdx.x * (int64_t)1024 + threadIdx.x, (int64_t)gridDim.x * 1024,
              [&](K k) { atomicAdd(&my[dig(k) * 32], 1u); });
@@ -135,17 +203,20 @@ __global__ void __launch_bounds__(256) k_gvr_scan(const uint32_t* __restrict__ h
 
 template <typename K, typename V, int THREADS, int KPT, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) k_gvr_split(PassParams p,
-                                                             const K* __restrict__ split) {
+                                                             const K* __restrict__ split,
+                                                             const uint16_t* __restrict__ cell) {
   using S = OnesweepShape<K, V, 8, THREADS, KPT>;
   using E = EarlyShape<K, V, 8, THREADS, KPT>;
   constexpr int R = S::R, WARPS = S::WARPS, TILE = S::TILE;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ K s_split[kMaxSplit];
+  __shared__ uint16_t s_cell[kCells];
   uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
   uint32_t* s_misc = s_wcnt + WARPS * R + R;
   uint32_t* s_masks = reinterpret_cast<uint32_t*>(smem + E::MASKS);
   const int tid = threadIdx.x;
   for (int i = tid; i < kMaxSplit; i += THREADS) s_split[i] = split[i];
+  for (int i = tid; i < kCells; i += THREADS) s_cell[i] = cell[i];
   if (tid == 0) s_misc[0] = atomicAdd(p.counter, 1u);  // tiles in launch order
   zero_words<THREADS>(s_wcnt, WARPS * R);
   zero_words<THREADS>(s_masks, WARPS * S::MASK_BUFS * R);
@@ -162,7 +233,10 @@ __global__ void __launch_bounds__(THREADS, MINB) k_gvr_split(PassParams p,
     prefetch_tile(kin, pf, cnt);
     if constexpr (HasVal<V>::value) prefetch_tile(vin, pf, cnt);
   }
-  const SplitDigit<K> dig{s_split};
+  CachedSplitDigit<K, KPT> dig;
+  dig.s = s_split;
+  dig.cell = s_cell;
+  dig.s_slot = smem + E::SMEM;
   const int64_t tile_base = (int64_t)tile * TILE;
   if (tile_n == TILE)
     onesweep_tile_early<K, V, 8, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n, kin,
@@ -187,13 +261,14 @@ cudaError_t gvr_launch(const GvrArgs& a, cudaStream_t st) {
   K* split = static_cast<K*>(a.split);
 
   timer_begin(a.timer, "k_gvr_sample", st);
+  uint16_t* cell = static_cast<uint16_t*>(a.cell);
   k_gvr_sample<K><<<1, kSampleThreads, 0, st>>>(keys, a.n, a.buckets, a.oversample, a.seed,
-                                                split);
+                                                split, cell);
   timer_end(a.timer, st);
   timer_begin(a.timer, "k_gvr_hist", st);
   const int64_t want = (a.n / 4 + 4095) / 4096;
   const int hblocks = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)a.num_sms);
-  k_gvr_hist<K><<<hblocks, 1024, 0, st>>>(keys, a.n, split, a.hist);
+  k_gvr_hist<K><<<hblocks, 1024, 0, st>>>(keys, a.n, split, cell, a.hist);
   timer_end(a.timer, st);
   timer_begin(a.timer, "k_gvr_scan", st);
   k_gvr_scan<<<1, 256, 0, st>>>(a.hist, a.buckets, a.n, a.base, a.offsets, a.counts_out, a.skip);
@@ -219,11 +294,12 @@ cudaError_t gvr_launch(const GvrArgs& a, cudaStream_t st) {
   pp.trace = nullptr;
   pp.prefetch_tiles = (int64_t)a.num_sms * 4;
   auto kern = k_gvr_split<K, V, THREADS, KPT, MINB>;
-  const size_t smem = EarlyShape<K, V, 8, THREADS, KPT>::SMEM;
+  // the early-counts layout, then one bucket byte per tile slot
+  const size_t smem = EarlyShape<K, V, 8, THREADS, KPT>::SMEM + S::TILE;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
     return e;
   timer_begin(a.timer, "k_gvr_split", st);
-  kern<<<(unsigned)tiles, THREADS, smem, st>>>(pp, split);
+  kern<<<(unsigned)tiles, THREADS, smem, st>>>(pp, split, cell);
   timer_end(a.timer, st);
   return cudaGetLastError();
 }
