@@ -41,6 +41,8 @@ WORKLOADS = {
                                            "11, 11, 10 bits)"),
     "pairs_2p27": (1 << 27, 32, 32, 8, "stable pairs, 2^27 uint32 keys + uint32 index payloads"),
     "u64_2p26": (1 << 26, 64, 0, 8, "plain sort, 2^26 uint64 keys, radix 256 (8 passes)"),
+    "sample_2p28": (1 << 28, 32, 0, 8, "GVR sample sort (Algorithm 3; 256 buckets, oversampling "
+                                        "16) of 2^28 uint32 keys"),
     "u32_128M_paper": (131_072_000, 32, 0, 8, "the paper's 128M (1M = 1,024,000) uint32 keys"),
     # n is the total over 20,000 ranges with log-uniform lengths in [1, 2^20]
     "segmented_20000": (0, 32, 0, 8, "batched segmented sort, 20,000 ranges, lengths "
@@ -52,7 +54,8 @@ WORKLOADS = {
 }
 ALIASES = {"r16": "u32_2p28_r65536", "r11": "u32_2p28_r2048", "pairs": "pairs_2p27", "u64": "u64_2p26",
            "paper128m": "u32_128M_paper", "default": "u32_2p28_r256",
-           "segmented": "segmented_20000", "serve": "serve_poisson", "networks": "short_ranges"}
+           "segmented": "segmented_20000", "serve": "serve_poisson", "networks": "short_ranges",
+           "gvr": "sample_2p28"}
 
 
 def parse():
@@ -238,9 +241,11 @@ def cpu_cores_available() -> int:
         return os.cpu_count() or 1
 
 
-def oracle_sample(n_full, key_bits, val_bits, radix_bits, dist, seed, target_s, max_sorts=None):
+def oracle_sample(n_full, key_bits, val_bits, radix_bits, dist, seed, target_s, max_sorts=None,
+                  gvr=False):
     """Time the oracle on a bounded sample of the workload: sorts of a 2^24-key
-    slice (or the whole input if smaller) until target_s seconds have passed."""
+    slice (or the whole input if smaller) until target_s seconds have passed
+    (the oracle's GVR sample sort for the sample-sort workload)."""
     import inputs
     import oracle
     n = min(n_full, 1 << 24)
@@ -251,7 +256,10 @@ def oracle_sample(n_full, key_bits, val_bits, radix_bits, dist, seed, target_s, 
     t_end = time.perf_counter() + target_s
     while time.perf_counter() < t_end and (max_sorts is None or len(times) < max_sorts):
         t0 = time.perf_counter()
-        oracle.radix_sort(k, v, radix_bits)
+        if gvr:
+            oracle.gvr_sort(k, v, buckets=256, oversample=16, seed=seed)
+        else:
+            oracle.radix_sort(k, v, radix_bits)
         times.append(time.perf_counter() - t0)
     return n, times
 
@@ -264,7 +272,7 @@ def run_reference(a):
     n_full, kb, vb, rb, desc = WORKLOADS[a.workload]
     # each step: one oracle sort of a 2^24-key slice of the workload
     n, times = oracle_sample(n_full, kb, vb, rb, a.dist, a.seed, target_s=1e9,
-                             max_sorts=a.steps + a.warmup)
+                             max_sorts=a.steps + a.warmup, gvr=a.workload == "sample_2p28")
     timed = times[a.warmup:]
     total = sum(timed)
     value = n * len(timed) / total
@@ -367,14 +375,18 @@ def run_ours(a):
             vals.copy_(vpr)
         flush.sum()  # read-only pass over 512 MiB: evicts keys from L2 without dirty lines
 
+    gvr = a.workload == "sample_2p28"
+
     def sort():
-        if vb:
+        if gvr:
+            isort.sample_sort(keys, vals, buckets=256, oversample=16, seed=a.seed)
+        elif vb:
             isort.sort_pairs(keys, vals, rb)
         else:
             isort.sort_keys(keys, rb)
 
     variant = None
-    if rb == 8:
+    if rb == 8 and not gvr:
         variant = isort.tune_variants(kb, vb, rb)[0]
 
     clocks = ClockSampler(local)
@@ -426,8 +438,8 @@ def run_ours(a):
     dom = max(kernel_ms, key=lambda k: sum(kernel_ms[k]))
     dom_ms = statistics.mean(kernel_ms[dom])
     bytes_per_key = (kb + vb) // 8
-    passes = -(-kb // rb)
-    if dom in ("k_onesweep", "k_scatter16", "k_scatter11"):
+    passes = -(-kb // rb) + (1 if gvr else 0)  # GVR: the split round, then the radix rounds
+    if dom in ("k_onesweep", "k_scatter16", "k_scatter11", "k_seg_onesweep", "k_gvr_split"):
         # one count-sort round: read and write every key (and payload) once
         alg_bytes = 2 * n * bytes_per_key
     else:
@@ -450,7 +462,7 @@ def run_ours(a):
 
     cpu = None
     if not a.no_cpu_baseline and rank == 0 and world == 1:
-        sn, times = oracle_sample(n, kb, vb, rb, a.dist, a.seed, a.cpu_seconds)
+        sn, times = oracle_sample(n, kb, vb, rb, a.dist, a.seed, a.cpu_seconds, gvr=gvr)
         cpu = {"value": sn * len(times) / sum(times), "unit": "keys/s", "cores": 1,
                "kind": "oracle",
                "sample": f"{len(times)} single-thread oracle sorts of a {sn}-key slice "
@@ -506,14 +518,20 @@ def measure_e2e(a, n, kb, vb, rb, torch, isort, inputs, stream):
         dv = torch.empty(n, dtype=hv_in.dtype, device="cuda")
     steps = max(3, min(a.steps, 10))
 
+    gvr = a.workload == "sample_2p28"
+
     def step():
         dev.copy_(host_in, non_blocking=True)
         if vb:
             dv.copy_(hv_in, non_blocking=True)
+        if gvr:
+            isort.sample_sort(dev, dv, buckets=256, oversample=16, seed=a.seed)
+        elif vb:
             isort.sort_pairs(dev, dv, rb)
-            hv_out.copy_(dv, non_blocking=True)
         else:
             isort.sort_keys(dev, rb)
+        if vb:
+            hv_out.copy_(dv, non_blocking=True)
         host_out.copy_(dev, non_blocking=True)
 
     for _ in range(2):
