@@ -48,13 +48,15 @@ WORKLOADS = {
     "segmented_20000": (0, 32, 0, 8, "batched segmented sort, 20,000 ranges, lengths "
                                      "log-uniform in [1, 2^20], uniform uint32 keys"),
     "short_ranges": (1 << 26, 32, 0, 8, "short ranges (32 .. 4096 keys), BTN vs OET networks"),
+    "mbsp_model": (1 << 28, 32, 0, 8, "MBSP cost model calibrated on the radix-256 round, "
+                                      "predicted vs measured sort times"),
     "serve_poisson": (0, 32, 32, 8, "serving loop: Poisson arrivals at 2,000 req/s, sizes "
                                     "log-uniform in [2^10, 2^24] uint32 keys, half with "
                                     "uint32 payloads, 40 GB admission budget"),
 }
 ALIASES = {"r16": "u32_2p28_r65536", "r11": "u32_2p28_r2048", "pairs": "pairs_2p27", "u64": "u64_2p26",
            "paper128m": "u32_128M_paper", "default": "u32_2p28_r256",
-           "segmented": "segmented_20000", "serve": "serve_poisson", "networks": "short_ranges",
+           "segmented": "segmented_20000", "serve": "serve_poisson", "networks": "short_ranges", "mbsp": "mbsp_model",
            "gvr": "sample_2p28"}
 
 
@@ -801,6 +803,89 @@ def run_ours_short_ranges(a):
     return 0
 
 
+def run_mbsp(a):
+    """The paper's MBSP accounting (paper_1808_10292_gb300/mbsp.py) on this GPU:
+    g from the measured copy bandwidth, G from the measured radix-256 round of
+    2^28 uint32 keys; then model vs measured whole-sort times for other widths,
+    payloads and radixes, and with the paper's own g = 5G."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    import inputs
+    import paper_1808_10292_gb300 as isort
+    from paper_1808_10292_gb300 import _lib, mbsp
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda").view(torch.int32)
+    flush.zero_()
+    isort.debug_set(_lib.DEBUG_KERNEL_TIMING, 1)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    cases = [(1 << 28, 32, 0, 8), (1 << 27, 32, 32, 8), (1 << 26, 64, 0, 8),
+             (1 << 28, 32, 0, 11), (1 << 28, 32, 0, 16)]
+    measured, launches = {}, 0
+    for n, kb, vb, rb in cases:
+        pristine = inputs.device_keys(n, kb, a.dist, a.seed)
+        keys = torch.empty_like(pristine)
+        vals = inputs.device_iota(n, vb) if vb else None
+        ms, rounds_ms = [], []
+        for i in range(a.warmup + a.steps):
+            keys.copy_(pristine)
+            flush.sum()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if vb:
+                isort.sort_pairs(keys, vals, rb)
+            else:
+                isort.sort_keys(keys, rb)
+            e1.record(stream)
+            e1.synchronize()
+            kt = isort.kernel_times()
+            if i >= a.warmup:
+                ms.append(e0.elapsed_time(e1))
+                rounds_ms += [t for k, t in kt if k == "k_onesweep"]
+                launches += len(kt)
+        if isort.stream_status() != _lib.OK:
+            raise RuntimeError("device error in the model benchmark")
+        measured[(n, kb, vb, rb)] = {"sort_ms": statistics.median(ms),
+                                     "round_ms": statistics.median(rounds_ms) if rounds_ms else None}
+        del pristine, keys, vals
+        torch.cuda.empty_cache()
+    isort.debug_set(_lib.DEBUG_KERNEL_TIMING, 0)
+    clocks.window(t_wall0, time.perf_counter())
+    clk = clocks.stop()
+    peak, peak_kind = measured_peak_hbm()
+    base = measured[cases[0]]
+    cal = mbsp.calibrate(peak, base["round_ms"] / 1000.0, cases[0][0])
+    g, G = cal["g"], cal["G"]
+    rows = []
+    for (n, kb, vb, rb) in cases:
+        m = measured[(n, kb, vb, rb)]["sort_ms"]
+        pred = 1000 * mbsp.gpu_sort(n, kb, vb, 1 << rb, g, G)
+        pred5 = 1000 * mbsp.gpu_sort(n, kb, vb, 1 << rb, g, g / 5)
+        rows.append({"n": n, "key_bits": kb, "val_bits": vb, "radix": 1 << rb,
+                     "measured_ms": m, "model_ms": pred, "model_error": pred / m - 1,
+                     "model_g5G_ms": pred5, "model_g5G_error": pred5 / m - 1})
+    line = {
+        "metric": "MBSP model vs measured sort time (calibrated on the 2^28 uint32 radix-256 round)",
+        "value": cases[0][0] / (base["sort_ms"] / 1000.0),
+        "unit": "keys/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": base["sort_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": a.workload, "dist": a.dist, "seed": a.seed,
+                   "l2": "inputs larger than L2; restored and L2 flushed before each sort"},
+        "calibration": {"hbm_gbs": peak, "peak_kind": peak_kind, "g_s_per_word": g,
+                        "G_s_per_access": G, "g_over_G": cal["g_over_G"],
+                        "shared_accesses_per_key_round": mbsp.SHARED_ACCESSES_ONESWEEP,
+                        "onesweep_round_ms": base["round_ms"]},
+        "predictions": rows,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours_serve(a):
     """Served (continuous batching) vs sequential plain sorts on one Poisson trace;
     then both arms on a backlog (every request queued at once) for capacity."""
@@ -901,6 +986,12 @@ def main():
         if a.impl == "reference":
             return run_reference_segmented(a)
         return run_ours_segmented(a)
+    if a.workload == "mbsp_model":
+        if a.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "model comparison only; the "
+                              "oracle arm is timed on the plain and segmented workloads"}))
+            return 0
+        return run_mbsp(a)
     if a.workload == "short_ranges":
         if a.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "network comparison only; "
