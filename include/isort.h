@@ -129,6 +129,29 @@ isort_status isort_sample_sort(void *keys, void *vals, int64_t n, int key_bits, 
                                int buckets, int oversample, uint64_t seed,
                                uint32_t *bucket_counts, void *stream);
 
+/* Deterministic regular-oversampling sort: the paper's GSD (Algorithm 1,
+ * Theorem 1). Sorts keys[0..n) ascending in place (stable with vals, which may
+ * be NULL):
+ *   1. the p sequences [n*k/p, n*(k+1)/p) are sorted independently;
+ *   2. from each sorted sequence the r*p keys that end its r*p evenly sized
+ *      segments (position floor(i * len / (r*p)) - 1, i = 1..r*p; the last is
+ *      its maximum) are sampled, and all r*p*p samples sorted with BTN;
+ *   3. the (i*r*p)-th smallest samples, 1 <= i <= p-1, are the splitters;
+ *   4. each sorted sequence is split by binary search: part j holds its keys
+ *      above splitter j-1 and at most splitter j;
+ *   5. the p parts of every bucket are merged (lg p rounds of pairwise stable
+ *      merges) and the buckets concatenated.
+ * buckets = p: a power of two, 1..64; oversample = r >= 1 with r*p*p <= 4096
+ * (else ISORT_EINVAL); n <= 2^30. bucket_counts: DEVICE array of p uint32 that
+ * receives the bucket sizes, or NULL. No randomness: the result and the bucket
+ * sizes depend on the input only. */
+isort_status isort_gsd_sort(void *keys, void *vals, int64_t n, int key_bits, int val_bits,
+                            int buckets, int oversample, uint32_t *bucket_counts, void *stream);
+
+/* Bytes of workspace one isort_gsd_sort call with these arguments needs. */
+isort_status isort_gsd_sort_workspace_size(int64_t n, int key_bits, int val_bits, int buckets,
+                                           int oversample, size_t *bytes);
+
 /* Bytes of workspace one isort_sample_sort call with these arguments needs. */
 isort_status isort_sample_sort_workspace_size(int64_t n, int key_bits, int val_bits, int buckets,
                                               int oversample, size_t *bytes);

@@ -41,8 +41,9 @@ def load_library(path: str):
     lib.oracle_segmented_sort.argtypes = [vp, vp, vp, i64, i32, i32, i32]
     lib.oracle_num_passes.argtypes = [i32, i32]
     lib.oracle_gvr_sort.argtypes = [vp, vp, i64, i32, i32, i32, i32, ctypes.c_uint64, vp, vp]
+    lib.oracle_gsd_sort.argtypes = [vp, vp, i64, i32, i32, i32, i32, vp, vp]
     for f in (lib.oracle_count_sort_round, lib.oracle_radix_sort, lib.oracle_segmented_sort,
-              lib.oracle_num_passes, lib.oracle_gvr_sort):
+              lib.oracle_num_passes, lib.oracle_gvr_sort, lib.oracle_gsd_sort):
         f.restype = i32
     return lib
 
@@ -127,5 +128,18 @@ def gvr_sort(keys: np.ndarray, vals: np.ndarray | None = None, buckets: int = 25
     _check((lib or _load()).oracle_gvr_sort(_ptr(k), _ptr(v), k.size, _bits(k), _bits(v), buckets,
                                             oversample, seed, _ptr(counts), _ptr(split)),
            "gvr_sort")
+    out = (k,) if v is None else (k, v)
+    return out + (counts, split[:buckets - 1])
+
+
+def gsd_sort(keys: np.ndarray, vals: np.ndarray | None = None, buckets: int = 16,
+             oversample: int = 4, lib=None):
+    """GSD (Algorithm 1). Returns (sorted keys[, vals], bucket sizes, splitters) as copies."""
+    k = np.array(keys, copy=True, order="C")
+    v = None if vals is None else np.array(vals, copy=True, order="C")
+    counts = np.zeros(buckets, dtype=np.uint32)
+    split = np.zeros(max(buckets - 1, 1), dtype=np.uint64)
+    _check((lib or _load()).oracle_gsd_sort(_ptr(k), _ptr(v), k.size, _bits(k), _bits(v), buckets,
+                                            oversample, _ptr(counts), _ptr(split)), "gsd_sort")
     out = (k,) if v is None else (k, v)
     return out + (counts, split[:buckets - 1])

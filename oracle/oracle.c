@@ -242,3 +242,118 @@ done:
   free(vout);
   return rc;
 }
+
+/* ------------------------------------------------------------------------
+ * GSD, the paper's deterministic regular-oversampling sort (Algorithm 1), in
+ * the algorithm's order:
+ *   1. LocalSorting: sequences [n*k/p, n*(k+1)/p), each sorted by SR4;
+ *   2. Sample Selection: from each sorted sequence X_k the r*p keys that end its
+ *      r*p evenly sized segments (position floor(i*len/(r*p)) - 1, i = 1..r*p,
+ *      the last one its maximum); all r*p*p samples sorted (qsort);
+ *   3. Splitter Selection: the (i*r*p)-th smallest samples, 1 <= i <= p-1;
+ *   4. Split: part (k, j) of X_k holds its keys above splitter j-1 and at most
+ *      splitter j (binary search);
+ *   5. Merging: bucket j = the p-way merge of parts (0, j) .. (p-1, j), taking
+ *      the smallest head each time (the lowest k on equal keys); the buckets
+ *      concatenated.
+ * An empty sequence contributes samples equal to the largest key value.
+ */
+static int64_t count_le(const void *keys, int64_t lo, int64_t hi, uint64_t s, int kb) {
+  /* number of keys in the sorted range [lo, hi) that are at most s */
+  int64_t a = lo, b = hi;
+  while (a < b) {
+    const int64_t mid = a + (b - a) / 2;
+    if (get_key(keys, mid, kb) <= s)
+      a = mid + 1;
+    else
+      b = mid;
+  }
+  return a - lo;
+}
+
+int oracle_gsd_sort(void *keys, void *vals, int64_t n, int key_bits, int val_bits, int p, int r,
+                    uint32_t *bucket_counts, uint64_t *splitters) {
+  if (n < 0 || (key_bits != 32 && key_bits != 64) ||
+      (val_bits != 0 && val_bits != 32 && val_bits != 64) || p < 1 || r < 1)
+    return 1;
+  const int kb = key_bits / 8, vb = val_bits / 8;
+  const int rp = r * p;
+  const uint64_t maxkey = key_bits == 32 ? 0xFFFFFFFFull : ~0ull;
+  int64_t *start = malloc(sizeof(int64_t) * (size_t)(p + 1));
+  uint64_t *sample = malloc(sizeof(uint64_t) * (size_t)rp * p);
+  uint64_t *split = malloc(sizeof(uint64_t) * (size_t)(p > 1 ? p - 1 : 1));
+  int64_t *part = malloc(sizeof(int64_t) * (size_t)p * (p + 1)); /* part[k][j]: start in X_k */
+  int64_t *head = malloc(sizeof(int64_t) * (size_t)p);
+  void *kout = malloc((size_t)(n > 0 ? n : 1) * kb);
+  void *vout = vb ? malloc((size_t)(n > 0 ? n : 1) * vb) : NULL;
+  int rc = 0;
+  if (!start || !sample || !split || !part || !head || !kout || (vb && !vout)) {
+    rc = 2;
+    goto done;
+  }
+  /* 1. LocalSorting */
+  for (int k = 0; k <= p; ++k) start[k] = n * k / p;
+  rc = oracle_segmented_sort(keys, vals, start, p, key_bits, val_bits, 8);
+  if (rc) goto done;
+  /* 2. Sample Selection */
+  for (int k = 0; k < p; ++k) {
+    const int64_t len = start[k + 1] - start[k];
+    for (int i = 1; i <= rp; ++i) {
+      int64_t pos = (int64_t)i * len / rp - 1;
+      if (pos < 0) pos = 0;
+      sample[(int64_t)k * rp + (i - 1)] = len > 0 ? get_key(keys, start[k] + pos, kb) : maxkey;
+    }
+  }
+  qsort(sample, (size_t)rp * p, sizeof(uint64_t), cmp_u64);
+  /* 3. Splitter Selection */
+  for (int i = 1; i <= p - 1; ++i) split[i - 1] = sample[(int64_t)i * rp - 1];
+  /* 4. Split each sorted sequence */
+  for (int k = 0; k < p; ++k) {
+    int64_t *row = part + (size_t)k * (p + 1);
+    row[0] = 0;
+    for (int j = 1; j <= p - 1; ++j)
+      row[j] = count_le(keys, start[k], start[k + 1], split[j - 1], kb);
+    row[p] = start[k + 1] - start[k];
+  }
+  /* 5. Merging: p-way merge per bucket, smallest head first, lowest k on ties */
+  {
+    int64_t o = 0;
+    for (int j = 0; j < p; ++j) {
+      int64_t size = 0;
+      for (int k = 0; k < p; ++k) {
+        head[k] = part[(size_t)k * (p + 1) + j];
+        size += part[(size_t)k * (p + 1) + j + 1] - head[k];
+      }
+      if (bucket_counts) bucket_counts[j] = (uint32_t)size;
+      for (int64_t m = 0; m < size; ++m) {
+        int best = -1;
+        uint64_t bk = 0;
+        for (int k = 0; k < p; ++k) {
+          if (head[k] >= part[(size_t)k * (p + 1) + j + 1]) continue;
+          const uint64_t x = get_key(keys, start[k] + head[k], kb);
+          if (best < 0 || x < bk) {
+            best = k;
+            bk = x;
+          }
+        }
+        put_key(kout, o, bk, kb);
+        if (vb) copy_val(vout, o, vals, start[best] + head[best], vb);
+        ++head[best];
+        ++o;
+      }
+    }
+  }
+  memcpy(keys, kout, (size_t)n * kb);
+  if (vb) memcpy(vals, vout, (size_t)n * vb);
+  if (splitters)
+    for (int i = 0; i < p - 1; ++i) splitters[i] = split[i];
+done:
+  free(start);
+  free(sample);
+  free(split);
+  free(part);
+  free(head);
+  free(kout);
+  free(vout);
+  return rc;
+}

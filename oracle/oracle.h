@@ -42,6 +42,14 @@ int oracle_segmented_sort(void *keys, void *vals, const int64_t *offsets, int64_
 int oracle_gvr_sort(void *keys, void *vals, int64_t n, int key_bits, int val_bits, int p, int s,
                     uint64_t seed, uint32_t *bucket_counts, uint64_t *splitters);
 
+/* GSD (Algorithm 1): p sequences [n*k/p, n*(k+1)/p) sorted by SR4, r*p regular
+ * samples per sequence, splitters = the (i*r*p)-th smallest samples, split by
+ * binary search (part j: keys above splitter j-1, at most splitter j), p-way
+ * merge per bucket (lowest sequence first on equal keys). Sorts in place;
+ * bucket_counts (p) and splitters (p - 1) receive the intermediates when not NULL. */
+int oracle_gsd_sort(void *keys, void *vals, int64_t n, int key_bits, int val_bits, int p, int r,
+                    uint32_t *bucket_counts, uint64_t *splitters);
+
 #ifdef __cplusplus
 }
 #endif

@@ -122,6 +122,31 @@ def sample_sort(keys, vals=None, buckets: int = 256, oversample: int = 16, seed:
     return keys if vals is None else (keys, vals)
 
 
+def gsd_sort(keys, vals=None, buckets: int = 16, oversample: int = 4, bucket_counts=None,
+             stream=None):
+    """The paper's GSD (Algorithm 1), in place: p sequences sorted locally,
+    r*p regular samples from each, p - 1 splitters, each sequence split by
+    binary search and every bucket's parts merged. buckets: a power of two
+    up to 64; oversample * buckets^2 <= 4096. bucket_counts: optional CUDA
+    uint32 tensor of at least `buckets` entries for the bucket sizes."""
+    _dev(keys, "keys")
+    vb, vptr = 0, None
+    if vals is not None:
+        _dev(vals, "vals")
+        if vals.numel() != keys.numel():
+            raise ValueError("keys and vals differ in length")
+        vb, vptr = _bits(vals), vals.data_ptr()
+    cptr = None
+    if bucket_counts is not None:
+        _dev(bucket_counts, "bucket_counts")
+        if _bits(bucket_counts) != 32 or bucket_counts.numel() < buckets:
+            raise ValueError("bucket_counts must be uint32 with at least `buckets` entries")
+        cptr = bucket_counts.data_ptr()
+    check(load().isort_gsd_sort(keys.data_ptr(), vptr, keys.numel(), _bits(keys), vb, buckets,
+                                oversample, cptr, _stream(stream)), "isort_gsd_sort")
+    return keys if vals is None else (keys, vals)
+
+
 def sample_sort_workspace_size(n: int, key_bits: int = 32, val_bits: int = 0, buckets: int = 256,
                                oversample: int = 16) -> int:
     out = ctypes.c_size_t(0)

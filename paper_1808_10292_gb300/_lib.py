@@ -50,6 +50,8 @@ def _sig(lib):
         "isort_segmented_workspace_size": [i64, i64, i32, i32, ctypes.POINTER(sz)],
         "isort_sample_sort": [vp, vp, i64, i32, i32, i32, i32, ctypes.c_uint64, vp, vp],
         "isort_sample_sort_workspace_size": [i64, i32, i32, i32, i32, ctypes.POINTER(sz)],
+        "isort_gsd_sort": [vp, vp, i64, i32, i32, i32, i32, vp, vp],
+        "isort_gsd_sort_workspace_size": [i64, i32, i32, i32, i32, ctypes.POINTER(sz)],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)

@@ -317,6 +317,43 @@ GvrLayout gvr_layout(const SegConfig& c, int64_t n, int buckets) {
   return G;
 }
 
+// GSD workspace: the segmented-sort layout of the p sequences (error word at
+// offset 0; its alternate buffers serve the merge rounds too), then the
+// sequence offsets, splitters and the split and merge plans.
+struct GsdLayout {
+  SegLayout seg;
+  size_t off, split, bound, pre, bucket_off, pair_info, pair_tile, cut, total;
+};
+
+GsdLayout gsd_layout(const SegConfig& c, int64_t n, int p) {
+  GsdLayout L;
+  L.seg = seg_layout(c, p, n, seg_btn_max(c));
+  const size_t pp1 = sizeof(int64_t) * (size_t)p * (p + 1);
+  const size_t pairs = (size_t)p * p / 2 + 1;
+  size_t o = L.seg.total;
+  L.off = o;         o = align256(o + sizeof(int64_t) * (p + 1));
+  L.split = o;       o = align256(o + sizeof(uint64_t) * (p > 1 ? p - 1 : 1));
+  L.bound = o;       o = align256(o + pp1);
+  L.pre = o;         o = align256(o + pp1);
+  L.bucket_off = o;  o = align256(o + sizeof(int64_t) * (p + 1));
+  L.pair_info = o;   o = align256(o + sizeof(int64_t) * 5 * pairs);
+  L.pair_tile = o;   o = align256(o + sizeof(int64_t) * (pairs + 1));
+  L.cut = o;         o = align256(o + sizeof(int64_t) * (size_t)(n / 2048 + (int64_t)p * p + 2));
+  L.total = o;
+  return L;
+}
+
+isort_status check_gsd_args(int64_t n, int key_bits, int val_bits, bool pairs, int buckets,
+                            int oversample) {
+  isort_status s = check_widths(key_bits, val_bits, pairs);
+  if (s != ISORT_OK) return s;
+  if (n < 0 || buckets < 1 || buckets > 64 || (buckets & (buckets - 1)) || oversample < 1 ||
+      (int64_t)oversample * buckets * buckets > 4096)
+    return ISORT_EINVAL;
+  if (n > (int64_t(1) << 30)) return ISORT_EUNSUPPORTED;
+  return ISORT_OK;
+}
+
 isort_status check_sample_args(int64_t n, int key_bits, int val_bits, bool pairs, int buckets,
                                int oversample) {
   isort_status s = check_widths(key_bits, val_bits, pairs);
@@ -409,6 +446,62 @@ isort_status isort_sample_sort(void* keys, void* vals, int64_t n, int key_bits, 
   if (vals && cudaMemcpyAsync(vals, g.out_vals, (size_t)n * (val_bits / 8),
                               cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return ISORT_ECUDA;
+  return ISORT_OK;
+}
+
+isort_status isort_gsd_sort(void* keys, void* vals, int64_t n, int key_bits, int val_bits,
+                            int buckets, int oversample, uint32_t* bucket_counts, void* stream) {
+  if (!vals) val_bits = 0;
+  isort_status s = check_gsd_args(n, key_bits, val_bits, vals != nullptr, buckets, oversample);
+  if (s != ISORT_OK) return s;
+  if (n == 0) return ISORT_OK;
+  if (!keys || !aligned(keys, key_bits / 8) || (vals && !aligned(vals, val_bits / 8)) ||
+      (bucket_counts && !aligned(bucket_counts, 4)))
+    return ISORT_EINVAL;
+  const SegConfig* c = key_bits == 32 ? seg_config_k32(val_bits) : seg_config_k64(val_bits);
+  if (!c) return ISORT_EUNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lock(g_mu);
+  const GsdLayout L = gsd_layout(*c, n, buckets);
+  void* ws = nullptr;
+  if ((s = acquire(st, L.total, &ws)) != ISORT_OK) return s;
+  char* b = static_cast<char*>(ws);
+  int64_t* off = reinterpret_cast<int64_t*>(b + L.off);
+  // 1. LocalSorting of the p sequences, in place
+  if (gsd_offsets_launch(n, buckets, off, st) != cudaSuccess) return ISORT_ECUDA;
+  SegArgs sa = seg_args(*c, L.seg, b, keys, vals, off, buckets, n);
+  if (c->launch(sa, st) != cudaSuccess) return ISORT_ECUDA;
+  // 2-5. sample, splitters, split, lg p merge rounds
+  GsdArgs g;
+  g.keys = keys;
+  g.vals = vals;
+  g.alt_keys = b + L.seg.alt_k;
+  g.alt_vals = vals ? b + L.seg.alt_v : nullptr;
+  g.n = n;
+  g.buckets = buckets;
+  g.oversample = oversample;
+  g.split = b + L.split;
+  g.bound = reinterpret_cast<int64_t*>(b + L.bound);
+  g.pre = reinterpret_cast<int64_t*>(b + L.pre);
+  g.bucket_off = reinterpret_cast<int64_t*>(b + L.bucket_off);
+  g.pair_info = reinterpret_cast<int64_t*>(b + L.pair_info);
+  g.pair_tile = reinterpret_cast<int64_t*>(b + L.pair_tile);
+  g.cut = reinterpret_cast<int64_t*>(b + L.cut);
+  g.counts_out = bucket_counts;
+  g.err = sa.err;
+  g.timer = sa.timer;
+  return gsd_merge_launch(key_bits, val_bits, g, st) == cudaSuccess ? ISORT_OK : ISORT_ECUDA;
+}
+
+isort_status isort_gsd_sort_workspace_size(int64_t n, int key_bits, int val_bits, int buckets,
+                                           int oversample, size_t* bytes) {
+  if (!bytes) return ISORT_EINVAL;
+  isort_status s = check_gsd_args(n, key_bits, val_bits, val_bits != 0, buckets, oversample);
+  if (s != ISORT_OK) return s;
+  const SegConfig* c = key_bits == 32 ? seg_config_k32(val_bits) : seg_config_k64(val_bits);
+  if (!c) return ISORT_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_mu);
+  *bytes = gsd_layout(*c, n, buckets).total;
   return ISORT_OK;
 }
 

@@ -135,6 +135,30 @@ struct GvrArgs {
   int num_sms;
   KernelTimer* timer;
 };
+// The sample, split and merge steps of GSD (gsd.cu), after the local sort of
+// the p sequences [n*k/p, n*(k+1)/p) in keys/vals.
+struct GsdArgs {
+  void* keys;            // caller's keys, each sequence sorted; the result ends here
+  void* vals;            // caller's payloads or nullptr
+  void* alt_keys;        // workspace: n keys
+  void* alt_vals;        // workspace: n payloads (when vals != nullptr)
+  int64_t n;
+  int buckets;           // p, a power of two, 1..64
+  int oversample;        // r, r * p * p <= 4096
+  void* split;           // [p - 1] keys
+  int64_t* bound;        // [p][p + 1] part ends inside each sequence
+  int64_t* pre;          // [p][p + 1] part offsets inside each bucket
+  int64_t* bucket_off;   // [p + 1]
+  int64_t* pair_info;    // [p * p / 2][5] merge pairs of one round
+  int64_t* pair_tile;    // [p * p / 2 + 1] first output tile of each pair
+  int64_t* cut;          // [n / 2048 + p * p + 1] merge-path split of each output tile
+  uint32_t* counts_out;  // [p] caller's copy of the bucket sizes, or nullptr
+  uint32_t* err;
+  KernelTimer* timer;
+};
+cudaError_t gsd_merge_launch(int key_bits, int val_bits, const GsdArgs& a, cudaStream_t st);
+cudaError_t gsd_offsets_launch(int64_t n, int p, int64_t* off, cudaStream_t st);
+
 int64_t gvr_tile(int key_bits, int val_bits);  // keys per tile of the round
 cudaError_t gvr_split_launch(int key_bits, int val_bits, const GvrArgs& a, cudaStream_t st);
 

@@ -196,6 +196,43 @@ def test_gvr_sorts_stably_and_its_intermediates_follow_the_definition(key_bits, 
             assert np.array_equal(split, want_split), n
 
 
+# ---- GSD (Algorithm 1) ------------------------------------------------------
+def gsd_definition(k, p, r):
+    """Splitters and bucket sizes recomputed with numpy from the algorithm's
+    definitions: sequences [n*j/p, n*(j+1)/p) sorted, the keys ending their
+    r*p evenly sized segments sampled, splitters = the (i*r*p)-th smallest
+    samples, bucket j = the keys above splitter j-1 and at most splitter j."""
+    n = k.size
+    rp = r * p
+    maxkey = np.iinfo(k.dtype).max
+    samples = []
+    for j in range(p):
+        seq = np.sort(k[n * j // p:n * (j + 1) // p]).astype(np.uint64)
+        for i in range(1, rp + 1):
+            pos = max(i * seq.size // rp - 1, 0)
+            samples.append(seq[pos] if seq.size else np.uint64(maxkey))
+    samples = np.sort(np.array(samples, dtype=np.uint64))
+    split = samples[np.arange(1, p) * rp - 1]
+    srt = np.sort(k).astype(np.uint64)
+    edges = np.concatenate([[0], np.searchsorted(srt, split, side="right"), [n]])
+    return split, np.diff(edges)
+
+
+@pytest.mark.parametrize("key_bits", [32, 64])
+@pytest.mark.parametrize("dist", inputs.DISTS)
+@pytest.mark.parametrize("p,r", [(1, 1), (2, 3), (8, 4), (16, 16), (64, 1)])
+def test_gsd_sorts_stably_and_its_intermediates_follow_the_definition(key_bits, dist, p, r):
+    for n in (0, 1, 5, 63, 1000, 20_011):
+        k = inputs.keys(n, key_bits, dist, seed=n + 13)
+        v = inputs.iota(n)
+        ks, vs, counts, split = oracle.gsd_sort(k, v, buckets=p, oversample=r)
+        order = np.argsort(k, kind="stable")
+        assert np.array_equal(ks, k[order]) and np.array_equal(vs, v[order]), n
+        want_split, want_counts = gsd_definition(k, p, r)
+        assert np.array_equal(counts.astype(np.int64), want_counts), n
+        assert np.array_equal(split, want_split), n
+
+
 # ---- planted mistakes -------------------------------------------------------
 # Each mutant is a textual edit of oracle.c that a plausible bug would make. None
 # writes out of bounds (every output slot stays in [0, n)), so running it is safe.
@@ -214,6 +251,11 @@ MUTANTS = {
                     "const uint64_t mask = ((uint64_t)r - 1) >> 1;"),
     "gvr_bucket_takes_equal_keys_up": ("split[j] < k) ++j;", "split[j] <= k) ++j;"),
     "gvr_splitter_rank_off_by_one": ("sample[(int64_t)i * s - 1]", "sample[(int64_t)i * s]"),
+    "gsd_sample_position_off_by_one": ("int64_t pos = (int64_t)i * len / rp - 1;",
+                                       "int64_t pos = (int64_t)i * len / rp - 2;"),
+    "gsd_merge_prefers_later_sequence": ("if (best < 0 || x < bk) {", "if (best < 0 || x <= bk) {"),
+    "gsd_split_takes_equal_keys_up": ("if (get_key(keys, mid, kb) <= s)",
+                                      "if (get_key(keys, mid, kb) < s)"),
     "gvr_split_round_backwards": (
         "for (int64_t i = 0; i < n; ++i) {\n      const int64_t o = next[dest[i]]++;",
         "for (int64_t i = n - 1; i >= 0; --i) {\n      const int64_t o = next[dest[i]]++;"),
@@ -244,6 +286,19 @@ def _pins_pass(lib):
             return False
         order = np.argsort(k, kind="stable")
         want_split, want_counts = gvr_definition(k, 16, 4, 7)
+        if not (np.array_equal(ks, k[order]) and np.array_equal(vs, v[order]) and
+                np.array_equal(counts.astype(np.int64), want_counts) and
+                np.array_equal(split, want_split)):
+            return False
+    for dist in ("uniform", "u16", "and4", "equal"):
+        k = inputs.keys(3000, 32, dist, seed=5)
+        v = inputs.iota(3000)
+        try:
+            ks, vs, counts, split = oracle.gsd_sort(k, v, buckets=8, oversample=4, lib=lib)
+        except (RuntimeError, IndexError):
+            return False
+        order = np.argsort(k, kind="stable")
+        want_split, want_counts = gsd_definition(k, 8, 4)
         if not (np.array_equal(ks, k[order]) and np.array_equal(vs, v[order]) and
                 np.array_equal(counts.astype(np.int64), want_counts) and
                 np.array_equal(split, want_split)):
