@@ -43,6 +43,8 @@ WORKLOADS = {
     "u64_2p26": (1 << 26, 64, 0, 8, "plain sort, 2^26 uint64 keys, radix 256 (8 passes)"),
     "sample_2p28": (1 << 28, 32, 0, 8, "GVR sample sort (Algorithm 3; 256 buckets, oversampling "
                                         "16) of 2^28 uint32 keys"),
+    "gsd_2p28": (1 << 28, 32, 0, 8, "GSD regular-oversampling sort (Algorithm 1; p = 16, r = 4) "
+                                     "of 2^28 uint32 keys"),
     "u32_128M_paper": (131_072_000, 32, 0, 8, "the paper's 128M (1M = 1,024,000) uint32 keys"),
     # n is the total over 20,000 ranges with log-uniform lengths in [1, 2^20]
     "segmented_20000": (0, 32, 0, 8, "batched segmented sort, 20,000 ranges, lengths "
@@ -57,7 +59,7 @@ WORKLOADS = {
 ALIASES = {"r16": "u32_2p28_r65536", "r11": "u32_2p28_r2048", "pairs": "pairs_2p27", "u64": "u64_2p26",
            "paper128m": "u32_128M_paper", "default": "u32_2p28_r256",
            "segmented": "segmented_20000", "serve": "serve_poisson", "networks": "short_ranges", "mbsp": "mbsp_model",
-           "gvr": "sample_2p28"}
+           "gvr": "sample_2p28", "gsd": "gsd_2p28"}
 
 
 def parse():
@@ -244,7 +246,7 @@ def cpu_cores_available() -> int:
 
 
 def oracle_sample(n_full, key_bits, val_bits, radix_bits, dist, seed, target_s, max_sorts=None,
-                  gvr=False):
+                  gvr=False, gsd=False):
     """Time the oracle on a bounded sample of the workload: sorts of a 2^24-key
     slice (or the whole input if smaller) until target_s seconds have passed
     (the oracle's GVR sample sort for the sample-sort workload)."""
@@ -260,6 +262,8 @@ def oracle_sample(n_full, key_bits, val_bits, radix_bits, dist, seed, target_s, 
         t0 = time.perf_counter()
         if gvr:
             oracle.gvr_sort(k, v, buckets=256, oversample=16, seed=seed)
+        elif gsd:
+            oracle.gsd_sort(k, v, buckets=16, oversample=4)
         else:
             oracle.radix_sort(k, v, radix_bits)
         times.append(time.perf_counter() - t0)
@@ -274,7 +278,8 @@ def run_reference(a):
     n_full, kb, vb, rb, desc = WORKLOADS[a.workload]
     # each step: one oracle sort of a 2^24-key slice of the workload
     n, times = oracle_sample(n_full, kb, vb, rb, a.dist, a.seed, target_s=1e9,
-                             max_sorts=a.steps + a.warmup, gvr=a.workload == "sample_2p28")
+                             max_sorts=a.steps + a.warmup, gvr=a.workload == "sample_2p28",
+                             gsd=a.workload == "gsd_2p28")
     timed = times[a.warmup:]
     total = sum(timed)
     value = n * len(timed) / total
@@ -378,17 +383,20 @@ def run_ours(a):
         flush.sum()  # read-only pass over 512 MiB: evicts keys from L2 without dirty lines
 
     gvr = a.workload == "sample_2p28"
+    gsd = a.workload == "gsd_2p28"
 
     def sort():
         if gvr:
             isort.sample_sort(keys, vals, buckets=256, oversample=16, seed=a.seed)
+        elif gsd:
+            isort.gsd_sort(keys, vals, buckets=16, oversample=4)
         elif vb:
             isort.sort_pairs(keys, vals, rb)
         else:
             isort.sort_keys(keys, rb)
 
     variant = None
-    if rb == 8 and not gvr:
+    if rb == 8 and not gvr and not gsd:
         variant = isort.tune_variants(kb, vb, rb)[0]
 
     clocks = ClockSampler(local)
@@ -440,8 +448,10 @@ def run_ours(a):
     dom = max(kernel_ms, key=lambda k: sum(kernel_ms[k]))
     dom_ms = statistics.mean(kernel_ms[dom])
     bytes_per_key = (kb + vb) // 8
-    passes = -(-kb // rb) + (1 if gvr else 0)  # GVR: the split round, then the radix rounds
-    if dom in ("k_onesweep", "k_scatter16", "k_scatter11", "k_seg_onesweep", "k_gvr_split"):
+    # GVR: the split round, then the radix rounds; GSD: the radix rounds, then lg 16 merge rounds
+    passes = -(-kb // rb) + (1 if gvr else 0) + (4 if gsd else 0)
+    if dom in ("k_onesweep", "k_scatter16", "k_scatter11", "k_seg_onesweep", "k_gvr_split",
+               "k_gsd_merge"):
         # one count-sort round: read and write every key (and payload) once
         alg_bytes = 2 * n * bytes_per_key
     else:
@@ -464,7 +474,7 @@ def run_ours(a):
 
     cpu = None
     if not a.no_cpu_baseline and rank == 0 and world == 1:
-        sn, times = oracle_sample(n, kb, vb, rb, a.dist, a.seed, a.cpu_seconds, gvr=gvr)
+        sn, times = oracle_sample(n, kb, vb, rb, a.dist, a.seed, a.cpu_seconds, gvr=gvr, gsd=gsd)
         cpu = {"value": sn * len(times) / sum(times), "unit": "keys/s", "cores": 1,
                "kind": "oracle",
                "sample": f"{len(times)} single-thread oracle sorts of a {sn}-key slice "
@@ -521,6 +531,7 @@ def measure_e2e(a, n, kb, vb, rb, torch, isort, inputs, stream):
     steps = max(3, min(a.steps, 10))
 
     gvr = a.workload == "sample_2p28"
+    gsd = a.workload == "gsd_2p28"
 
     def step():
         dev.copy_(host_in, non_blocking=True)
@@ -528,6 +539,8 @@ def measure_e2e(a, n, kb, vb, rb, torch, isort, inputs, stream):
             dv.copy_(hv_in, non_blocking=True)
         if gvr:
             isort.sample_sort(dev, dv, buckets=256, oversample=16, seed=a.seed)
+        elif gsd:
+            isort.gsd_sort(dev, dv, buckets=16, oversample=4)
         elif vb:
             isort.sort_pairs(dev, dv, rb)
         else:
