@@ -147,6 +147,15 @@ def gsd_sort(keys, vals=None, buckets: int = 16, oversample: int = 4, bucket_cou
     return keys if vals is None else (keys, vals)
 
 
+def gsd_sort_workspace_size(n: int, key_bits: int = 32, val_bits: int = 0, buckets: int = 16,
+                            oversample: int = 4) -> int:
+    out = ctypes.c_size_t(0)
+    check(load().isort_gsd_sort_workspace_size(n, key_bits, val_bits, buckets, oversample,
+                                               ctypes.byref(out)),
+          "isort_gsd_sort_workspace_size")
+    return out.value
+
+
 def sample_sort_workspace_size(n: int, key_bits: int = 32, val_bits: int = 0, buckets: int = 256,
                                oversample: int = 16) -> int:
     out = ctypes.c_size_t(0)

@@ -200,23 +200,24 @@ struct PassParams {
 //   of(k, i)      the digit of this thread's key i (k = key[i]);
 //   keep(pos, d)  the key with digit d was placed at tile slot pos;
 //   staged(k, j)  the digit of the key at tile slot j (k = that key).
+// RadixDigit refers to the round's parameters (shift and mask stay where the
+// kernel received them instead of being copied into registers).
 struct RadixDigit {
-  int shift;
-  uint32_t mask;
+  const PassParams& p;
   template <typename K>
   __device__ __forceinline__ uint32_t operator()(K k) const {
-    return digit_of(k, shift, mask);
+    return digit_of(k, p.shift, p.mask);
   }
   template <typename K, int KPT>
   __device__ __forceinline__ void prepare(const K (&)[KPT]) {}
   template <typename K>
   __device__ __forceinline__ uint32_t of(K k, int) const {
-    return digit_of(k, shift, mask);
+    return digit_of(k, p.shift, p.mask);
   }
   __device__ __forceinline__ void keep(uint32_t, uint32_t) const {}
   template <typename K>
   __device__ __forceinline__ uint32_t staged(K k, int) const {
-    return digit_of(k, shift, mask);
+    return digit_of(k, p.shift, p.mask);
   }
 };
 
@@ -718,7 +719,7 @@ __device__ __forceinline__ void onesweep_tile(const PassParams& p, uint32_t tile
   if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 4] = globaltimer();
 
   tile_scatter<K, V, THREADS, KPT, FULL>(s_keys, s_vals, s_adj, val, rank2,
-                                         RadixDigit{p.shift, p.mask}, tile_n, wofs, kout, vout,
+                                         RadixDigit{p}, tile_n, wofs, kout, vout,
                                          bound, p.err);
   if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 5] = globaltimer();
 }
@@ -767,7 +768,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
   V* vout = static_cast<V*>(src ? p.vals[0] : p.vals[1]);
   const int64_t tile_base = (int64_t)tile * TILE;
   if constexpr (EARLY) {
-    RadixDigit dig{p.shift, p.mask};
+    RadixDigit dig{p};
     if (tile_n == TILE)
       onesweep_tile_early<K, V, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n,
                                                           kin, kout, vin, vout, p.base,
@@ -897,7 +898,7 @@ __device__ __forceinline__ void onesweep_tile_tma(const PassParams& p, uint32_t 
   __syncthreads();
   const NoVal nv[1] = {};
   tile_scatter<K, NoVal, THREADS, KPT, FULL>(s_keys, nullptr, s_adj, nv, rank2,
-                                             RadixDigit{p.shift, p.mask}, tile_n, wofs, kout,
+                                             RadixDigit{p}, tile_n, wofs, kout,
                                              nullptr, (uint32_t)p.n, p.err);
 }
 
@@ -1086,7 +1087,7 @@ __device__ __forceinline__ void onesweep_cluster_tile(const PassParams& p, uint3
   }
   __syncthreads();
   tile_scatter<K, V, THREADS, KPT, FULL>(s_keys, s_vals, s_adj, val, rank2,
-                                         RadixDigit{p.shift, p.mask}, tile_n, wofs, kout, vout,
+                                         RadixDigit{p}, tile_n, wofs, kout, vout,
                                          (uint32_t)p.n, p.err);
 }
 

@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp
   V* vout = static_cast<V*>(src ? p.vals[0] : p.vals[1]);
   if constexpr (HasVal<V>::value) vout += start;
   const uint32_t* base = sp.seg_base + ((size_t)slot * sp.passes + p.pass) * R;
-  RadixDigit dig{p.shift, p.mask};
+  RadixDigit dig{p};
   if (tile_n == TILE)
     onesweep_tile_early<K, V, BITS, THREADS, KPT, true>(p, tile, lt == 0, tile_base, tile_n, kin,
                                                         kout, vin, vout, base, (uint32_t)len,

@@ -118,6 +118,7 @@ class SortServer:
         self.failed = 0
         self.submitted = 0
         self.rejected = []
+        self.cancelled = []
         self.sched = threading.Thread(target=self._schedule, daemon=True)
         self.waiters = [threading.Thread(target=self._complete, args=(i,), daemon=True)
                         for i in range(self.num_streams)]
@@ -136,6 +137,20 @@ class SortServer:
             self.queue.append(req)
             self.cv.notify()
         return True
+
+    def cancel(self, req: Request) -> bool:
+        """Withdraw a request that is still waiting in the queue. Returns True if
+        it was withdrawn (it will never run and its done callback is never
+        called); a request already in a batch runs to completion (False)."""
+        with self.cv:
+            for i, r in enumerate(self.queue):
+                if r is req:
+                    del self.queue[i]
+                    self.submitted -= 1  # close() waits for what is still admitted
+                    self.cancelled.append(req)
+                    self.cv.notify_all()
+                    return True
+        return False
 
     def close(self, wait: bool = True):
         if wait:  # until every admitted request has completed (or failed to launch)

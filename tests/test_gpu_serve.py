@@ -80,3 +80,29 @@ def test_admission_budget_refuses_what_can_never_fit_and_serves_the_rest():
     for rid in got:
         k, _ = got[rid]
         assert (k[1:] >= k[:-1]).all()
+
+
+def test_cancelled_requests_never_run_and_the_rest_are_exact():
+    """A tight budget keeps most requests queued; the second half is withdrawn
+    right after submission. Withdrawn requests never reach the GPU or their done
+    callback; every request that ran gives the result of sorting it alone."""
+    got, done = collect()
+    n = 1 << 18
+    srv = serve.SortServer(budget_bytes=2 * n * 4, num_streams=1, max_batch_keys=n,
+                           max_batch_requests=1)
+    reqs = []
+    import time
+    for rid in range(24):
+        r = serve.Request(rid=rid, n=n, payload=False, arrival=time.perf_counter(),
+                          fill=make_fill(rid, n, False), done=done)
+        assert srv.submit(r)
+        reqs.append(r)
+    withdrawn = {r.rid for r in reqs[12:] if srv.cancel(r)}
+    srv.close()
+    assert not srv.errors
+    assert len(withdrawn) > 0  # the budget held them in the queue
+    assert set(got) == {r.rid for r in reqs} - withdrawn
+    assert {r.rid for r in srv.cancelled} == withdrawn
+    for rid, (k, _) in got.items():
+        alone = inputs.keys(n, 32, "uniform", seed=3, stream=inputs.STREAM_REQUEST_BASE + rid)
+        assert np.array_equal(k, oracle.radix_sort(alone))
