@@ -922,7 +922,42 @@ def run_ours_serve(a):
                 inputs.device_iota(n, 32, out=vals, cuda_stream=stream)
         return fill
 
-    def arm(batching, arr, duration):
+    # self-checks of the served loop: every 100th request and every request of
+    # at most 2^16 keys keeps a copy of its result (taken in its done callback,
+    # before its arena space is reused), verified after the run
+    kept = {}
+
+    def keep(r, keys, vals):
+        if r.rid % 100 == 0 or r.n <= (1 << 16):
+            kept[r.rid] = (r, keys.clone(), None if vals is None else vals.clone())
+            torch.cuda.current_stream().synchronize()
+
+    def verify():
+        """Each kept result equals the same request sorted alone (plain sort,
+        bit for bit, on the device); every 10th kept one also the CPU oracle."""
+        import oracle
+        bad = oracle_checked = 0
+        for i, (rid, (r, k, v)) in enumerate(sorted(kept.items())):
+            alone_k = torch.empty(r.n, dtype=torch.uint32, device="cuda")
+            alone_v = torch.empty(r.n, dtype=torch.uint32, device="cuda") if r.payload else None
+            make_fill(rid, r.n, r.payload)(alone_k, alone_v, torch.cuda.current_stream())
+            if r.payload:
+                isort.sort_pairs(alone_k, alone_v, 8)
+            else:
+                isort.sort_keys(alone_k, 8)
+            ok = torch.equal(alone_k, k) and (v is None or torch.equal(alone_v, v))
+            if ok and i % 10 == 0:
+                src = inputs.keys(r.n, 32, "uniform", seed=a.seed,
+                                  stream=inputs.STREAM_REQUEST_BASE + rid)
+                ok = bool(np.array_equal(k.cpu().numpy(), oracle.radix_sort(src)))
+                oracle_checked += 1
+            bad += 0 if ok else 1
+        return {"kept": len(kept), "mismatches": bad, "oracle_checked": oracle_checked,
+                "how": "every 100th request and all of at most 2^16 keys: bit-exact against the "
+                       "same request sorted alone on the device; every 10th of those against "
+                       "the CPU oracle"}
+
+    def arm(batching, arr, duration, done=None):
         srv = serve.SortServer(budget_bytes=40 << 30, num_streams=4, max_batch_keys=1 << 27,
                                max_batch_requests=2048, batching=batching)
         # warm-up: a few requests through the same server
@@ -935,7 +970,7 @@ def run_ours_serve(a):
         clocks.start()
         l0 = isort.launch_count()
         t0 = time.perf_counter()
-        reqs = serve.drive(srv, arr, sizes, payload, make_fill, duration_s=duration)
+        reqs = serve.drive(srv, arr, sizes, payload, make_fill, duration_s=duration, done=done)
         srv.close()
         wall = time.perf_counter() - t0
         launches = isort.launch_count() - l0
@@ -951,6 +986,13 @@ def run_ours_serve(a):
         return out
 
     served = arm(True, arrivals, a.serve_seconds)
+    # a separate, untimed served run of the trace's first seconds keeps and checks
+    # results (the copies would disturb the latencies of the timed run)
+    arm(True, arrivals, min(5.0, a.serve_seconds), done=keep)
+    served["self_check"] = verify()
+    if served["self_check"]["mismatches"]:
+        raise RuntimeError(f"served results differ: {served['self_check']}")
+    kept.clear()
     sequential = arm(False, arrivals, a.serve_seconds)
     # capacity: a backlog of the first 4,000 requests, all queued at t = 0
     backlog = np.zeros_like(arrivals)
