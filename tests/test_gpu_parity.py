@@ -300,3 +300,31 @@ def test_full_size_pairs_2p27_and_u64_2p26():
     isort.sort_keys(k, 8)
     assert isort.stream_status() == _lib.OK
     assert np.array_equal(to_host(k), oracle.radix_sort(kin, radix_bits=8))
+
+
+@pytest.mark.slow
+def test_max_size_2p30_u32():
+    """n = 2^30, the largest n the 30-bit look-back counts allow: the output is
+    non-decreasing and every digit histogram (each byte position) of the
+    output equals the input's -- the paper's invariants, which hold at any size
+    -- and the first and last 2^20 keys equal the oracle's sort of the whole
+    input at those positions (the oracle sorts the 4 GiB input on the host)."""
+    n = 1 << 30
+    t = inputs.device_keys(n, 32, "uniform", seed=3)
+    before = [torch.bincount(((t.view(torch.int32) >> (8 * b)) & 0xFF).to(torch.int64),
+                             minlength=256) for b in range(4)]
+    isort.sort_keys(t, 8)
+    assert isort.stream_status() == _lib.OK
+    sk = t.view(torch.int32) ^ (-(1 << 31))  # unsigned order as signed
+    assert bool((sk[1:] >= sk[:-1]).all())
+    del sk
+    for b in range(4):
+        after = torch.bincount(((t.view(torch.int32) >> (8 * b)) & 0xFF).to(torch.int64),
+                               minlength=256)
+        assert torch.equal(after, before[b]), b
+    head, tail = to_host(t[: 1 << 20]), to_host(t[-(1 << 20):])
+    del t
+    torch.cuda.empty_cache()
+    src = to_host(inputs.device_keys(n, 32, "uniform", seed=3))  # the same input, again
+    want = oracle.radix_sort(src, radix_bits=8)
+    assert np.array_equal(head, want[: 1 << 20]) and np.array_equal(tail, want[-(1 << 20):])
