@@ -788,6 +788,135 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
 }
 
 // ---------------------------------------------------------------------------
+// First round of a keys-only sort. Radix sort needs every round to be stable
+// so that a round keeps the order the earlier rounds made; the first round has
+// no earlier round, and keys with equal digits in it may land in any order
+// without changing the final (unique) sorted result. So this round drops the
+// stable rank: a key's tile slot is the return value of one shared atomic add
+// on its digit's counter (which holds the tile start of the digit after the
+// scan). Per key that is a count add, a slot add and the store into the
+// staging area, against the stable round's count, mark, mask read, counter
+// update, mask clear and store. Later rounds keep the stable rank.
+template <typename K, int BITS, int THREADS, int KPT>
+struct FirstShape {
+  using S = OnesweepShape<K, NoVal, BITS, THREADS, KPT>;
+  static constexpr int HEADER_WORDS = 2 * S::R + 64;  // s_slot, s_adj, s_misc
+  static constexpr size_t SMEM = (size_t)HEADER_WORDS * 4 + (size_t)S::TILE * sizeof(K);
+};
+
+// Arguments as for onesweep_tile_early (keys only).
+template <typename K, int BITS, int THREADS, int KPT, bool FULL, typename DS = RadixDigit>
+__device__ __forceinline__ void onesweep_tile_first(const PassParams& p, uint32_t tile, bool first,
+                                                    int64_t tile_base, int tile_n,
+                                                    const K* __restrict__ kin,
+                                                    K* __restrict__ kout, const uint32_t* base,
+                                                    uint32_t bound, unsigned char* smem,
+                                                    DS& dig) {
+  using S = OnesweepShape<K, NoVal, BITS, THREADS, KPT>;
+  using F = FirstShape<K, BITS, THREADS, KPT>;
+  constexpr int R = S::R, DPT = S::DPT;
+  uint32_t* s_slot = reinterpret_cast<uint32_t*>(smem);  // [R] counts, then next free slot
+  uint32_t* s_adj = s_slot + R;                           // [R]
+  uint32_t* s_misc = s_adj + R;                           // [64]
+  K* s_keys = reinterpret_cast<K*>(smem + F::HEADER_WORDS * 4);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wofs = warp * 32 * KPT + lane;
+  const bool publish = (int64_t)tile != p.stall_tile;
+
+  K key[KPT];
+  NoVal val[1];
+  tile_load<K, NoVal, KPT, FULL>(kin, nullptr, tile_base, tile_n, wofs, key, val);
+  dig.prepare(key);
+#pragma unroll
+  for (int i = 0; i < KPT; ++i)
+    if (FULL || wofs + i * 32 < tile_n) atomicAdd(&s_slot[dig.of(key[i], i)], 1u);
+  __syncthreads();
+
+  uint32_t dcnt[DPT];
+  uint32_t tsum = 0;
+  const bool owner = tid < S::DTHREADS;
+  if (owner) {
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+      dcnt[j] = s_slot[tid * DPT + j];
+      tsum += dcnt[j];
+      if (publish)
+        st_relaxed(&p.status[(size_t)tile * R + tid * DPT + j],
+                   (first ? kFlagInc : kFlagAgg) | dcnt[j]);
+    }
+  }
+  uint32_t total;
+  uint32_t run = block_exclusive_scan<THREADS>(tsum, s_misc + 1, total);
+  uint32_t tstart[DPT];
+  if (owner) {
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+      tstart[j] = run;
+      s_slot[tid * DPT + j] = run;
+      run += dcnt[j];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < KPT; ++i)
+    if (FULL || wofs + i * 32 < tile_n) {
+      const uint32_t d = dig.of(key[i], i);
+      const uint32_t pos = atomicAdd(&s_slot[d], 1u);
+      s_keys[pos] = key[i];
+      dig.keep(pos, d);
+    }
+
+  uint32_t windows = 0;
+  if (owner) {
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+      const int d = tid * DPT + j;
+      uint32_t excl = 0;
+      if (!first) {
+        excl = lookback_exclusive<R, kLookbackWindow>(p.status, tile, d, p.spin_limit, p.err,
+                                                      windows);
+        if (publish) st_relaxed(&p.status[(size_t)tile * R + d], kFlagInc | (excl + dcnt[j]));
+      }
+      s_adj[d] = base[d] + excl - tstart[j];
+    }
+  }
+  __syncthreads();
+  uint32_t rank2[(KPT + 1) / 2];
+  tile_scatter<K, NoVal, THREADS, KPT, FULL>(s_keys, nullptr, s_adj, val, rank2, dig, tile_n,
+                                             wofs, kout, nullptr, bound, p.err);
+}
+
+// The first round (pass 0) of a keys-only sort; a skipped pass 0 leaves the
+// first executed round to the stable kernel.
+template <typename K, int BITS, int THREADS, int KPT, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_onesweep_first(PassParams p) {
+  using S = OnesweepShape<K, NoVal, BITS, THREADS, KPT>;
+  constexpr int R = S::R, TILE = S::TILE;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* s_slot = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* s_misc = s_slot + 2 * R;
+  const int tid = threadIdx.x;
+  if (p.status_next)
+    for (int d = tid; d < R; d += THREADS) p.status_next[(size_t)blockIdx.x * R + d] = 0;
+  if (p.skip[0]) return;
+  if (tid == 0) s_misc[0] = atomicAdd(p.counter, 1u);  // tiles in launch order
+  zero_words<THREADS>(s_slot, R);
+  __syncthreads();
+  const uint32_t tile = s_misc[0];
+  const int tile_n = (int)min((int64_t)TILE, p.n - (int64_t)tile * TILE);
+  const K* kin = static_cast<const K*>(p.keys[0]);
+  K* kout = static_cast<K*>(p.keys[1]);
+  const int64_t tile_base = (int64_t)tile * TILE;
+  RadixDigit dig{p};
+  if (tile_n == TILE)
+    onesweep_tile_first<K, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n, kin,
+                                                     kout, p.base, (uint32_t)p.n, smem, dig);
+  else
+    onesweep_tile_first<K, BITS, THREADS, KPT, false>(p, tile, tile == 0, tile_base, tile_n, kin,
+                                                      kout, p.base, (uint32_t)p.n, smem, dig);
+}
+
+// ---------------------------------------------------------------------------
 // TMA variant of the round (keys only): one thread issues bulk copies of the
 // whole tile into shared memory as soon as the tile id is known, completing on
 // an mbarrier, while the CTA clears its counters. Ranking and the reorder read
@@ -1212,6 +1341,13 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
       if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return e;
     }
+    // keys only: pass 0 drops the stable rank (k_onesweep_first), unless it is traced
+    constexpr size_t fsmem = FirstShape<K, BITS, THREADS, KPT>::SMEM;
+    if constexpr (!HasVal<V>::value && fsmem > 48 * 1024) {
+      if ((e = cudaFuncSetAttribute(k_onesweep_first<K, BITS, THREADS, KPT, MINB>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem)))
+        return e;
+    }
     for (int q = 0; q < P; ++q) {
       pp.pass = q;
       pp.shift = q * BITS;
@@ -1222,8 +1358,18 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
       pp.counter = a.counters + q;
       pp.stall_tile = (q == 0) ? a.stall_tile : -1;
       pp.trace = (q == a.trace_pass) ? a.trace : nullptr;
-      timer_begin(a.timer, "k_onesweep", st);
-      kern<<<(unsigned)tiles, THREADS, smem, st>>>(pp);
+      bool launched = false;
+      if constexpr (!HasVal<V>::value) {
+        if (q == 0 && !pp.trace) {
+          timer_begin(a.timer, "k_onesweep_first", st);
+          k_onesweep_first<K, BITS, THREADS, KPT, MINB><<<(unsigned)tiles, THREADS, fsmem, st>>>(pp);
+          launched = true;
+        }
+      }
+      if (!launched) {
+        timer_begin(a.timer, "k_onesweep", st);
+        kern<<<(unsigned)tiles, THREADS, smem, st>>>(pp);
+      }
       timer_end(a.timer, st);
     }
   } else {

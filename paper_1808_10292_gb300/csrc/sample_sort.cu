@@ -207,19 +207,26 @@ __global__ void __launch_bounds__(THREADS, MINB) k_gvr_split(PassParams p,
                                                              const uint16_t* __restrict__ cell) {
   using S = OnesweepShape<K, V, 8, THREADS, KPT>;
   using E = EarlyShape<K, V, 8, THREADS, KPT>;
+  // keys only: the split round is the first round over the input, so the
+  // order of keys within a bucket is free (onesweep_tile_first)
+  constexpr bool FIRST = !HasVal<V>::value;
   constexpr int R = S::R, WARPS = S::WARPS, TILE = S::TILE;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ K s_split[kMaxSplit];
   __shared__ uint16_t s_cell[kCells];
   uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* s_misc = s_wcnt + WARPS * R + R;
+  uint32_t* s_misc = FIRST ? s_wcnt + 2 * R : s_wcnt + WARPS * R + R;
   uint32_t* s_masks = reinterpret_cast<uint32_t*>(smem + E::MASKS);
   const int tid = threadIdx.x;
   for (int i = tid; i < kMaxSplit; i += THREADS) s_split[i] = split[i];
   for (int i = tid; i < kCells; i += THREADS) s_cell[i] = cell[i];
   if (tid == 0) s_misc[0] = atomicAdd(p.counter, 1u);  // tiles in launch order
-  zero_words<THREADS>(s_wcnt, WARPS * R);
-  zero_words<THREADS>(s_masks, WARPS * S::MASK_BUFS * R);
+  if constexpr (FIRST) {
+    zero_words<THREADS>(s_wcnt, R);
+  } else {
+    zero_words<THREADS>(s_wcnt, WARPS * R);
+    zero_words<THREADS>(s_masks, WARPS * S::MASK_BUFS * R);
+  }
   __syncthreads();
   const uint32_t tile = s_misc[0];
   const int tile_n = (int)min((int64_t)TILE, p.n - (int64_t)tile * TILE);
@@ -236,8 +243,18 @@ __global__ void __launch_bounds__(THREADS, MINB) k_gvr_split(PassParams p,
   CachedSplitDigit<K, KPT> dig;
   dig.s = s_split;
   dig.cell = s_cell;
-  dig.s_slot = smem + E::SMEM;
   const int64_t tile_base = (int64_t)tile * TILE;
+  if constexpr (FIRST) {
+    dig.s_slot = smem + FirstShape<K, 8, THREADS, KPT>::SMEM;
+    if (tile_n == TILE)
+      onesweep_tile_first<K, 8, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n, kin,
+                                                    kout, p.base, (uint32_t)p.n, smem, dig);
+    else
+      onesweep_tile_first<K, 8, THREADS, KPT, false>(p, tile, tile == 0, tile_base, tile_n, kin,
+                                                     kout, p.base, (uint32_t)p.n, smem, dig);
+    return;
+  }
+  dig.s_slot = smem + E::SMEM;
   if (tile_n == TILE)
     onesweep_tile_early<K, V, 8, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n, kin,
                                                      kout, vin, vout, p.base, (uint32_t)p.n,
@@ -294,8 +311,9 @@ cudaError_t gvr_launch(const GvrArgs& a, cudaStream_t st) {
   pp.trace = nullptr;
   pp.prefetch_tiles = (int64_t)a.num_sms * 4;
   auto kern = k_gvr_split<K, V, THREADS, KPT, MINB>;
-  // the early-counts layout, then one bucket byte per tile slot
-  const size_t smem = EarlyShape<K, V, 8, THREADS, KPT>::SMEM + S::TILE;
+  // the round's layout (order-free for keys only), then one bucket byte per tile slot
+  const size_t smem = (HasVal<V>::value ? EarlyShape<K, V, 8, THREADS, KPT>::SMEM
+                                        : FirstShape<K, 8, THREADS, KPT>::SMEM) + S::TILE;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
     return e;
   timer_begin(a.timer, "k_gvr_split", st);

@@ -260,22 +260,28 @@ struct SegPassParams {
   int passes;
 };
 
-template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB>
+// FIRST (keys only, pass 0): the order-free first round of onesweep_tile_first.
+template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB, bool FIRST = false>
 __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp) {
+  static_assert(!FIRST || !HasVal<V>::value, "the order-free round is keys-only");
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
   using E = EarlyShape<K, V, BITS, THREADS, KPT>;
   constexpr int R = S::R, WARPS = S::WARPS, TILE = S::TILE;
   const PassParams& p = sp.p;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* s_misc = s_wcnt + WARPS * R + R;
+  uint32_t* s_misc = FIRST ? s_wcnt + 2 * R : s_wcnt + WARPS * R + R;
   uint32_t* s_stage = reinterpret_cast<uint32_t*>(smem + E::MASKS);  // the peer masks
   const int tid = threadIdx.x;
   if (p.status_next)
     for (int d = tid; d < R; d += THREADS) p.status_next[(size_t)blockIdx.x * R + d] = 0;
   if (tid == 0) s_misc[0] = atomicAdd(p.counter, 1u);
-  for (int i = tid; i < WARPS * R; i += THREADS) s_wcnt[i] = 0;
-  for (int i = tid; i < WARPS * S::MASK_BUFS * R; i += THREADS) s_stage[i] = 0;
+  if constexpr (FIRST) {
+    zero_words<THREADS>(s_wcnt, R);
+  } else {
+    for (int i = tid; i < WARPS * R; i += THREADS) s_wcnt[i] = 0;
+    for (int i = tid; i < WARPS * S::MASK_BUFS * R; i += THREADS) s_stage[i] = 0;
+  }
   __syncthreads();
   const uint32_t tile = s_misc[0];
   if (tile >= sp.cnt[kCntTiles]) return;  // more CTAs than tiles: nothing left
@@ -293,6 +299,15 @@ __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp
   if constexpr (HasVal<V>::value) vout += start;
   const uint32_t* base = sp.seg_base + ((size_t)slot * sp.passes + p.pass) * R;
   RadixDigit dig{p};
+  if constexpr (FIRST) {
+    if (tile_n == TILE)
+      onesweep_tile_first<K, BITS, THREADS, KPT, true>(p, tile, lt == 0, tile_base, tile_n, kin,
+                                                       kout, base, (uint32_t)len, smem, dig);
+    else
+      onesweep_tile_first<K, BITS, THREADS, KPT, false>(p, tile, lt == 0, tile_base, tile_n, kin,
+                                                        kout, base, (uint32_t)len, smem, dig);
+    return;
+  }
   if (tile_n == TILE)
     onesweep_tile_early<K, V, BITS, THREADS, KPT, true>(p, tile, lt == 0, tile_base, tile_n, kin,
                                                         kout, vin, vout, base, (uint32_t)len,
@@ -376,6 +391,12 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
                                   (int)SEG_SMEM)))
       return e;
   }
+  if constexpr (!HasVal<V>::value && FirstShape<K, 8, THREADS, KPT>::SMEM > 48 * 1024) {
+    if ((e = cudaFuncSetAttribute(k_seg_onesweep<K, V, 8, THREADS, KPT, MINB, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)FirstShape<K, 8, THREADS, KPT>::SMEM)))
+      return e;
+  }
   SegPassParams sp;
   sp.off = a.offsets;
   sp.nseg = a.nseg;
@@ -406,6 +427,15 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
     pp.status = a.status[q & 1];
     pp.status_next = (q + 1 < P) ? a.status[(q + 1) & 1] : nullptr;
     pp.counter = a.cnt + kCntPassTiles + q;
+    if constexpr (!HasVal<V>::value) {
+      if (q == 0) {  // keys only: the order-free first round
+        timer_begin(a.timer, "k_seg_onesweep_first", st);
+        k_seg_onesweep<K, V, 8, THREADS, KPT, MINB, true>
+            <<<(unsigned)a.max_tiles, THREADS, FirstShape<K, 8, THREADS, KPT>::SMEM, st>>>(sp);
+        timer_end(a.timer, st);
+        continue;
+      }
+    }
     timer_begin(a.timer, "k_seg_onesweep", st);
     kern<<<(unsigned)a.max_tiles, THREADS, SEG_SMEM, st>>>(sp);
     timer_end(a.timer, st);

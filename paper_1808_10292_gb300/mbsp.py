@@ -85,6 +85,10 @@ def speedup_bound_gsd(p: int) -> float:
 # count, mark, mask read, counter update (by one lane per digit group, counted
 # per key), key store, mask clear, staged read, offset read.
 SHARED_ACCESSES_ONESWEEP = 8
+# The first round of a keys-only sort keeps no order among equal digits:
+# count add, slot add (its return value is the tile slot), key store, staged
+# read, offset read.
+SHARED_ACCESSES_FIRST = 5
 # Per key of a wide-radix scatter: two stable 8-bit partitions (mark, mask read,
 # counter, store of key and index each), the run pass (read key and index, run
 # edges) and the offset update.
@@ -114,12 +118,15 @@ def gpu_wide_round(n: float, words_per_item: float, key_words: float, g: float, 
 
 def gpu_sort(n: float, key_bits: int, val_bits: int, r: int, g: float, G: float,
              block_keys: int | None = None) -> float:
-    """Model time of one whole sort of n keys at radix r (all rounds executed)."""
+    """Model time of one whole sort of n keys at radix r (all rounds executed;
+    keys only at radix 256: the first round is the order-free one)."""
     kw = key_bits / 32
     w = kw + val_bits / 32
     P = rounds(key_bits, r)
     if r == 256:
-        return gpu_histogram(n, kw, P, g, G) + P * gpu_onesweep_round(n, w, g, G)
+        first = SHARED_ACCESSES_FIRST if val_bits == 0 else SHARED_ACCESSES_ONESWEEP
+        return (gpu_histogram(n, kw, P, g, G) + gpu_onesweep_round(n, w, g, G, first) +
+                (P - 1) * gpu_onesweep_round(n, w, g, G))
     blocks = -(-int(n) // (block_keys or (1 << 19 if r == 65536 else 1 << 16)))
     return P * gpu_wide_round(n, w, kw, g, G, r, blocks)
 

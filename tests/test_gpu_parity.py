@@ -328,3 +328,55 @@ def test_max_size_2p30_u32():
     src = to_host(inputs.device_keys(n, 32, "uniform", seed=3))  # the same input, again
     want = oracle.radix_sort(src, radix_bits=8)
     assert np.array_equal(head, want[: 1 << 20]) and np.array_equal(tail, want[-(1 << 20):])
+
+
+def kernels_of_one_sort(run):
+    isort.debug_set(_lib.DEBUG_KERNEL_TIMING, 1)
+    try:
+        run()
+        torch.cuda.synchronize()
+        return [name for name, _ in isort.kernel_times()]
+    finally:
+        isort.debug_set(_lib.DEBUG_KERNEL_TIMING, 0)
+
+
+@pytest.mark.parametrize("key_bits", [32, 64])
+def test_keys_only_first_round_is_order_free_and_exact(key_bits):
+    """Keys only: pass 0 runs the order-free first round (k_onesweep_first),
+    the other passes the stable round; pairs keep the stable round in pass 0.
+    Either way the result is the oracle's, bit for bit."""
+    n = 3 * 8192 * 5 + 77  # many tiles of every variant, a ragged tail
+    k = inputs.keys(n, key_bits, "uniform", seed=31)
+    want = oracle.radix_sort(k, radix_bits=8)
+    for v in range(len(isort.tune_variants(key_bits, 0, 8))):
+        isort.tune_set(key_bits, 0, 8, v)
+        try:
+            t = to_dev(k)
+            names = kernels_of_one_sort(lambda: isort.sort_keys(t, 8))
+            assert isort.stream_status() == _lib.OK
+            assert np.array_equal(to_host(t), want), v
+        finally:
+            isort.tune_set(key_bits, 0, 8, -1)
+        passes = key_bits // 8
+        rounds = names.count("k_onesweep_first") + names.count("k_onesweep")
+        assert rounds == passes, names
+        cluster = names.count("k_onesweep_first") == 0
+        assert cluster or names.index("k_onesweep_first") < names.index("k_onesweep"), names
+    v = inputs.iota(n)
+    t, tv = to_dev(k), to_dev(v)
+    names = kernels_of_one_sort(lambda: isort.sort_pairs(t, tv, 8))
+    assert "k_onesweep_first" not in names
+    wk, wv = oracle.radix_sort(k, v, radix_bits=8)
+    assert np.array_equal(to_host(t), wk) and np.array_equal(to_host(tv), wv)
+
+
+@pytest.mark.parametrize("key_bits", [32, 64])
+def test_keys_only_constant_low_digit(key_bits):
+    """Digit 0 constant: pass 0 is skipped inside the order-free kernel, and the
+    first executed round is the stable one. Digits 0 and 1 constant as well."""
+    n = 100_003
+    base = inputs.keys(n, key_bits, "uniform", seed=32)
+    for shift in (8, 16):
+        k = (base >> np.array(shift, dtype=base.dtype)) << np.array(shift, dtype=base.dtype)
+        k = k | np.array(0x5A, dtype=base.dtype)  # digit 0 = 0x5A, not zero
+        assert np.array_equal(gpu_sort(k), oracle.radix_sort(k, radix_bits=8)), shift

@@ -97,3 +97,13 @@ def test_network_ratio_limits():
     assert mbsp.network_time_ratio(256, 0.0) == pytest.approx(256 / 36)
     assert mbsp.network_time_ratio(32, 0.0) == pytest.approx(32 / 15)
     assert mbsp.network_time_ratio(64, 1.0) == pytest.approx(1.0)
+
+
+def test_gpu_sort_keys_only_first_round_is_cheaper_by_three_shared_accesses():
+    """Keys only at radix 256: the order-free first round saves the mark, the
+    mask read and the mask clear (3 shared accesses per key); pairs do not."""
+    n, g, G = 1 << 20, 2.0, 1.0
+    stable = mbsp.gpu_histogram(n, 1, 4, g, G) + 4 * mbsp.gpu_onesweep_round(n, 1, g, G)
+    assert mbsp.gpu_sort(n, 32, 0, 256, g, G) == pytest.approx(stable - 3 * n * G)
+    pairs = mbsp.gpu_histogram(n, 1, 4, g, G) + 4 * mbsp.gpu_onesweep_round(n, 2, g, G)
+    assert mbsp.gpu_sort(n, 32, 32, 256, g, G) == pytest.approx(pairs)
