@@ -463,6 +463,14 @@ def run_ours(a):
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
                 "avg_launch_ms": dom_ms, "launches": len(kernel_ms[dom])}
+    # keys only: the order-free pass-0 round is its own kernel; same algorithmic bytes
+    first = next((k for k in ("k_onesweep_first", "k_seg_onesweep_first") if k in kernel_ms), None)
+    if first and dom in ("k_onesweep", "k_seg_onesweep"):
+        f_ms = statistics.mean(kernel_ms[first])
+        roofline["first_round"] = {"kernel": first, "avg_launch_ms": f_ms,
+                                   "achieved": alg_bytes / (f_ms / 1000.0) / 1e9,
+                                   "frac": alg_bytes / (f_ms / 1000.0) / 1e9 / peak,
+                                   "launches": len(kernel_ms[first])}
     # whole-sort roofline by the headline formula: 2 n (w_k + w_v) per executed pass
     sort_alg_bytes = 2 * n * bytes_per_key * passes
     per_kernel = {k: {"launches": len(v), "mean_ms": statistics.mean(v), "total_ms": sum(v)}

@@ -797,6 +797,21 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
 // scan). Per key that is a count add, a slot add and the store into the
 // staging area, against the stable round's count, mark, mask read, counter
 // update, mask clear and store. Later rounds keep the stable rank.
+// The first round's CTA shape for a stable round of THREADS x KPT at MINB
+// CTAs per SM: the same tile (so the look-back rows match), with twice the
+// threads holding half the keys each where their registers fit (the keys'
+// words plus about 26 more per thread, against 65536 / (threads x MINB)).
+// The round keeps no ranks or peer masks, so it needs fewer registers than the
+// stable round; more warps per SM hide more of the load and atomic latency.
+template <typename K, int THREADS, int KPT, int MINB>
+struct FirstCfg {
+  static constexpr bool WIDE = KPT % 2 == 0 && THREADS * 2 <= 1024 &&
+                               (KPT / 2) * (int)(sizeof(K) / 4) + 26 <= 65536 / (2 * THREADS * MINB);
+  static constexpr int T = WIDE ? THREADS * 2 : THREADS;
+  static constexpr int KP = WIDE ? KPT / 2 : KPT;
+  static_assert(T * KP == THREADS * KPT, "same tile as the stable round");
+};
+
 template <typename K, int BITS, int THREADS, int KPT>
 struct FirstShape {
   using S = OnesweepShape<K, NoVal, BITS, THREADS, KPT>;
@@ -1342,9 +1357,10 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
         return e;
     }
     // keys only: pass 0 drops the stable rank (k_onesweep_first), unless it is traced
-    constexpr size_t fsmem = FirstShape<K, BITS, THREADS, KPT>::SMEM;
+    using FC = FirstCfg<K, THREADS, KPT, MINB>;
+    constexpr size_t fsmem = FirstShape<K, BITS, FC::T, FC::KP>::SMEM;
     if constexpr (!HasVal<V>::value && fsmem > 48 * 1024) {
-      if ((e = cudaFuncSetAttribute(k_onesweep_first<K, BITS, THREADS, KPT, MINB>,
+      if ((e = cudaFuncSetAttribute(k_onesweep_first<K, BITS, FC::T, FC::KP, MINB>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem)))
         return e;
     }
@@ -1362,7 +1378,7 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
       if constexpr (!HasVal<V>::value) {
         if (q == 0 && !pp.trace) {
           timer_begin(a.timer, "k_onesweep_first", st);
-          k_onesweep_first<K, BITS, THREADS, KPT, MINB><<<(unsigned)tiles, THREADS, fsmem, st>>>(pp);
+          k_onesweep_first<K, BITS, FC::T, FC::KP, MINB><<<(unsigned)tiles, FC::T, fsmem, st>>>(pp);
           launched = true;
         }
       }

@@ -310,14 +310,18 @@ cudaError_t gvr_launch(const GvrArgs& a, cudaStream_t st) {
   pp.stall_tile = -1;
   pp.trace = nullptr;
   pp.prefetch_tiles = (int64_t)a.num_sms * 4;
-  auto kern = k_gvr_split<K, V, THREADS, KPT, MINB>;
-  // the round's layout (order-free for keys only), then one bucket byte per tile slot
-  const size_t smem = (HasVal<V>::value ? EarlyShape<K, V, 8, THREADS, KPT>::SMEM
-                                        : FirstShape<K, 8, THREADS, KPT>::SMEM) + S::TILE;
+  // keys only: the order-free round, in its own CTA shape (same tile)
+  using FC = FirstCfg<K, THREADS, KPT, MINB>;
+  constexpr bool HV = HasVal<V>::value;
+  constexpr int CT = HV ? THREADS : FC::T, CK = HV ? KPT : FC::KP;
+  auto kern = k_gvr_split<K, V, CT, CK, MINB>;
+  // the round's layout, then one bucket byte per tile slot
+  const size_t smem =
+      (HV ? EarlyShape<K, V, 8, CT, CK>::SMEM : FirstShape<K, 8, CT, CK>::SMEM) + S::TILE;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
     return e;
   timer_begin(a.timer, "k_gvr_split", st);
-  kern<<<(unsigned)tiles, THREADS, smem, st>>>(pp, split, cell);
+  kern<<<(unsigned)tiles, CT, smem, st>>>(pp, split, cell);
   timer_end(a.timer, st);
   return cudaGetLastError();
 }

@@ -391,10 +391,11 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
                                   (int)SEG_SMEM)))
       return e;
   }
-  if constexpr (!HasVal<V>::value && FirstShape<K, 8, THREADS, KPT>::SMEM > 48 * 1024) {
-    if ((e = cudaFuncSetAttribute(k_seg_onesweep<K, V, 8, THREADS, KPT, MINB, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)FirstShape<K, 8, THREADS, KPT>::SMEM)))
+  using FC = FirstCfg<K, THREADS, KPT, MINB>;  // the order-free first round's CTA shape
+  constexpr size_t FIRST_SMEM = FirstShape<K, 8, FC::T, FC::KP>::SMEM;
+  if constexpr (!HasVal<V>::value && FIRST_SMEM > 48 * 1024) {
+    if ((e = cudaFuncSetAttribute(k_seg_onesweep<K, V, 8, FC::T, FC::KP, MINB, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FIRST_SMEM)))
       return e;
   }
   SegPassParams sp;
@@ -430,8 +431,8 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
     if constexpr (!HasVal<V>::value) {
       if (q == 0) {  // keys only: the order-free first round
         timer_begin(a.timer, "k_seg_onesweep_first", st);
-        k_seg_onesweep<K, V, 8, THREADS, KPT, MINB, true>
-            <<<(unsigned)a.max_tiles, THREADS, FirstShape<K, 8, THREADS, KPT>::SMEM, st>>>(sp);
+        k_seg_onesweep<K, V, 8, FC::T, FC::KP, MINB, true>
+            <<<(unsigned)a.max_tiles, FC::T, FIRST_SMEM, st>>>(sp);
         timer_end(a.timer, st);
         continue;
       }
