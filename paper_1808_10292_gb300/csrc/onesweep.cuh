@@ -481,13 +481,38 @@ __device__ __forceinline__ void tile_count(const K (&key)[KPT], const DS& dig, i
 // key (peer masks, as in tile_rank) is its final tile position and the key is
 // written straight into the staging area. The masks live in a separate area
 // (the staging area is being filled). rank2 receives the positions.
-template <typename K, int R, int KPT, int MASK_BUFS, bool FULL, typename DS>
+//
+// RELAX (keys only, rounds after the first): the round's input is sorted by
+// the key bits below its digit (`low`), so keys with equal digits need their
+// input order kept only where those low bits differ. When all of the warp's
+// keys share the low bits (its first and last key agree on them), the warp
+// places equal digits in any order: every key takes its slot with its own add
+// on the warp's counter, with no masks. The warps' counters start at their own
+// offsets, so the order between warps is kept either way.
+template <typename K, int R, int KPT, int MASK_BUFS, bool FULL, bool RELAX = false,
+          typename DS>
 __device__ __forceinline__ void tile_rank_place(const K (&key)[KPT], const DS& dig, int tile_n,
                                                 int wofs, uint32_t* my,
                                                 uint32_t* mm, K* s_keys,
-                                                uint32_t (&rank2)[(KPT + 1) / 2]) {
+                                                uint32_t (&rank2)[(KPT + 1) / 2], K low = 0) {
   static_assert(MASK_BUFS == 3, "row r marks slot array r mod 3");
   const int lane = threadIdx.x & 31;
+  if constexpr (RELAX) {
+    const K first = __shfl_sync(kFullMask, key[0], 0);
+    const K last = __shfl_sync(kFullMask, key[KPT - 1], 31);
+    const bool full = FULL || wofs - lane + KPT * 32 <= tile_n;
+    if (full && ((first ^ last) & low) == 0) {  // warp-uniform
+#pragma unroll
+      for (int i = 0; i < KPT; ++i) {
+        const uint32_t d = dig.of(key[i], i);
+        const uint32_t pos = atomicAdd(&my[d], 1u);
+        s_keys[pos] = key[i];
+        dig.keep(pos, d);
+        rank2[i >> 1] = (i & 1) ? (rank2[i >> 1] | (pos << 16)) : pos;
+      }
+      return;
+    }
+  }
   const uint32_t ge = lanemask_ge();
   const uint32_t bit = 1u << lane;
   auto valid_row = [&](int i) { return FULL || wofs + i * 32 < tile_n; };
@@ -549,8 +574,9 @@ struct EarlyShape {
 // tile's counts, scan, rank straight into the reordered tile, look back,
 // publish the inclusive counts, write out.
 // dig: the key -> digit rule of this round (RadixDigit for a radix round).
+// RELAX: see tile_rank_place (keys only, RadixDigit rounds).
 template <typename K, typename V, int BITS, int THREADS, int KPT, bool FULL,
-          typename DS = RadixDigit>
+          typename DS = RadixDigit, bool RELAX = false>
 __device__ __forceinline__ void onesweep_tile_early(const PassParams& p, uint32_t tile, bool first,
                                                     int64_t tile_base, int tile_n,
                                                     const K* __restrict__ kin,
@@ -606,10 +632,13 @@ __device__ __forceinline__ void onesweep_tile_early(const PassParams& p, uint32_
   }
   __syncthreads();
   uint32_t rank2[(KPT + 1) / 2];
-  tile_rank_place<K, R, KPT, S::MASK_BUFS, FULL>(key, dig, tile_n, wofs,
-                                                 s_wcnt + warp * R,
-                                                 s_masks + warp * S::MASK_BUFS * R, s_keys,
-                                                 rank2);
+  static_assert(!RELAX || !HV, "equal keys keep their payloads' order: no relaxed warps");
+  K low = 0;  // key bits below this round's digit
+  if constexpr (RELAX) low = p.shift ? (K(1) << p.shift) - K(1) : K(0);
+  tile_rank_place<K, R, KPT, S::MASK_BUFS, FULL, RELAX>(key, dig, tile_n, wofs,
+                                                        s_wcnt + warp * R,
+                                                        s_masks + warp * S::MASK_BUFS * R,
+                                                        s_keys, rank2, low);
   if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 2] = globaltimer();
 
   // look back over earlier tiles, publish the inclusive counts, output offsets
@@ -769,14 +798,17 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
   const int64_t tile_base = (int64_t)tile * TILE;
   if constexpr (EARLY) {
     RadixDigit dig{p};
+    // keys only, 32-bit keys (for 64-bit keys the extra registers of the test
+    // spill in every round, and only rounds 1 and 2 have shared low bits)
+    constexpr bool RELAX = !HasVal<V>::value && sizeof(K) == 4;
     if (tile_n == TILE)
-      onesweep_tile_early<K, V, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n,
-                                                          kin, kout, vin, vout, p.base,
-                                                          (uint32_t)p.n, smem, dig);
+      onesweep_tile_early<K, V, BITS, THREADS, KPT, true, RadixDigit, RELAX>(
+          p, tile, tile == 0, tile_base, tile_n, kin, kout, vin, vout, p.base, (uint32_t)p.n,
+          smem, dig);
     else
-      onesweep_tile_early<K, V, BITS, THREADS, KPT, false>(p, tile, tile == 0, tile_base,
-                                                           tile_n, kin, kout, vin, vout, p.base,
-                                                           (uint32_t)p.n, smem, dig);
+      onesweep_tile_early<K, V, BITS, THREADS, KPT, false, RadixDigit, RELAX>(
+          p, tile, tile == 0, tile_base, tile_n, kin, kout, vin, vout, p.base, (uint32_t)p.n,
+          smem, dig);
   } else {
     if (tile_n == TILE)
       onesweep_tile<K, V, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n, kin,

@@ -380,3 +380,30 @@ def test_keys_only_constant_low_digit(key_bits):
         k = (base >> np.array(shift, dtype=base.dtype)) << np.array(shift, dtype=base.dtype)
         k = k | np.array(0x5A, dtype=base.dtype)  # digit 0 = 0x5A, not zero
         assert np.array_equal(gpu_sort(k), oracle.radix_sort(k, radix_bits=8)), shift
+
+
+@pytest.mark.parametrize("low_values", [1, 3, 40])
+def test_keys_only_relaxed_warps_every_variant(low_values):
+    """Keys only, 32-bit: a round after the first lets a warp whose keys all
+    share the bits below the digit place equal digits in any order. Keys whose
+    low 8 (then 16) bits take few values make such warps common in rounds 1
+    and 2 at small n, next to warps that straddle a change of the low bits and
+    must keep order, and partial warps in the ragged last tile."""
+    n = 5 * 8192 + 1234
+    hi = inputs.keys(n, 32, "uniform", seed=41) & np.uint32(0xFFFF0000)
+    mid = (inputs.keys(n, 32, "uniform", seed=42) % np.uint32(low_values)) << np.uint32(8)
+    lo = inputs.keys(n, 32, "uniform", seed=43) % np.uint32(low_values)
+    k = hi | mid | lo
+    want = oracle.radix_sort(k, radix_bits=8)
+    for v in range(len(isort.tune_variants(32, 0, 8))):
+        isort.tune_set(32, 0, 8, v)
+        try:
+            assert np.array_equal(gpu_sort(k), want), v
+        finally:
+            isort.tune_set(32, 0, 8, -1)
+    # the segmented form on the same keys: ranges of mixed lengths
+    off = np.array([0, 7, 4000, 4001, 20000, n], dtype=np.int64)
+    t = to_dev(k)
+    isort.sort_segmented(t, to_dev(off))
+    assert isort.stream_status() == _lib.OK
+    assert np.array_equal(to_host(t), oracle.segmented_sort(k, off))
