@@ -116,17 +116,36 @@ def gpu_wide_round(n: float, words_per_item: float, key_words: float, g: float, 
             2 * n * words_per_item * g + shared * n * G)
 
 
+def relaxed_share(n: float, j: int, radix_bits: int = 8, warp_keys: int = 1024) -> float:
+    """Keys only, uniform keys: the share of warps of round j that place keys
+    in any order. Round 0 is order-free; round j >= 1 reads input sorted by the
+    j*radix_bits low bits, which come in runs of n / 2^(j*radix_bits) equal
+    values, and a warp of warp_keys consecutive keys relaxes when no run ends
+    inside it."""
+    if j == 0:
+        return 1.0
+    run = n / 2.0 ** (radix_bits * j)
+    return max(0.0, 1.0 - (warp_keys - 1) / run) if run >= warp_keys else 0.0
+
+
 def gpu_sort(n: float, key_bits: int, val_bits: int, r: int, g: float, G: float,
              block_keys: int | None = None) -> float:
-    """Model time of one whole sort of n keys at radix r (all rounds executed;
-    keys only at radix 256: the first round is the order-free one)."""
+    """Model time of one whole sort of n keys at radix r (all rounds executed).
+    Keys only at radix 256: the first round is order-free, and for 32-bit
+    keys the warps of later rounds that share their low bits (relaxed_share,
+    uniform keys) cost what the order-free round costs."""
     kw = key_bits / 32
     w = kw + val_bits / 32
     P = rounds(key_bits, r)
     if r == 256:
-        first = SHARED_ACCESSES_FIRST if val_bits == 0 else SHARED_ACCESSES_ONESWEEP
-        return (gpu_histogram(n, kw, P, g, G) + gpu_onesweep_round(n, w, g, G, first) +
-                (P - 1) * gpu_onesweep_round(n, w, g, G))
+        t = gpu_histogram(n, kw, P, g, G)
+        for j in range(P):
+            f = 0.0
+            if val_bits == 0 and (j == 0 or key_bits == 32):
+                f = relaxed_share(n, j)
+            shared = f * SHARED_ACCESSES_FIRST + (1 - f) * SHARED_ACCESSES_ONESWEEP
+            t += gpu_onesweep_round(n, w, g, G, shared)
+        return t
     blocks = -(-int(n) // (block_keys or (1 << 19 if r == 65536 else 1 << 16)))
     return P * gpu_wide_round(n, w, kw, g, G, r, blocks)
 

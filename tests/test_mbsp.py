@@ -101,9 +101,31 @@ def test_network_ratio_limits():
 
 def test_gpu_sort_keys_only_first_round_is_cheaper_by_three_shared_accesses():
     """Keys only at radix 256: the order-free first round saves the mark, the
-    mask read and the mask clear (3 shared accesses per key); pairs do not."""
-    n, g, G = 1 << 20, 2.0, 1.0
+    mask read and the mask clear (3 shared accesses per key); pairs do not.
+    At 2^16 keys no warp of a later round shares its low bits (runs of 256
+    keys in round 1), so only round 0 is cheaper."""
+    n, g, G = 1 << 16, 2.0, 1.0
     stable = mbsp.gpu_histogram(n, 1, 4, g, G) + 4 * mbsp.gpu_onesweep_round(n, 1, g, G)
     assert mbsp.gpu_sort(n, 32, 0, 256, g, G) == pytest.approx(stable - 3 * n * G)
     pairs = mbsp.gpu_histogram(n, 1, 4, g, G) + 4 * mbsp.gpu_onesweep_round(n, 2, g, G)
     assert mbsp.gpu_sort(n, 32, 32, 256, g, G) == pytest.approx(pairs)
+
+
+def test_relaxed_share_of_warps():
+    """Round 0 is order-free; at 2^28 uniform keys the low byte comes in runs
+    of 2^20 keys (almost every 1024-key warp inside one), the low 16 bits in
+    runs of 4096 (three warps in four), the low 24 bits in runs of 16 (none)."""
+    n = 1 << 28
+    assert mbsp.relaxed_share(n, 0) == 1.0
+    assert mbsp.relaxed_share(n, 1) == pytest.approx(1 - 1023 / 2**20)
+    assert mbsp.relaxed_share(n, 2) == pytest.approx(1 - 1023 / 4096)
+    assert mbsp.relaxed_share(n, 3) == 0.0
+    # 64-bit keys keep the stable rank after round 0; 32-bit keys relax
+    g, G = 2.0, 1.0
+    t32 = mbsp.gpu_sort(n, 32, 0, 256, g, G)
+    full = mbsp.gpu_histogram(n, 1, 4, g, G) + 4 * mbsp.gpu_onesweep_round(n, 1, g, G)
+    saved = 3 * n * G * (1 + mbsp.relaxed_share(n, 1) + mbsp.relaxed_share(n, 2))
+    assert t32 == pytest.approx(full - saved)
+    t64 = mbsp.gpu_sort(n, 64, 0, 256, g, G)
+    full64 = mbsp.gpu_histogram(n, 2, 8, g, G) + 8 * mbsp.gpu_onesweep_round(n, 2, g, G)
+    assert t64 == pytest.approx(full64 - 3 * n * G)
