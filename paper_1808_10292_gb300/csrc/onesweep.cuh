@@ -16,10 +16,15 @@
 //               counts are the same).
 //   k_scan      exclusive prefix of each pass's digit counts -> global digit
 //               bases; flags passes whose digit is constant (identity).
-//   k_onesweep  one round: load a tile, rank each key among equal digits in
-//               input order (warp match + per-warp counters), publish the tile's
-//               digit counts, look back over earlier tiles, reorder the tile by
-//               digit in shared memory and write it out in runs.
+//   k_onesweep  one round: load a tile, count and publish the tile's digit
+//               counts, rank each key among equal digits in input order
+//               (shared-memory peer masks + per-warp counters) straight into
+//               the reordered tile, look back over earlier tiles, write the
+//               tile out in runs. Keys-only sorts of 32-bit keys relax the rank
+//               in warps whose keys share every bit below the digit.
+//   k_onesweep_first  pass 0 of a keys-only sort: the same round without the
+//               stable rank (one shared atomic gives each key its slot), since
+//               the first round's input order carries no information.
 //   k_copy_back copies the result home when an odd number of rounds ran.
 #pragma once
 #include <cooperative_groups.h>
