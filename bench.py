@@ -219,9 +219,14 @@ def measured_peak_hbm():
 
 
 def onesweep_source_hash() -> str:
+    """Hash of the radix-256 round's code: its sources with // comments and
+    blank lines removed (a comment edit does not change the kernel)."""
     h = hashlib.sha256()
     for f in ("onesweep.cuh", "common.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1808_10292_gb300", "csrc", f), "rb").read())
+        for line in open(os.path.join(ROOT, "paper_1808_10292_gb300", "csrc", f)):
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
