@@ -489,11 +489,16 @@ __device__ __forceinline__ void tile_count(const K (&key)[KPT], const DS& dig, i
 //
 // RELAX (keys only, rounds after the first): the round's input is sorted by
 // the key bits below its digit (`low`), so keys with equal digits need their
-// input order kept only where those low bits differ. When all of the warp's
-// keys share the low bits (its first and last key agree on them), the warp
-// places equal digits in any order: every key takes its slot with its own add
-// on the warp's counter, with no masks. The warps' counters start at their own
-// offsets, so the order between warps is kept either way.
+// input order kept only between runs of equal low bits; inside a run, equal
+// digits mean equal keys so far, in any order. When the warp holds one run
+// (its first and last key agree on the low bits), or a few (at most
+// kRelaxRuns + 1, bounded by the difference of those low bits), every key
+// takes its slot with its own add on the warp's counter, with no masks; with
+// several runs a warp barrier between two keeps the runs in order. The warps'
+// counters start at their own offsets, so the order between warps is kept
+// either way.
+constexpr int kRelaxRuns = 32;  // runs per warp (beyond the first) the relaxed form takes on
+
 template <typename K, int R, int KPT, int MASK_BUFS, bool FULL, bool RELAX = false,
           typename DS>
 __device__ __forceinline__ void tile_rank_place(const K (&key)[KPT], const DS& dig, int tile_n,
@@ -506,11 +511,45 @@ __device__ __forceinline__ void tile_rank_place(const K (&key)[KPT], const DS& d
     const K first = __shfl_sync(kFullMask, key[0], 0);
     const K last = __shfl_sync(kFullMask, key[KPT - 1], 31);
     const bool full = FULL || wofs - lane + KPT * 32 <= tile_n;
-    if (full && ((first ^ last) & low) == 0) {  // warp-uniform
+    // The warp's keys are sorted by their low bits, so they form at most
+    // span + 1 runs of equal low bits.
+    const K span = (last & low) - (first & low);
+    if (full && span == 0) {  // one run: no order to keep at all (warp-uniform)
 #pragma unroll
       for (int i = 0; i < KPT; ++i) {
         const uint32_t d = dig.of(key[i], i);
         const uint32_t pos = atomicAdd(&my[d], 1u);
+        s_keys[pos] = key[i];
+        dig.keep(pos, d);
+        rank2[i >> 1] = (i & 1) ? (rank2[i >> 1] | (pos << 16)) : pos;
+      }
+      return;
+    }
+    if (full && span <= K(kRelaxRuns)) {  // a few runs (warp-uniform)
+      const uint32_t le = lanemask_lt() | (1u << lane);
+      K prev = first;  // at lane 0: the previous row's last key (row 0: itself)
+#pragma unroll
+      for (int i = 0; i < KPT; ++i) {
+        // lanes that start a new run (their low bits differ from the key before)
+        const K rot = __shfl_sync(kFullMask, key[i], (lane + 31) & 31);
+        const K before = lane ? rot : prev;
+        prev = rot;  // at lane 0: this row's last key
+        const uint32_t starts = __ballot_sync(kFullMask, ((key[i] ^ before) & low) != 0);
+        const uint32_t d = dig.of(key[i], i);
+        uint32_t pos = 0;
+        if (starts == 0) {  // one run, the one the previous row ended in
+          pos = atomicAdd(&my[d], 1u);
+        } else {
+          // segments of the row split at run starts take their slots in order,
+          // a warp barrier between two (segment 0 is empty when lane 0 starts a
+          // run: its barrier orders the row after the previous one)
+          const int seg = __popc(starts & le), segs = __popc(starts);
+#pragma unroll 1
+          for (int sg = 0; sg <= segs; ++sg) {
+            if (seg == sg) pos = atomicAdd(&my[d], 1u);
+            if (sg < segs) __syncwarp();
+          }
+        }
         s_keys[pos] = key[i];
         dig.keep(pos, d);
         rank2[i >> 1] = (i & 1) ? (rank2[i >> 1] | (pos << 16)) : pos;
