@@ -338,7 +338,7 @@ GsdLayout gsd_layout(const SegConfig& c, int64_t n, int p) {
   L.bucket_off = o;  o = align256(o + sizeof(int64_t) * (p + 1));
   L.pair_info = o;   o = align256(o + sizeof(int64_t) * 5 * pairs);
   L.pair_tile = o;   o = align256(o + sizeof(int64_t) * (pairs + 1));
-  L.cut = o;         o = align256(o + sizeof(int64_t) * (size_t)(n / 2048 + (int64_t)p * p + 2));
+  L.cut = o;         o = align256(o + sizeof(int64_t) * (size_t)(n / kGsdMinMergeTile + (int64_t)p * p + 2));
   L.total = o;
   return L;
 }

@@ -27,8 +27,19 @@ namespace {
 constexpr int kSampleThreads = 256;
 constexpr int kSampleItems = 16;  // r*p*p <= 4096 sampled keys
 constexpr int kMergeThreads = 256;
-constexpr int kMergeItems = 8;
-constexpr int kMergeTile = kMergeThreads * kMergeItems;  // output keys per merge CTA
+
+// Output keys per merge CTA: ITEMS per thread, odd so that a warp's merge
+// reads and writes (stride ITEMS) spread over all 32 banks, and as many as the
+// staged tile (keys and payloads) allows within 48 KB of static shared memory.
+template <typename K, typename V>
+struct MergeShape {
+  static constexpr int BYTES = (int)sizeof(K) + (HasVal<V>::value ? (int)sizeof(V) : 0);
+  static constexpr int ITEMS = BYTES <= 12 ? 15 : 11;
+  static constexpr int TILE = kMergeThreads * ITEMS;
+  static_assert(ITEMS % 2 == 1, "odd items per thread");
+  static_assert((size_t)TILE * BYTES <= 48 * 1024, "static shared memory");
+  static_assert(TILE >= kGsdMinMergeTile, "the workspace sizes one cut per kGsdMinMergeTile keys");
+};
 
 __device__ __forceinline__ int64_t seq_start(int64_t n, int p, int k) { return n * k / p; }
 
@@ -139,7 +150,7 @@ __global__ void __launch_bounds__(256) k_gsd_plan(const int64_t* __restrict__ bo
 __global__ void __launch_bounds__(256) k_gsd_round(const int64_t* __restrict__ bound,
                                                    const int64_t* __restrict__ pre,
                                                    const int64_t* __restrict__ bucket_off,
-                                                   int64_t n, int p, int t,
+                                                   int64_t n, int p, int t, int64_t tile_keys,
                                                    int64_t* __restrict__ pair_info,
                                                    int64_t* __restrict__ pair_tile) {
   const int per = 1 << t;                 // parts per output run
@@ -165,7 +176,7 @@ __global__ void __launch_bounds__(256) k_gsd_round(const int64_t* __restrict__ b
     info[2] = sb;
     info[3] = lb;
     info[4] = bucket_off[j] + P[ka];
-    s_tiles[id] = (la + lb + kMergeTile - 1) / kMergeTile;
+    s_tiles[id] = (la + lb + tile_keys - 1) / tile_keys;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -215,13 +226,14 @@ template <typename K>
 __global__ void __launch_bounds__(256) k_gsd_cuts(const K* __restrict__ kin,
                                                   const int64_t* __restrict__ pair_info,
                                                   const int64_t* __restrict__ pair_tile,
-                                                  int pairs, int64_t* __restrict__ cut) {
+                                                  int pairs, int64_t tile_keys,
+                                                  int64_t* __restrict__ cut) {
   const int64_t tile = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (tile >= pair_tile[pairs]) return;
   const int q = pair_of(pair_tile, pairs, tile);
   const int64_t* info = pair_info + (size_t)q * 5;
   const int64_t sa = info[0], la = info[1], sb = info[2], lb = info[3];
-  const int64_t d0 = (tile - pair_tile[q]) * kMergeTile;
+  const int64_t d0 = (tile - pair_tile[q]) * tile_keys;
   cut[tile] = merge_split<K>([&](int64_t i) { return kin[sa + i]; },
                              [&](int64_t i) { return kin[sb + i]; }, la, lb, d0);
 }
@@ -233,6 +245,7 @@ __global__ void __launch_bounds__(kMergeThreads)
                 const int64_t* __restrict__ pair_tile, const int64_t* __restrict__ cut,
                 int pairs, int64_t n, uint32_t* err) {
   constexpr bool HV = HasVal<V>::value;
+  constexpr int kMergeItems = MergeShape<K, V>::ITEMS, kMergeTile = MergeShape<K, V>::TILE;
   using VS = typename std::conditional<HV, V, uint32_t>::type;
   __shared__ K s_k[kMergeTile];                // staged A then B, later the merged tile
   __shared__ VS s_v[HV ? kMergeTile : 1];
@@ -306,19 +319,20 @@ cudaError_t gsd_launch(const GsdArgs& a, cudaStream_t st) {
   k_gsd_plan<<<1, 256, 0, st>>>(a.bound, p, a.pre, a.bucket_off, a.counts_out);
   timer_end(a.timer, st);
   // lg p merge rounds, ping-pong between the caller's arrays and the workspace
-  const int64_t max_tiles = a.n / kMergeTile + (int64_t)p * p + 1;
+  constexpr int64_t kTile = MergeShape<K, V>::TILE;
+  const int64_t max_tiles = a.n / kTile + (int64_t)p * p + 1;
   K* kbuf[2] = {keys, static_cast<K*>(a.alt_keys)};
   V* vbuf[2] = {vals, static_cast<V*>(a.alt_vals)};
   int src = 0;
   for (int t = 1; (1 << t) <= p; ++t) {
     const int pairs = p * (p >> t);
     timer_begin(a.timer, "k_gsd_round", st);
-    k_gsd_round<<<1, 256, 0, st>>>(a.bound, a.pre, a.bucket_off, a.n, p, t, a.pair_info,
+    k_gsd_round<<<1, 256, 0, st>>>(a.bound, a.pre, a.bucket_off, a.n, p, t, kTile, a.pair_info,
                                    a.pair_tile);
     timer_end(a.timer, st);
     timer_begin(a.timer, "k_gsd_cuts", st);
     k_gsd_cuts<K><<<(unsigned)((max_tiles + 255) / 256), 256, 0, st>>>(
-        kbuf[src], a.pair_info, a.pair_tile, pairs, a.cut);
+        kbuf[src], a.pair_info, a.pair_tile, pairs, kTile, a.cut);
     timer_end(a.timer, st);
     timer_begin(a.timer, "k_gsd_merge", st);
     k_gsd_merge<K, V><<<(unsigned)max_tiles, kMergeThreads, 0, st>>>(

@@ -135,6 +135,10 @@ struct GvrArgs {
   int num_sms;
   KernelTimer* timer;
 };
+
+// GSD merge tiles hold at least this many output keys (sizes the cut array).
+constexpr int64_t kGsdMinMergeTile = 2048;
+
 // The sample, split and merge steps of GSD (gsd.cu), after the local sort of
 // the p sequences [n*k/p, n*(k+1)/p) in keys/vals.
 struct GsdArgs {
@@ -151,7 +155,7 @@ struct GsdArgs {
   int64_t* bucket_off;   // [p + 1]
   int64_t* pair_info;    // [p * p / 2][5] merge pairs of one round
   int64_t* pair_tile;    // [p * p / 2 + 1] first output tile of each pair
-  int64_t* cut;          // [n / 2048 + p * p + 1] merge-path split of each output tile
+  int64_t* cut;          // [n / kGsdMinMergeTile + p * p + 1] merge-path split of each output tile
   uint32_t* counts_out;  // [p] caller's copy of the bucket sizes, or nullptr
   uint32_t* err;
   KernelTimer* timer;

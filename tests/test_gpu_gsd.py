@@ -30,7 +30,7 @@ def gpu_gsd(k, v=None, p=16, r=4):
                                                (64, 64)])
 @pytest.mark.parametrize("dist", inputs.DISTS)
 def test_gsd_matches_oracle(key_bits, val_bits, dist):
-    n = 555_557  # 16 sequences of ~34,722 keys; merge tiles of 2048 with ragged ends
+    n = 555_557  # 16 sequences of ~34,722 keys; merge tiles with ragged ends
     k = inputs.keys(n, key_bits, dist, seed=61)
     v = inputs.iota(n, val_bits) if val_bits else None
     st, gk, gv, gc = gpu_gsd(k, v, p=16, r=4)
@@ -46,7 +46,7 @@ def test_gsd_matches_oracle(key_bits, val_bits, dist):
 
 @pytest.mark.parametrize("p,r", [(1, 1), (2, 1), (2, 5), (4, 16), (8, 64), (32, 2), (64, 1)])
 def test_gsd_bucket_and_oversampling_edges(p, r):
-    for n in (0, 1, 2, 3, 63, 64, 65, 2047, 2048, 2049, 100_003):
+    for n in (0, 1, 2, 3, 63, 64, 65, 2047, 2048, 2049, 2303, 2304, 2305, 3839, 3840, 3841, 4609, 7681, 100_003):
         k = inputs.keys(n, 32, "and4", seed=n + 17)
         v = inputs.iota(n)
         st, gk, gv, gc = gpu_gsd(k, v, p=p, r=r)
