@@ -18,7 +18,9 @@
 //   k_seg_scan      per range and pass, exclusive digit bases.
 //   k_seg_onesweep  one count-sort round over the tiles of ALL radix ranges; the
 //                   look-back never crosses a range (the first tile of a range
-//                   publishes its counts as inclusive).
+//                   publishes its counts as inclusive). Keys only: pass 0 is the
+//                   order-free round (onesweep_tile_first) and later passes relax
+//                   the rank in warps with few runs of equal low bits.
 // All passes run (4 for 32-bit keys, 8 for 64-bit): an even number, so the
 // result ends in the caller's arrays. Offsets are checked on the device; a bad
 // range is skipped and flagged in the error word.
