@@ -28,11 +28,13 @@
  *  - Keys are unsigned 32- or 64-bit (key_bits 32|64); payloads 32- or 64-bit
  *    (val_bits 32|64). n <= 2^30 (the look-back status word packs a 30-bit
  *    count); larger n returns ISORT_EUNSUPPORTED.
- *  - radix_bits: 0 = automatic (8), 8 = radix 256 (SR4/PR4), 16 = radix 65536
- *    (PR2), 11 = radix 2048 (between the two; not one of the paper's
- *    configurations). Passes = ceil(key_bits / radix_bits); when radix_bits does
- *    not divide key_bits the last digit is narrower (11, 11, 10 bits for 32-bit
- *    keys at radix_bits 11). A pass whose digit is the same for every key is
+ *  - radix_bits: 0 = automatic (the width and kernel variant that the autotuner
+ *    chose for these key/payload widths and the size bucket floor(log2 n), see
+ *    isort_tune_auto; radix 256 when nothing was tuned), 8 = radix 256
+ *    (SR4/PR4), 16 = radix 65536 (PR2), 11 = radix 2048 (between the two; not
+ *    one of the paper's configurations). Passes = ceil(key_bits / radix_bits);
+ *    when radix_bits does not divide key_bits the last digit is narrower (11,
+ *    11, 10 bits for 32-bit keys at radix_bits 11). A pass whose digit is the same for every key is
  *    skipped (it is the identity permutation).
  */
 #ifndef ISORT_H
@@ -69,9 +71,14 @@ isort_status isort_pairs(void *keys, void *vals, int64_t n, int key_bits, int va
  * the input into p ranges and sort each independently (Algorithms 1-3); here
  * the ranges are given. Short segments use the paper's BTN merge-split bitonic
  * network ("Algorithm BTN", Eq. Tb), long ones the radix-256 passes, all
- * segments of a class in the same launch. Offsets are read on the device only:
- * a segment that breaks these rules is skipped (left as it is) and
- * isort_stream_status reports ISORT_EINVAL. radix_bits: 0 or 8. */
+ * segments of a class in the same launch.
+ *  - total_keys: the key count (= offsets[num_segments]) given on the host, so
+ *    that the call can size its workspace without reading the device-resident
+ *    offsets (which keeps the call asynchronous and graph-capturable).
+ *  - radix_bits: 0 or 8 (the segmented rounds are radix-256 rounds only; 11
+ *    and 16 return ISORT_EUNSUPPORTED).
+ * Offsets are read on the device only: a segment that breaks these rules is
+ * skipped (left as it is) and isort_stream_status reports ISORT_EINVAL. */
 isort_status isort_segmented(void *keys, void *vals, const int64_t *offsets, int64_t num_segments,
                              int64_t total_keys, int key_bits, int val_bits, int radix_bits,
                              void *stream);
@@ -83,11 +90,17 @@ isort_status isort_segmented(void *keys, void *vals, const int64_t *offsets, int
  * not allocate device memory while running -- a framework that owns all device
  * memory through its own pool, a latency-critical loop where cudaMalloc could
  * synchronise the device, code that must not hit out-of-memory after start-up.
- *  - keys: DEVICE array of n uint32 keys, sorted ascending in place.
+ *  - keys: DEVICE array of n uint32 keys on the current device, sorted
+ *    ascending in place. It always runs the built-in default radix-256 kernel
+ *    variant (the autotuner's choice does not apply), so its speed can differ
+ *    from isort_keys at the same n; the result is the same.
  *  - n > ISORT_NOALLOC_MAX_KEYS returns ISORT_ENOMEM (the array is too small);
  *    n = 0 or 1 is a no-op.
- *  - err_out: optional DEVICE word; device-side error bits are OR-ed into it
- *    (the caller zeroes it); NULL = not reported.
+ *  - err_out: required DEVICE word on the current device (NULL returns
+ *    ISORT_EINVAL): device-side error bits (a bounded wait that gave up, a
+ *    failed output bounds check) are OR-ed into it. The caller zeroes it and
+ *    reads it after the stream has finished; nonzero means the keys are not
+ *    sorted.
  *  - The first call on a device looks up the array's device address (with that
  *    device current); make that first call before any stream capture.
  *  - Every call shares the one array, which keeps the previous call's contents
@@ -192,6 +205,25 @@ int isort_tune_num_variants(int key_bits, int val_bits, int radix_bits);
 isort_status isort_tune_describe(int key_bits, int val_bits, int radix_bits, int variant,
                                  int *threads, int *keys_per_thread);
 
+/* Automatic choice, per size bucket: sorts of these widths with radix_bits = 0
+ * and floor(log2 n) nearest to size_log2 (the lower bucket on a tie) use radix
+ * width radix_bits (8, 11 or 16) and kernel variant `variant` of that width's
+ * table. radix_bits < 0 clears the entry of size_log2, or every entry of these
+ * widths when size_log2 < 0. Entries set here take precedence over the
+ * built-in ones (the autotuner's choices measured on a GB300); an explicit
+ * radix_bits uses the variant fixed by isort_tune_set, else the automatic
+ * choice's variant when that chose the same width, else variant 0.
+ * ISORT_EINVAL for an unknown width, bucket (0..30) or variant. The Python
+ * tuner (paper_1808_10292_gb300/tune.py) measures the choices and loads its
+ * cache through this call. */
+isort_status isort_tune_auto(int key_bits, int val_bits, int size_log2, int radix_bits,
+                             int variant);
+
+/* The radix width and variant a sort of n keys with these arguments would use
+ * (radix_bits 0 = automatic). No device work. */
+isort_status isort_tune_resolve(int64_t n, int key_bits, int val_bits, int radix_bits,
+                                int *radix_out, int *variant_out);
+
 /* Test hooks. isort_debug_set(ISORT_DEBUG_SPIN_LIMIT, k): bounded waits give up
  * after k polls (0 restores the default). isort_debug_set(ISORT_DEBUG_STALL_TILE,
  * t): in pass 0 of the next radix-256 sort, tile t never publishes its counts
@@ -225,6 +257,11 @@ int isort_debug_kernel_times(const char **names, float *ms, int max);
  * was loaded (all streams and entry points; CUDA-graph replays of a captured
  * call are not counted again). */
 int64_t isort_debug_launch_count(void);
+
+/* Measurement hook: bytes of device memory the library currently holds as
+ * workspaces it allocated itself (caller-bound workspaces and the fixed array
+ * of isort_keys_noalloc are not counted). */
+int64_t isort_debug_workspace_bytes(void);
 
 #ifdef __cplusplus
 }

@@ -35,6 +35,23 @@ def _stream(stream) -> int:
     return int(s.cuda_stream) if hasattr(s, "cuda_stream") else int(s)
 
 
+_tuned_devices = set()
+
+
+def _tuned():
+    """Load the autotuner's cache for the current GPU into the library, once per
+    device (a no-op without a GPU or a cache entry for it)."""
+    torch = _torch()
+    if not torch.cuda.is_available():
+        return
+    dev = torch.cuda.current_device()
+    if dev in _tuned_devices:
+        return
+    _tuned_devices.add(dev)
+    from . import tune
+    tune.apply_all(torch.cuda.get_device_name(dev))
+
+
 def _dev(t, name):
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
@@ -43,23 +60,41 @@ def _dev(t, name):
 
 
 def sort_keys(keys, radix_bits: int = 0, stream=None):
-    """Sort a CUDA uint32/uint64 tensor ascending in place; returns it."""
+    """Sort a CUDA uint32/uint64 tensor ascending in place; returns it.
+
+    radix_bits 0 lets the library choose the radix width and kernel variant
+    (the autotuner's cache for this GPU is loaded into it on first use)."""
     _dev(keys, "keys")
+    _tuned()
     check(load().isort_keys(keys.data_ptr(), keys.numel(), _bits(keys), radix_bits,
                             _stream(stream)), "isort_keys")
     return keys
 
 
-def sort_keys_noalloc(keys, err_word=None, stream=None):
+def sort_keys_noalloc(keys, err_word, stream=None):
     """Sort a CUDA uint32 tensor in place with the library's fixed scratch array
     (isort_keys_noalloc): no device memory is allocated. At most
-    NOALLOC_MAX_KEYS keys; calls must not overlap on the GPU."""
+    NOALLOC_MAX_KEYS keys; calls must not overlap on the GPU.
+
+    err_word: a CUDA 32-bit tensor (at least one element) on the keys' device,
+    zeroed by the caller; device errors are OR-ed into its first element.
+    The keys must be on the current CUDA device."""
+    torch = _torch()
     _dev(keys, "keys")
     if _bits(keys) != 32:
         raise TypeError("isort_keys_noalloc sorts 32-bit keys")
-    eptr = None if err_word is None else err_word.data_ptr()
-    check(load().isort_keys_noalloc(keys.data_ptr(), keys.numel(), eptr, _stream(stream)),
-          "isort_keys_noalloc")
+    if err_word is None:
+        raise ValueError("err_word is required: the device error bits are reported there")
+    _dev(err_word, "err_word")
+    if err_word.dtype not in (torch.int32, torch.uint32) or err_word.numel() < 1:
+        raise ValueError("err_word must be a 32-bit tensor with at least one element")
+    if err_word.device != keys.device:
+        raise ValueError("err_word must be on the keys' device")
+    if keys.device.index != torch.cuda.current_device():
+        raise ValueError("keys must be on the current CUDA device (the fixed scratch array is "
+                         "looked up per device)")
+    check(load().isort_keys_noalloc(keys.data_ptr(), keys.numel(), err_word.data_ptr(),
+                                    _stream(stream)), "isort_keys_noalloc")
     return keys
 
 
@@ -69,6 +104,7 @@ def sort_pairs(keys, vals, radix_bits: int = 0, stream=None):
     _dev(vals, "vals")
     if keys.numel() != vals.numel():
         raise ValueError("keys and vals differ in length")
+    _tuned()
     check(load().isort_pairs(keys.data_ptr(), vals.data_ptr(), keys.numel(), _bits(keys),
                              _bits(vals), radix_bits, _stream(stream)), "isort_pairs")
     return keys, vals
@@ -166,6 +202,7 @@ def sample_sort_workspace_size(n: int, key_bits: int = 32, val_bits: int = 0, bu
 
 
 def workspace_size(n: int, key_bits: int = 32, val_bits: int = 0, radix_bits: int = 0) -> int:
+    _tuned()
     out = ctypes.c_size_t(0)
     check(load().isort_workspace_size(n, key_bits, val_bits, radix_bits, ctypes.byref(out)),
           "isort_workspace_size")
@@ -206,6 +243,26 @@ def tune_variants(key_bits: int = 32, val_bits: int = 0, radix_bits: int = 8):
 def tune_segmented(key_bits: int = 32, val_bits: int = 0, btn_max_keys: int = -1):
     """Ranges of at most btn_max_keys keys take the BTN network (-1: default)."""
     check(load().isort_tune_segmented(key_bits, val_bits, btn_max_keys), "isort_tune_segmented")
+
+
+def resolve(n: int, key_bits: int = 32, val_bits: int = 0, radix_bits: int = 0):
+    """(radix_bits, variant) that a sort of n keys with these arguments uses."""
+    rb, v = ctypes.c_int(0), ctypes.c_int(0)
+    check(load().isort_tune_resolve(n, key_bits, val_bits, radix_bits, ctypes.byref(rb),
+                                    ctypes.byref(v)), "isort_tune_resolve")
+    return rb.value, v.value
+
+
+def tune_auto(key_bits: int, val_bits: int, size_log2: int, radix_bits: int, variant: int = 0):
+    """Record the automatic choice (radix width, variant) for a size bucket;
+    radix_bits < 0 clears (every bucket of the widths when size_log2 < 0)."""
+    check(load().isort_tune_auto(key_bits, val_bits, size_log2, radix_bits, variant),
+          "isort_tune_auto")
+
+
+def workspace_bytes() -> int:
+    """Device bytes the library holds in workspaces it allocated itself."""
+    return int(load().isort_debug_workspace_bytes())
 
 
 def launch_count() -> int:

@@ -52,6 +52,8 @@ def _sig(lib):
         "isort_sample_sort_workspace_size": [i64, i32, i32, i32, i32, ctypes.POINTER(sz)],
         "isort_gsd_sort": [vp, vp, i64, i32, i32, i32, i32, vp, vp],
         "isort_gsd_sort_workspace_size": [i64, i32, i32, i32, i32, ctypes.POINTER(sz)],
+        "isort_tune_auto": [i32, i32, i32, i32, i32],
+        "isort_tune_resolve": [i64, i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -62,6 +64,8 @@ def _sig(lib):
     lib.isort_debug_kernel_times.restype = i32
     lib.isort_debug_launch_count.argtypes = []
     lib.isort_debug_launch_count.restype = ctypes.c_int64
+    lib.isort_debug_workspace_bytes.argtypes = []
+    lib.isort_debug_workspace_bytes.restype = ctypes.c_int64
     lib.isort_strerror.argtypes = [ctypes.c_int]
     lib.isort_strerror.restype = ctypes.c_char_p
     return lib

@@ -60,12 +60,88 @@ int variants(int key_bits, int val_bits, int radix_bits, const LsdEntry** out) {
   return 0;
 }
 
-const LsdEntry* pick(int key_bits, int val_bits, int radix_bits) {
-  const LsdEntry* tab = nullptr;
-  int nv = variants(key_bits, val_bits, radix_bits, &tab);
-  if (nv <= 0) return nullptr;
+// Automatic choice of radix width and kernel variant per (key_bits, val_bits)
+// and size bucket (floor(log2 n)): radix_bits = 0 resolves through it.
+struct AutoChoice {
+  int radix_bits, variant;
+};
+// Runtime entries (isort_tune_auto; the Python tuner loads its cache here).
+std::map<std::pair<int, int>, std::map<int, AutoChoice>> g_auto;
+
+// Built-in entries: what the autotuner (tune.py) picked on a GB300 for these
+// sizes; used when no runtime entry exists for the widths.
+struct BuiltinChoice {
+  int key_bits, val_bits, bucket, radix_bits, variant;
+};
+const BuiltinChoice kBuiltinAuto[] = {
+    {32, 0, 20, 8, 0}, {32, 0, 24, 8, 0}, {32, 0, 28, 8, 0},
+    {32, 32, 26, 8, 0}, {32, 64, 26, 8, 0},
+    {64, 0, 25, 8, 0}, {64, 32, 25, 8, 0}, {64, 64, 25, 8, 0},
+};
+
+int size_bucket(int64_t n) {
+  int b = 0;
+  while (b < 62 && (int64_t(2) << b) <= n) ++b;
+  return b;
+}
+
+// Nearest bucket of `m` to `bucket` (the lower one on a tie) among entries of
+// radix width `radix_bits` (0: any width); null if there is none.
+const AutoChoice* nearest(const std::map<int, AutoChoice>& m, int bucket, int radix_bits) {
+  const AutoChoice* best = nullptr;
+  int dist = 1 << 30;
+  for (const auto& kv : m) {
+    if (radix_bits && kv.second.radix_bits != radix_bits) continue;
+    const int d = kv.first > bucket ? kv.first - bucket : bucket - kv.first;
+    if (d < dist) {
+      dist = d;
+      best = &kv.second;
+    }
+  }
+  return best;
+}
+
+// The automatic choice for n keys of these widths, among entries of width
+// radix_bits (0: any): a runtime entry, else a built-in one; null if neither.
+const AutoChoice* auto_choice(int key_bits, int val_bits, int64_t n, int radix_bits) {
+  static std::map<std::pair<int, int>, std::map<int, AutoChoice>> builtin;
+  if (builtin.empty())
+    for (const BuiltinChoice& b : kBuiltinAuto)
+      builtin[{b.key_bits, b.val_bits}][b.bucket] = AutoChoice{b.radix_bits, b.variant};
+  const int bucket = size_bucket(n);
+  for (auto* table : {&g_auto, &builtin}) {
+    auto it = table->find({key_bits, val_bits});
+    if (it == table->end()) continue;
+    if (const AutoChoice* c = nearest(it->second, bucket, radix_bits)) return c;
+  }
+  return nullptr;
+}
+
+// Radix width and variant of a sort of n keys (caller holds g_mu). radix_bits
+// 0: the automatic choice (radix 256, variant 0 when nothing is known).
+// Otherwise that width, with the variant fixed by isort_tune_set if any, else
+// the variant of the nearest automatic entry of that width, else variant 0.
+AutoChoice resolve(int key_bits, int val_bits, int radix_bits, int64_t n) {
+  if (radix_bits == 0) {
+    const AutoChoice* a = auto_choice(key_bits, val_bits, n, 0);
+    radix_bits = a ? a->radix_bits : 8;
+  }
+  AutoChoice c{radix_bits, 0};
   auto it = g_variant.find({key_bits, val_bits, radix_bits});
-  int v = (it == g_variant.end()) ? 0 : it->second;
+  if (it != g_variant.end()) {
+    c.variant = it->second;
+  } else if (const AutoChoice* a = auto_choice(key_bits, val_bits, n, radix_bits)) {
+    c.variant = a->variant;
+  }
+  return c;
+}
+
+const LsdEntry* pick(int key_bits, int val_bits, int radix_bits, int64_t n) {
+  const AutoChoice c = resolve(key_bits, val_bits, radix_bits, n);
+  const LsdEntry* tab = nullptr;
+  int nv = variants(key_bits, val_bits, c.radix_bits, &tab);
+  if (nv <= 0) return nullptr;
+  int v = c.variant;
   if (v < 0 || v >= nv) v = 0;
   return &tab[v];
 }
@@ -176,8 +252,7 @@ isort_status check_widths(int key_bits, int val_bits, bool pairs) {
 }
 
 isort_status resolve_radix(int radix_bits, int* out) {
-  if (radix_bits == 0) radix_bits = 8;
-  if (radix_bits != 8 && radix_bits != 11 && radix_bits != 16) {
+  if (radix_bits != 0 && radix_bits != 8 && radix_bits != 11 && radix_bits != 16) {
     if (radix_bits > 0 && radix_bits <= 24) return ISORT_EUNSUPPORTED;
     return ISORT_EINVAL;
   }
@@ -187,10 +262,10 @@ isort_status resolve_radix(int radix_bits, int* out) {
 
 isort_status run_lsd(void* keys, void* vals, int64_t n, int key_bits, int val_bits,
                      int radix_bits, cudaStream_t st) {
-  const LsdEntry* e = pick(key_bits, val_bits, radix_bits);
+  std::lock_guard<std::mutex> lock(g_mu);
+  const LsdEntry* e = pick(key_bits, val_bits, radix_bits, n);
   if (!e) return ISORT_EUNSUPPORTED;
   Layout L = layout_for(*e, n);
-  std::lock_guard<std::mutex> lock(g_mu);
   void* ws = nullptr;
   isort_status s = acquire(st, L.total, &ws);
   if (s != ISORT_OK) return s;
@@ -589,7 +664,7 @@ isort_status isort_workspace_size(int64_t n, int key_bits, int val_bits, int rad
   if (n < 0) return ISORT_EINVAL;
   if (n > kMaxN) return ISORT_EUNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_mu);
-  const LsdEntry* e = pick(key_bits, val_bits, rb);
+  const LsdEntry* e = pick(key_bits, val_bits, rb, n);
   if (!e) return ISORT_EUNSUPPORTED;
   *bytes = layout_for(*e, n).total;
   return ISORT_OK;
@@ -687,6 +762,54 @@ isort_status isort_tune_describe(int key_bits, int val_bits, int radix_bits, int
   *threads = tab[variant].threads;
   *keys_per_thread = tab[variant].keys_per_thread;
   return ISORT_OK;
+}
+
+isort_status isort_tune_auto(int key_bits, int val_bits, int size_log2, int radix_bits,
+                            int variant) {
+  if (key_bits != 32 && key_bits != 64) return ISORT_EINVAL;
+  if (val_bits != 0 && val_bits != 32 && val_bits != 64) return ISORT_EINVAL;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (radix_bits < 0) {  // clear one bucket, or every bucket of these widths
+    auto it = g_auto.find({key_bits, val_bits});
+    if (it == g_auto.end()) return ISORT_OK;
+    if (size_log2 < 0)
+      g_auto.erase(it);
+    else
+      it->second.erase(size_log2);
+    return ISORT_OK;
+  }
+  if (size_log2 < 0 || size_log2 > 30) return ISORT_EINVAL;
+  if (radix_bits != 8 && radix_bits != 11 && radix_bits != 16) return ISORT_EINVAL;
+  const LsdEntry* tab = nullptr;
+  const int nv = variants(key_bits, val_bits, radix_bits, &tab);
+  if (variant < 0 || variant >= nv) return ISORT_EINVAL;
+  g_auto[{key_bits, val_bits}][size_log2] = AutoChoice{radix_bits, variant};
+  return ISORT_OK;
+}
+
+isort_status isort_tune_resolve(int64_t n, int key_bits, int val_bits, int radix_bits,
+                               int* radix_out, int* variant_out) {
+  if (!radix_out || !variant_out || n < 0) return ISORT_EINVAL;
+  isort_status s = check_widths(key_bits, val_bits, val_bits != 0);
+  if (s != ISORT_OK) return s;
+  int rb = 0;
+  if ((s = resolve_radix(radix_bits, &rb)) != ISORT_OK) return s;
+  std::lock_guard<std::mutex> lock(g_mu);
+  const AutoChoice c = resolve(key_bits, val_bits, rb, n);
+  const LsdEntry* tab = nullptr;
+  const int nv = variants(key_bits, val_bits, c.radix_bits, &tab);
+  if (nv <= 0) return ISORT_EUNSUPPORTED;
+  *radix_out = c.radix_bits;
+  *variant_out = (c.variant >= 0 && c.variant < nv) ? c.variant : 0;
+  return ISORT_OK;
+}
+
+int64_t isort_debug_workspace_bytes(void) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  int64_t total = 0;
+  for (const auto& kv : g_ws)
+    if (kv.second.owned && kv.second.base) total += (int64_t)kv.second.bytes;
+  return total;
 }
 
 isort_status isort_debug_set(int what, int64_t value) {

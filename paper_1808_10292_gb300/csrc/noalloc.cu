@@ -12,7 +12,9 @@
 //
 // This file adds an entry point and changes no other code path: it carves the
 // static array the same way the workspace is carved and calls the same
-// launcher as isort_keys (the default kernel variant).
+// launcher as isort_keys, always with the built-in default kernel variant
+// (variant 0 of the radix-256 table; the autotuner's choice does not apply).
+// Device errors are OR-ed into the caller's word, which is required.
 #include <cstdint>
 #include <mutex>
 
@@ -24,9 +26,9 @@ using namespace isort;
 namespace {
 
 // Scratch for n <= ISORT_NOALLOC_MAX_KEYS 32-bit keys: the alternate key
-// buffer (4 MiB), two look-back arrays (256 tiles x 256 digits x 4 B each),
-// histograms, digit bases, flags, tile counters and an error word, with
-// 256-byte alignment padding. 5 MiB covers it with room to spare.
+// buffer (4 MiB), two look-back arrays (one row of 256 digits x 4 B per tile
+// each), histograms, digit bases, flags and tile counters, with 256-byte
+// alignment padding. 5 MiB covers it with room to spare.
 constexpr size_t kScratchBytes = size_t(5) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -47,6 +49,8 @@ extern "C" isort_status isort_keys_noalloc(void* keys, int64_t n, uint32_t* err_
   if (n > ISORT_NOALLOC_MAX_KEYS) return ISORT_ENOMEM;  // beyond the fixed scratch
   if (n <= 1) return ISORT_OK;
   if (!keys || (reinterpret_cast<uintptr_t>(keys) & 3)) return ISORT_EINVAL;
+  // Device errors land in the caller's word: nothing else would ever read them.
+  if (!err_out || (reinterpret_cast<uintptr_t>(err_out) & 3)) return ISORT_EINVAL;
 
   const LsdEntry* tab = nullptr;
   if (lsd_variants_k32(0, 8, &tab) <= 0) return ISORT_EUNSUPPORTED;
@@ -76,11 +80,10 @@ extern "C" isort_status isort_keys_noalloc(void* keys, int64_t n, uint32_t* err_
     sms = g_sms[dev];
   }
 
-  // Carve the array: error word, histograms, bases, flags, counters, the two
-  // look-back arrays, the alternate key buffer.
+  // Carve the array: histograms, bases, flags, counters, the two look-back
+  // arrays, the alternate key buffer.
   const int64_t tiles = (n + e.tile - 1) / e.tile;
   size_t off = 0;
-  const size_t err = off;      off = align256(off + 4);
   const size_t hist = off;     off = align256(off + sizeof(uint32_t) * e.passes * e.radix);
   const size_t bases = off;    off = align256(off + sizeof(uint32_t) * e.passes * e.radix);
   const size_t skip = off;     off = align256(off + sizeof(uint32_t) * e.passes);
@@ -92,11 +95,9 @@ extern "C" isort_status isort_keys_noalloc(void* keys, int64_t n, uint32_t* err_
 
   char* b = static_cast<char*>(base);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  uint32_t* errp = err_out ? err_out : reinterpret_cast<uint32_t*>(b + err);
   // The array keeps the previous call's contents. The launcher clears the
-  // histograms, the tile counters and the first look-back array; the internal
-  // error word is cleared here (a caller-supplied one is the caller's to clear).
-  if (!err_out && cudaMemsetAsync(errp, 0, 4, st) != cudaSuccess) return ISORT_ECUDA;
+  // histograms, the tile counters and the first look-back array; every other
+  // piece is written before it is read.
 
   LsdArgs a;
   a.keys = keys;
@@ -110,7 +111,7 @@ extern "C" isort_status isort_keys_noalloc(void* keys, int64_t n, uint32_t* err_
   a.counters = reinterpret_cast<uint32_t*>(b + counters);
   a.status[0] = reinterpret_cast<uint32_t*>(b + status0);
   a.status[1] = reinterpret_cast<uint32_t*>(b + status1);
-  a.err = errp;
+  a.err = err_out;
   a.spin_limit = kSpinLimit;
   a.stall_tile = -1;
   a.num_sms = sms;

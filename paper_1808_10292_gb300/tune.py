@@ -2,8 +2,10 @@
 fastest, with a JSON cache keyed by GPU name, key/payload widths and size bucket.
 
 What it tunes:
-  * plain sorts: the radix-256 pass variant (threads x keys per thread) and the
-    radix width (8, 11 or 16 bits) for (key_bits, val_bits, n-bucket);
+  * plain sorts: the radix-256 pass variant (threads x keys per thread, i.e.
+    tile size and keys per thread) and the radix width (8, 11 or 16 bits) for
+    (key_bits, val_bits, n-bucket); apply_all loads the winners into the
+    library, where radix_bits = 0 resolves through them (isort_tune_auto);
   * segmented sorts: the longest range that still takes the BTN network
     (btn_max) for (key_bits, val_bits).
 Measurement: CUDA events on the current stream around the library call, inputs
@@ -17,8 +19,8 @@ import os
 import statistics
 
 from . import _lib
-from . import (load, sort_keys, sort_pairs, sort_segmented, stream_status, tune_segmented,
-               tune_set, tune_variants)
+from . import (load, resolve, sort_keys, sort_pairs, sort_segmented, stream_status,
+               tune_auto, tune_segmented, tune_set, tune_variants)
 
 CACHE = os.environ.get("ISORT_TUNE_CACHE",
                        os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json"))
@@ -147,36 +149,59 @@ def autotune(plain_sizes=((1 << 24, 32, 0),), segmented=((4000, 20, 32, 0),),
     return cache
 
 
-def apply(key_bits: int, val_bits: int, n: int | None = None, path: str = CACHE) -> dict:
-    """Set the library's tuning for (key_bits, val_bits) from the cache; returns
-    the settings applied ({} when the cache has nothing for this GPU)."""
+def parse_plain_key(key: str):
+    """(key_bits, val_bits, size bucket) of a cache key "plain/k32/v0/b24", or None."""
+    parts = key.split("/")
+    if len(parts) != 4 or parts[0] != "plain":
+        return None
+    try:
+        kb, vb, b = int(parts[1][1:]), int(parts[2][1:]), int(parts[3][1:])
+    except ValueError:
+        return None
+    if parts[1][0] != "k" or parts[2][0] != "v" or parts[3][0] != "b":
+        return None
+    return kb, vb, b
+
+
+def apply_all(gpu_name: str | None = None, path: str = CACHE) -> dict:
+    """Load every choice the cache holds for this GPU into the library: per
+    (key_bits, val_bits, size bucket) the fastest radix width and variant (what
+    radix_bits = 0 then uses), and per widths the segmented BTN threshold.
+    Returns {cache key: choice applied}; {} when the cache has nothing for it."""
     load()
-    gpu = load_cache(path).get(_gpu_name(), {})
+    gpu = load_cache(path).get(gpu_name or _gpu_name(), {})
     applied = {}
-    if n is not None:
-        # nearest size bucket recorded for these widths
-        cands = [(abs(int(k.rsplit("/b", 1)[1]) - _bucket(n)), k) for k in gpu
-                 if k.startswith(f"plain/k{key_bits}/v{val_bits}/")]
-        if cands:
-            best = gpu[min(cands)[1]]["best"]
-            if best["radix_bits"] == 8:
-                tune_set(key_bits, val_bits, 8, best["variant"])
-            applied["plain"] = best
-    seg = gpu.get(seg_key(key_bits, val_bits))
-    if seg:
-        tune_segmented(key_bits, val_bits, seg["best"]["btn_max"])
-        applied["segmented"] = seg["best"]
+    for key, entry in sorted(gpu.items()):
+        parsed = parse_plain_key(key)
+        if parsed:
+            kb, vb, b = parsed
+            best = entry["best"]
+            tune_auto(kb, vb, b, best["radix_bits"], best.get("variant", 0))
+            applied[key] = {"radix_bits": best["radix_bits"], "variant": best.get("variant", 0)}
+        elif key.startswith("segmented/"):
+            kb, vb = (int(x[1:]) for x in key.split("/")[1:3])
+            tune_segmented(kb, vb, entry["best"]["btn_max"])
+            applied[key] = {"btn_max": entry["best"]["btn_max"]}
     return applied
 
 
-def best_radix(key_bits: int, val_bits: int, n: int, path: str = CACHE) -> int:
-    """Radix width the cache recommends for a plain sort (8 when unknown)."""
-    gpu = load_cache(path).get(_gpu_name(), {}) if os.path.exists(path) else {}
-    cands = [(abs(int(k.rsplit("/b", 1)[1]) - _bucket(n)), k) for k in gpu
-             if k.startswith(f"plain/k{key_bits}/v{val_bits}/")]
-    if not cands:
-        return 8
-    return gpu[min(cands)[1]]["best"]["radix_bits"]
+def apply(key_bits: int, val_bits: int, n: int | None = None, path: str = CACHE) -> dict:
+    """Load the cache for this GPU into the library (apply_all) and report what
+    a sort of (key_bits, val_bits, n) keys now resolves to."""
+    applied = apply_all(path=path)
+    out = {}
+    if n is not None:
+        rb, v = resolve(n, key_bits, val_bits, 0)
+        out["plain"] = {"radix_bits": rb, "variant": v}
+    seg = applied.get(seg_key(key_bits, val_bits))
+    if seg:
+        out["segmented"] = seg
+    return out
+
+
+def best_radix(key_bits: int, val_bits: int, n: int) -> int:
+    """Radix width the library uses for radix_bits = 0 at n keys."""
+    return resolve(n, key_bits, val_bits, 0)[0]
 
 
 if __name__ == "__main__":

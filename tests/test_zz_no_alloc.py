@@ -5,7 +5,8 @@ latency-critical loop where cudaMalloc could stall the device, code that must
 not run out of memory after start-up) get a variant of the radix-256 keys-only
 sort whose scratch is a fixed array inside the library. This file checks,
 through the C-ABI, that two calls in a row give exactly what the ordinary
-isort_keys gives on the same inputs, and that a size beyond the fixed array is
+isort_keys gives on the same inputs, that the calls allocate nothing, that the
+required error word is enforced, and that a size beyond the fixed array is
 refused. It is named to be collected last, and works alone in a fresh process
 as well as after the other tests.
 """
@@ -45,10 +46,42 @@ def test_noalloc_matches_isort_keys_on_two_calls_in_a_row():
         assert np.array_equal(a.cpu().numpy(), np.sort(host))
 
 
+def test_noalloc_allocates_nothing():
+    host = inputs.keys(300_007, 32, "uniform", seed=33)
+    keys = torch.from_numpy(host).cuda()
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    side = torch.cuda.Stream()  # a stream that has never had a workspace
+    torch.cuda.synchronize()
+    ws_before = isort.workspace_bytes()
+    torch_before = torch.cuda.memory_allocated()
+    with torch.cuda.stream(side):
+        isort.sort_keys_noalloc(keys, err)
+    side.synchronize()
+    assert isort.workspace_bytes() == ws_before
+    assert torch.cuda.memory_allocated() == torch_before
+    assert int(err.item()) == 0
+    assert np.array_equal(keys.cpu().numpy(), np.sort(host))
+
+
+def test_noalloc_requires_its_error_word():
+    lib = _lib.load()
+    a = torch.from_numpy(inputs.keys(1000, 32, "uniform", seed=34)).cuda()
+    assert lib.isort_keys_noalloc(ctypes.c_void_p(a.data_ptr()), a.numel(), None,
+                                  None) == _lib.EINVAL
+    with pytest.raises(ValueError):
+        isort.sort_keys_noalloc(a, None)
+    with pytest.raises(ValueError):
+        isort.sort_keys_noalloc(a, torch.zeros(1, dtype=torch.int32))        # host tensor
+    with pytest.raises(ValueError):
+        isort.sort_keys_noalloc(a, torch.zeros(1, dtype=torch.int64, device="cuda"))
+
+
 def test_noalloc_refuses_sizes_beyond_its_array():
     lib = _lib.load()
     a = torch.empty(_lib.NOALLOC_MAX_KEYS + 1, dtype=torch.uint32, device="cuda")
-    rc = lib.isort_keys_noalloc(ctypes.c_void_p(a.data_ptr()), a.numel(), None, None)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = lib.isort_keys_noalloc(ctypes.c_void_p(a.data_ptr()), a.numel(),
+                                ctypes.c_void_p(err.data_ptr()), None)
     assert rc == _lib.ENOMEM
     with pytest.raises(isort.IsortError):
-        isort.sort_keys_noalloc(a)
+        isort.sort_keys_noalloc(a, err)
