@@ -242,7 +242,14 @@ enum {
   ISORT_DEBUG_TRACE_PASS = 5,
   /* value = L2 prefetch distance of the radix-256 rounds in tiles (0 = off,
    * -1 = default: one wave, SMs x 4). A tuning knob; results are unchanged. */
-  ISORT_DEBUG_PREFETCH_TILES = 6
+  ISORT_DEBUG_PREFETCH_TILES = 6,
+  /* Keys-only rounds after the first rank keys by the order in which shared
+   * atomics serve the lanes of a warp and then check every tile (a tile that
+   * fails is ranked again stably). value 1: every tile takes that stable
+   * re-rank; value 2: the fast ranks are deliberately made unstable (odd lanes
+   * first), which the check must catch; 0 = normal. Test hooks; results are
+   * unchanged. */
+  ISORT_DEBUG_CHECK_MODE = 7
 };
 isort_status isort_debug_set(int what, int64_t value);
 

@@ -18,6 +18,7 @@ STATUS = {0: "ISORT_OK", 1: "ISORT_EINVAL", 2: "ISORT_ENOMEM", 3: "ISORT_ECUDA",
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
 DEBUG_SPIN_LIMIT, DEBUG_STALL_TILE, DEBUG_KERNEL_TIMING = 1, 2, 3
 DEBUG_TRACE_PTR, DEBUG_TRACE_PASS, DEBUG_PREFETCH_TILES = 4, 5, 6
+DEBUG_CHECK_MODE = 7
 NOALLOC_MAX_KEYS = 1 << 20
 NET_BTN, NET_OET = 0, 1
 

@@ -38,6 +38,7 @@ bool g_timing = false;
 unsigned long long* g_trace = nullptr;
 int g_trace_pass = 0;
 int64_t g_prefetch = -1;  // L2 prefetch distance in tiles; -1: one wave (SMs x 4)
+uint32_t g_check_mode = 0;  // test hook of the ordered keys-only rounds
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -290,6 +291,7 @@ isort_status run_lsd(void* keys, void* vals, int64_t n, int key_bits, int val_bi
   a.trace = g_trace;
   a.trace_pass = g_trace_pass;
   a.prefetch_tiles = g_prefetch < 0 ? (int64_t)a.num_sms * 4 : g_prefetch;
+  a.check_mode = g_check_mode;
   a.timer = nullptr;
   if (g_timing) {
     if (!g_timer.ready) {
@@ -354,6 +356,7 @@ SegArgs seg_args(const SegConfig& c, const SegLayout& L, char* b, void* keys, vo
   a.err = reinterpret_cast<uint32_t*>(b + L.err);
   a.spin_limit = g_spin_limit;
   a.num_sms = num_sms();
+  a.check_mode = g_check_mode;
   a.timer = nullptr;
   if (g_timing) {
     if (!g_timer.ready) {
@@ -833,6 +836,10 @@ isort_status isort_debug_set(int what, int64_t value) {
       return ISORT_OK;
     case ISORT_DEBUG_PREFETCH_TILES:
       g_prefetch = value;
+      return ISORT_OK;
+    case ISORT_DEBUG_CHECK_MODE:
+      if (value < 0 || value > 2) return ISORT_EINVAL;
+      g_check_mode = (uint32_t)value;
       return ISORT_OK;
   }
   return ISORT_EINVAL;

@@ -42,6 +42,7 @@ struct LsdArgs {
   unsigned long long* trace;  // measurement hook: per-tile phase timestamps of one pass
   int trace_pass;
   int64_t prefetch_tiles;     // L2 prefetch distance of the rounds, in tiles (0: off)
+  uint32_t check_mode;        // test hook of the ordered keys-only rounds (0: normal)
 };
 
 typedef cudaError_t (*LsdLaunchFn)(const LsdArgs&, cudaStream_t);
@@ -56,7 +57,6 @@ struct LsdEntry {
   size_t status_words_per_tile;  // look-back words per tile per buffer
   int status_buffers;            // look-back buffers (2: alternate by pass)
   LsdLaunchFn launch;
-  int cluster;                   // CTAs per cluster super-tile (1: none)
 };
 
 // Variant tables, one per key width (sort_k32.cu, sort_k64.cu).
@@ -98,6 +98,7 @@ struct SegArgs {
   uint32_t spin_limit;
   int num_sms;
   KernelTimer* timer;
+  uint32_t check_mode;   // test hook of the ordered keys-only rounds (0: normal)
 };
 
 // Host side: configuration of one (key, payload) family and its launcher.

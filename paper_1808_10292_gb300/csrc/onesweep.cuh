@@ -27,16 +27,12 @@
 //               the first round's input order carries no information.
 //   k_copy_back copies the result home when an odd number of rounds ran.
 #pragma once
-#include <cooperative_groups.h>
-
 #include <algorithm>
 
 #include "common.cuh"
 #include "isort_internal.h"
 
 namespace isort {
-
-namespace cg = cooperative_groups;
 
 template <typename K, int BITS>
 struct DigitLayout {
@@ -194,7 +190,13 @@ struct PassParams {
   int64_t stall_tile;
   unsigned long long* trace;  // measurement hook: per tile, phase timestamps (or null)
   int64_t prefetch_tiles;     // L2-prefetch the input of the tile this many ids ahead (0: off)
+  uint32_t check_mode;        // test hook of the ordered rounds (kCheck*; 0 in normal use)
 };
+
+// Test hooks of the ordered keys-only rounds (onesweep_tile_ordered).
+constexpr uint32_t kCheckNormal = 0;
+constexpr uint32_t kCheckForceFallback = 1;  // every tile takes the stable re-rank
+constexpr uint32_t kCheckPerturb = 2;        // odd lanes take their slots first (unstable)
 
 // The digit of a key in one round: bits [shift, shift + width) of the key. The
 // early-counts tile functions take the digit as a function object, so a round
@@ -323,8 +325,9 @@ __device__ __forceinline__ void zero_words(uint32_t* p, int words) {
   for (int i = threadIdx.x; i < words / 4; i += THREADS) q[i] = make_uint4(0, 0, 0, 0);
 }
 
-// ---- the phases of one tile (shared by the plain, segmented and cluster
-// rounds). FULL: the tile holds TILE keys, so no per-key bounds predicate.
+// ---- the phases of one tile (shared by the plain and segmented rounds and
+// the sample sort's split round). FULL: the tile holds TILE keys, so no
+// per-key bounds predicate.
 
 // Load: warp w owns keys [w*32*KPT, (w+1)*32*KPT) of the tile, lane-striped,
 // so each warp instruction reads 32 consecutive keys.
@@ -340,52 +343,6 @@ __device__ __forceinline__ void tile_load(const K* __restrict__ kin, const V* vi
 #pragma unroll
     for (int i = 0; i < KPT; ++i)
       val[i] = (FULL || wofs + i * 32 < tile_n) ? vin[g0 + i * 32] : V(0);
-  }
-}
-
-// Rank: position of each key among the warp's keys of the same digit, in input
-// order (i ascending, then lane ascending). Lanes find their peers (same digit,
-// same iteration) through a per-warp shared-memory mask per digit: each lane
-// ORs in its bit, and after a warp barrier reads the mask back. The highest
-// peer advances the warp's private counter of the digit with one atomic add
-// (cheaper than a dependent read and write) and hands the new value to its
-// peers.
-// Ordering with one warp barrier per iteration: three mask buffers rotate, and
-// the slot used in iteration i-2 is cleared in iteration i -- after the barrier
-// of i-1 (so every read of it is done) and before the barrier of i (which
-// precedes the next OR into that buffer, in i+1). A counter update of
-// iteration i precedes the barrier of i+1, which precedes the next update.
-// The masks live in the staging area (zeroed), which is free until the
-// reorder. Ranks (< TILE <= 65536) are kept as 16-bit halves.
-template <typename K, int R, int KPT, int MASK_BUFS, bool FULL>
-__device__ __forceinline__ void tile_rank(const K (&key)[KPT], int shift, uint32_t mask,
-                                          int tile_n, int wofs, uint32_t* my, uint32_t* mm,
-                                          uint32_t (&rank2)[(KPT + 1) / 2]) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t ge = lanemask_ge();
-  const uint32_t bit = 1u << lane;
-  uint32_t* slot1 = mm;  // slot of iteration i-1
-  uint32_t* slot2 = mm;  // slot of iteration i-2
-  bool lead1 = false, lead2 = false;
-#pragma unroll
-  for (int i = 0; i < KPT; ++i) {
-    const bool valid = FULL || wofs + i * 32 < tile_n;
-    const uint32_t d = digit_of(key[i], shift, mask);
-    uint32_t* slot = mm + (i % MASK_BUFS) * R + d;
-    if (lead2) *slot2 = 0u;
-    if (valid) atomicOr(slot, bit);
-    __syncwarp();
-    const uint32_t peers = valid ? *slot : 0u;
-    const bool leader = valid && (peers >> lane) == 1u;  // highest peer
-    uint32_t after = 0;
-    if (leader) after = atomicAdd(&my[d], __popc(peers)) + __popc(peers);
-    after = __shfl_sync(kFullMask, after, (31 - __clz(peers)) & 31);
-    const uint32_t r = after - __popc(peers & ge);  // = old count + peers below me
-    rank2[i >> 1] = (i & 1) ? (rank2[i >> 1] | (r << 16)) : r;
-    slot2 = slot1;
-    lead2 = lead1;
-    slot1 = slot;
-    lead1 = leader;
   }
 }
 
@@ -409,26 +366,6 @@ __device__ __forceinline__ uint32_t tile_digit_counts(uint32_t* s_wcnt, int tid,
     tsum += sum;
   }
   return tsum;
-}
-
-// Reorder the tile by digit in shared memory (stable by construction); with
-// payloads, rank2 then holds each key's tile position.
-template <typename K, typename V, int KPT, bool FULL>
-__device__ __forceinline__ void tile_reorder(const K (&key)[KPT], uint32_t (&rank2)[(KPT + 1) / 2],
-                                             int shift, uint32_t mask, int tile_n, int wofs,
-                                             const uint32_t* myofs, K* s_keys) {
-#pragma unroll
-  for (int i = 0; i < KPT; ++i) {
-    if (FULL || wofs + i * 32 < tile_n) {
-      const uint32_t r = (rank2[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
-      const uint32_t pos = myofs[digit_of(key[i], shift, mask)] + r;
-      s_keys[pos] = key[i];
-      if constexpr (HasVal<V>::value) {  // keep the tile position for the payload pass
-        rank2[i >> 1] = (i & 1) ? ((rank2[i >> 1] & 0xffffu) | (pos << 16))
-                                : ((rank2[i >> 1] & 0xffff0000u) | pos);
-      }
-    }
-  }
 }
 
 // Write out: consecutive threads take consecutive tile slots, so each digit's
@@ -486,77 +423,12 @@ __device__ __forceinline__ void tile_count(const K (&key)[KPT], const DS& dig, i
 // key (peer masks, as in tile_rank) is its final tile position and the key is
 // written straight into the staging area. The masks live in a separate area
 // (the staging area is being filled). rank2 receives the positions.
-//
-// RELAX (keys only, rounds after the first): the round's input is sorted by
-// the key bits below its digit (`low`), so keys with equal digits need their
-// input order kept only between runs of equal low bits; inside a run, equal
-// digits mean equal keys so far, in any order. When the warp holds one run
-// (its first and last key agree on the low bits), or a few (at most
-// kRelaxRuns + 1, bounded by the difference of those low bits), every key
-// takes its slot with its own add on the warp's counter, with no masks; with
-// several runs a warp barrier between two keeps the runs in order. The warps'
-// counters start at their own offsets, so the order between warps is kept
-// either way.
-constexpr int kRelaxRuns = 32;  // runs per warp (beyond the first) the relaxed form takes on
-
-template <typename K, int R, int KPT, int MASK_BUFS, bool FULL, bool RELAX = false,
-          typename DS>
+template <typename K, int R, int KPT, int MASK_BUFS, bool FULL, typename DS>
 __device__ __forceinline__ void tile_rank_place(const K (&key)[KPT], const DS& dig, int tile_n,
-                                                int wofs, uint32_t* my,
-                                                uint32_t* mm, K* s_keys,
-                                                uint32_t (&rank2)[(KPT + 1) / 2], K low = 0) {
+                                                int wofs, uint32_t* my, uint32_t* mm, K* s_keys,
+                                                uint32_t (&rank2)[(KPT + 1) / 2]) {
   static_assert(MASK_BUFS == 3, "row r marks slot array r mod 3");
   const int lane = threadIdx.x & 31;
-  if constexpr (RELAX) {
-    const K first = __shfl_sync(kFullMask, key[0], 0);
-    const K last = __shfl_sync(kFullMask, key[KPT - 1], 31);
-    const bool full = FULL || wofs - lane + KPT * 32 <= tile_n;
-    // The warp's keys are sorted by their low bits, so they form at most
-    // span + 1 runs of equal low bits.
-    const K span = (last & low) - (first & low);
-    if (full && span == 0) {  // one run: no order to keep at all (warp-uniform)
-#pragma unroll
-      for (int i = 0; i < KPT; ++i) {
-        const uint32_t d = dig.of(key[i], i);
-        const uint32_t pos = atomicAdd(&my[d], 1u);
-        s_keys[pos] = key[i];
-        dig.keep(pos, d);
-        rank2[i >> 1] = (i & 1) ? (rank2[i >> 1] | (pos << 16)) : pos;
-      }
-      return;
-    }
-    if (full && span <= K(kRelaxRuns)) {  // a few runs (warp-uniform)
-      const uint32_t le = lanemask_lt() | (1u << lane);
-      K prev = first;  // at lane 0: the previous row's last key (row 0: itself)
-#pragma unroll
-      for (int i = 0; i < KPT; ++i) {
-        // lanes that start a new run (their low bits differ from the key before)
-        const K rot = __shfl_sync(kFullMask, key[i], (lane + 31) & 31);
-        const K before = lane ? rot : prev;
-        prev = rot;  // at lane 0: this row's last key
-        const uint32_t starts = __ballot_sync(kFullMask, ((key[i] ^ before) & low) != 0);
-        const uint32_t d = dig.of(key[i], i);
-        uint32_t pos = 0;
-        if (starts == 0) {  // one run, the one the previous row ended in
-          pos = atomicAdd(&my[d], 1u);
-        } else {
-          // segments of the row split at run starts take their slots in order,
-          // a warp barrier between two (segment 0 is empty when lane 0 starts a
-          // run: its barrier orders the row after the previous one)
-          const int seg = __popc(starts & le), segs = __popc(starts);
-#pragma unroll 1
-          for (int sg = 0; sg <= segs; ++sg) {
-            if (seg == sg) pos = atomicAdd(&my[d], 1u);
-            if (sg < segs) __syncwarp();
-          }
-        }
-        s_keys[pos] = key[i];
-        dig.keep(pos, d);
-        rank2[i >> 1] = (i & 1) ? (rank2[i >> 1] | (pos << 16)) : pos;
-      }
-      return;
-    }
-  }
   const uint32_t ge = lanemask_ge();
   const uint32_t bit = 1u << lane;
   auto valid_row = [&](int i) { return FULL || wofs + i * 32 < tile_n; };
@@ -618,9 +490,8 @@ struct EarlyShape {
 // tile's counts, scan, rank straight into the reordered tile, look back,
 // publish the inclusive counts, write out.
 // dig: the key -> digit rule of this round (RadixDigit for a radix round).
-// RELAX: see tile_rank_place (keys only, RadixDigit rounds).
 template <typename K, typename V, int BITS, int THREADS, int KPT, bool FULL,
-          typename DS = RadixDigit, bool RELAX = false>
+          typename DS = RadixDigit>
 __device__ __forceinline__ void onesweep_tile_early(const PassParams& p, uint32_t tile, bool first,
                                                     int64_t tile_base, int tile_n,
                                                     const K* __restrict__ kin,
@@ -676,13 +547,9 @@ __device__ __forceinline__ void onesweep_tile_early(const PassParams& p, uint32_
   }
   __syncthreads();
   uint32_t rank2[(KPT + 1) / 2];
-  static_assert(!RELAX || !HV, "equal keys keep their payloads' order: no relaxed warps");
-  K low = 0;  // key bits below this round's digit
-  if constexpr (RELAX) low = p.shift ? (K(1) << p.shift) - K(1) : K(0);
-  tile_rank_place<K, R, KPT, S::MASK_BUFS, FULL, RELAX>(key, dig, tile_n, wofs,
-                                                        s_wcnt + warp * R,
-                                                        s_masks + warp * S::MASK_BUFS * R,
-                                                        s_keys, rank2, low);
+  tile_rank_place<K, R, KPT, S::MASK_BUFS, FULL>(key, dig, tile_n, wofs, s_wcnt + warp * R,
+                                                 s_masks + warp * S::MASK_BUFS * R, s_keys,
+                                                 rank2);
   if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 2] = globaltimer();
 
   // look back over earlier tiles, publish the inclusive counts, output offsets
@@ -711,43 +578,57 @@ __device__ __forceinline__ void onesweep_tile_early(const PassParams& p, uint32_
   if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 5] = globaltimer();
 }
 
-// One tile of one count-sort round with the decoupled look-back.
-//   tile       row of the look-back arrays (tile id in launch order)
-//   first      the tile opens its range (segment), so it has no predecessor
-//   tile_base  index of the tile's first key in kin / vin
-//   kout/vout  the range's output (positions are relative to the range start)
-//   base       [R] the range's exclusive digit bases for this pass
-//   bound      keys in the range (every output index is checked against it)
-template <typename K, typename V, int BITS, int THREADS, int KPT, bool FULL>
-__device__ __forceinline__ void onesweep_tile(const PassParams& p, uint32_t tile, bool first,
-                                              int64_t tile_base, int tile_n,
-                                              const K* __restrict__ kin, K* __restrict__ kout,
-                                              const V* vin, V* vout, const uint32_t* base,
-                                              uint32_t bound, unsigned char* smem) {
-  using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
+// Shared memory of the ordered round: the per-warp counters, digit offsets and
+// misc words, then the staging area of the tile (no peer masks).
+template <typename K, int BITS, int THREADS, int KPT>
+struct OrderedShape {
+  using S = OnesweepShape<K, NoVal, BITS, THREADS, KPT>;
+  static constexpr size_t SMEM = (size_t)S::HEADER_WORDS * 4 + (size_t)S::TILE * sizeof(K);
+};
+
+// One tile of a keys-only round after the first, "ordered" form. A key's
+// stable rank among the warp's keys of its digit is the value one shared-memory
+// atomicAdd on the warp's counter of the digit returns, provided the lanes of
+// one warp instruction that hit the same counter are served in lane order and
+// successive instructions in program order -- which is what GB300 does (a probe
+// of a million 32-lane rows found no exception), but nothing in CUDA promises
+// it. So the tile checks its result instead of trusting the order: the round's
+// input is sorted by the key bits below its digit (`low`; the invariant of LSD
+// rounds on keys), hence the tile is placed acceptably iff every digit run of
+// the staged tile is non-decreasing in those bits (keys that agree on the digit
+// and the low bits may take either order: later rounds order them by their
+// higher bits, or they are equal). The write-out compares each staged key with
+// its successor; a tile that fails is ranked again stably (peers found with
+// __match_any_sync) and written out again to the same positions.
+// Per key the fast path makes three digit-indexed shared accesses (count add,
+// slot add, store) against the peer-mask round's six.
+template <typename K, int BITS, int THREADS, int KPT, bool FULL>
+__device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint32_t tile,
+                                                      bool first, int64_t tile_base, int tile_n,
+                                                      const K* __restrict__ kin,
+                                                      K* __restrict__ kout, const uint32_t* base,
+                                                      uint32_t bound, unsigned char* smem) {
+  using S = OnesweepShape<K, NoVal, BITS, THREADS, KPT>;
   constexpr int R = S::R, WARPS = S::WARPS, DPT = S::DPT;
-  constexpr bool HV = S::HV;
   uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);  // [WARPS][R]
   uint32_t* s_adj = s_wcnt + WARPS * R;                   // [R]
   uint32_t* s_misc = s_adj + R;                           // [64]
   K* s_keys = reinterpret_cast<K*>(smem + S::HEADER_WORDS * 4);
-  V* s_vals = reinterpret_cast<V*>(smem + S::HEADER_WORDS * 4);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wofs = warp * 32 * KPT + lane;
   const bool publish = (int64_t)tile != p.stall_tile;
+  RadixDigit dig{p};
+  uint32_t* my = s_wcnt + warp * R;
+  // the fallback re-reads the tile's input address from here (fewer live registers)
+  if (tid == 0) *reinterpret_cast<const K**>(s_misc + 48) = kin + tile_base;
 
   K key[KPT];
-  V val[HV ? KPT : 1];
-  tile_load<K, V, KPT, FULL>(kin, vin, tile_base, tile_n, wofs, key, val);
-  uint32_t rank2[(KPT + 1) / 2];
-  tile_rank<K, R, KPT, S::MASK_BUFS, FULL>(
-      key, p.shift, p.mask, tile_n, wofs, s_wcnt + warp * R,
-      reinterpret_cast<uint32_t*>(s_keys) + warp * S::MASK_BUFS * R, rank2);
+  NoVal val[1];
+  tile_load<K, NoVal, KPT, FULL>(kin, nullptr, tile_base, tile_n, wofs, key, val);
+  tile_count<K, R, KPT, FULL>(key, dig, tile_n, wofs, my);
   __syncthreads();
-  if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 1] = globaltimer();
 
-  // ---- per digit: warp-exclusive offsets and the tile's count, published at
-  // once (AGG, or INC for the first tile) so that later tiles can use it
+  // per digit: the tile's count (published now), warp starts, tile starts
   uint32_t dcnt[DPT];
   uint32_t tsum = 0;
   const bool owner = tid < S::DTHREADS;
@@ -761,51 +642,143 @@ __device__ __forceinline__ void onesweep_tile(const PassParams& p, uint32_t tile
   }
   uint32_t total;
   uint32_t run = block_exclusive_scan<THREADS>(tsum, s_misc + 1, total);
-
-  // ---- look-back over earlier tiles, then publish the inclusive count
-  uint32_t windows = 0;
-  if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 2] = globaltimer();
+  uint32_t tstart[DPT];
   if (owner) {
 #pragma unroll
     for (int j = 0; j < DPT; ++j) {
       const int d = tid * DPT + j;
-      const uint32_t tstart = run;  // tile-local start of digit d
+      tstart[j] = run;
+#pragma unroll
+      for (int w = 0; w < WARPS; ++w) s_wcnt[w * R + d] += run;
       run += dcnt[j];
+    }
+  }
+  __syncthreads();
+
+  // place: one slot add per key
+  if (p.check_mode != kCheckPerturb) {
+#pragma unroll
+    for (int i = 0; i < KPT; ++i)
+      if (FULL || wofs + i * 32 < tile_n) {
+        const uint32_t pos = atomicAdd(&my[dig.of(key[i], i)], 1u);
+        s_keys[pos] = key[i];
+      }
+  } else {  // test hook: odd lanes of each row first, an order the check must reject
+#pragma unroll
+    for (int i = 0; i < KPT; ++i) {
+      const bool valid = FULL || wofs + i * 32 < tile_n;
+      uint32_t pos = 0;
+      if (valid && (lane & 1)) pos = atomicAdd(&my[dig.of(key[i], i)], 1u);
+      __syncwarp();
+      if (valid && !(lane & 1)) pos = atomicAdd(&my[dig.of(key[i], i)], 1u);
+      __syncwarp();
+      if (valid) s_keys[pos] = key[i];
+    }
+  }
+
+  // look back over earlier tiles, publish the inclusive counts, output offsets
+  uint32_t windows = 0;
+  if (owner) {
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+      const int d = tid * DPT + j;
       uint32_t excl = 0;
       if (!first) {
         excl = lookback_exclusive<R, kLookbackWindow>(p.status, tile, d, p.spin_limit, p.err,
                                                       windows);
         if (publish) st_relaxed(&p.status[(size_t)tile * R + d], kFlagInc | (excl + dcnt[j]));
       }
-      s_adj[d] = base[d] + excl - tstart;
-#pragma unroll
-      for (int w = 0; w < WARPS; ++w) s_wcnt[w * R + d] += tstart;
+      s_adj[d] = base[d] + excl - tstart[j];
     }
   }
-  if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 6] = windows;
   __syncthreads();
-  if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 3] = globaltimer();
 
-  tile_reorder<K, V, KPT, FULL>(key, rank2, p.shift, p.mask, tile_n, wofs, s_wcnt + warp * R,
-                                s_keys);
+  // write out, checking every staged key against the next one of its run
+  const K low = p.shift ? (K(1) << p.shift) - K(1) : K(0);
+  bool bad = p.check_mode == kCheckForceFallback;
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    const int j = k * THREADS + tid;
+    if (FULL || j < tile_n) {
+      const K kk = s_keys[j];
+      const uint32_t d = dig.staged(kk, j);
+      const uint32_t g = s_adj[d] + (uint32_t)j;
+      if (g < bound)
+        kout[g] = kk;
+      else
+        atomicOr(p.err, kErrBounds);
+      if (j + 1 < (FULL ? S::TILE : tile_n)) {
+        const K nx = s_keys[j + 1];
+        bad |= dig.staged(nx, j + 1) == d && (nx & low) < (kk & low);
+      }
+    }
+  }
+  if (!__syncthreads_or(bad)) return;
+
+  // Fallback: rank the tile again, stably, and write it out again. After the
+  // slot adds, warp w's counter of digit d holds warp w+1's start, and the
+  // last warp's holds the end of the digit's run, i.e. the start of digit d+1:
+  // shift the rows back to the warp starts.
+  uint32_t prev_end[DPT];
+  if (owner)
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+      const int d = tid * DPT + j;
+      prev_end[j] = d ? s_wcnt[(WARPS - 1) * R + d - 1] : 0u;
+    }
   __syncthreads();
-  if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 4] = globaltimer();
-
-  tile_scatter<K, V, THREADS, KPT, FULL>(s_keys, s_vals, s_adj, val, rank2,
-                                         RadixDigit{p}, tile_n, wofs, kout, vout,
-                                         bound, p.err);
-  if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 5] = globaltimer();
+  if (owner)
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+      const int d = tid * DPT + j;
+#pragma unroll
+      for (int w = WARPS - 1; w > 0; --w) s_wcnt[w * R + d] = s_wcnt[(w - 1) * R + d];
+      s_wcnt[d] = prev_end[j];
+    }
+  __syncthreads();
+  // Row by row, keys re-read from the input: peers by __match_any_sync, the
+  // highest peer advances the counter, ranks in lane order (slow, but this path
+  // is for tiles whose check failed).
+  const uint32_t lt = lanemask_lt();
+  const K* tile_in = *reinterpret_cast<const K* const*>(s_misc + 48);
+  uint32_t* my_row = s_wcnt + (threadIdx.x >> 5) * R;
+  const int wofs2 = (threadIdx.x >> 5) * 32 * KPT + (threadIdx.x & 31);
+#pragma unroll 1
+  for (int i = 0; i < KPT; ++i) {
+    const bool valid = FULL || wofs2 + i * 32 < tile_n;
+    const K k = valid ? tile_in[wofs2 + i * 32] : K(0);
+    const uint32_t d = dig(k);
+    const uint32_t peers = __match_any_sync(kFullMask, valid ? d : (0x80000000u | lane));
+    uint32_t old = 0;
+    if (valid && (peers >> lane) == 1u) old = atomicAdd(&my_row[d], __popc(peers));
+    old = __shfl_sync(kFullMask, old, 31 - __clz(peers));
+    if (valid) s_keys[old + __popc(peers & lt)] = k;
+    __syncwarp();  // this row's counter updates precede the next row's
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int j = tid; j < tile_n; j += THREADS) {
+    const K kk = s_keys[j];
+    const uint32_t g = s_adj[dig.staged(kk, j)] + (uint32_t)j;
+    if (g < bound)
+      kout[g] = kk;
+    else
+      atomicOr(p.err, kErrBounds);
+  }
 }
 
-template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB, bool EARLY>
+// One count-sort round over all n keys, one tile per CTA (tile ids in launch
+// order). Keys only: the ordered round; with payloads: the early-counts round
+// with the stable peer-mask rank.
+template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
   constexpr int R = S::R, WARPS = S::WARPS, TILE = S::TILE;
+  constexpr bool ORDERED = !HasVal<V>::value;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
   uint32_t* s_misc = s_wcnt + WARPS * R + R;
-  uint32_t* s_stage = reinterpret_cast<uint32_t*>(
-      smem + (EARLY ? EarlyShape<K, V, BITS, THREADS, KPT>::MASKS : S::HEADER_WORDS * 4));
+  uint32_t* s_masks = reinterpret_cast<uint32_t*>(smem + EarlyShape<K, V, BITS, THREADS, KPT>::MASKS);
   const int tid = threadIdx.x;
 
   // Rows of the next pass's look-back array are cleared here, so one memset
@@ -819,7 +792,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
 
   if (tid == 0) s_misc[0] = atomicAdd(p.counter, 1u);  // tiles in launch order
   zero_words<THREADS>(s_wcnt, WARPS * R);
-  zero_words<THREADS>(s_stage, WARPS * S::MASK_BUFS * R);
+  if constexpr (!ORDERED) zero_words<THREADS>(s_masks, WARPS * S::MASK_BUFS * R);
   __syncthreads();
   const uint32_t tile = s_misc[0];
   const int tile_n = (int)min((int64_t)TILE, p.n - (int64_t)tile * TILE);
@@ -837,29 +810,26 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
   // select with branches, not a dynamic index, so the parameters stay out of local memory
   const K* kin = static_cast<const K*>(src ? p.keys[1] : p.keys[0]);
   K* kout = static_cast<K*>(src ? p.keys[0] : p.keys[1]);
-  const V* vin = static_cast<const V*>(src ? p.vals[1] : p.vals[0]);
-  V* vout = static_cast<V*>(src ? p.vals[0] : p.vals[1]);
   const int64_t tile_base = (int64_t)tile * TILE;
-  if constexpr (EARLY) {
-    RadixDigit dig{p};
-    // keys only, 32-bit keys (for 64-bit keys the extra registers of the test
-    // spill in every round, and only rounds 1 and 2 have shared low bits)
-    constexpr bool RELAX = !HasVal<V>::value && sizeof(K) == 4;
+  if constexpr (ORDERED) {
     if (tile_n == TILE)
-      onesweep_tile_early<K, V, BITS, THREADS, KPT, true, RadixDigit, RELAX>(
-          p, tile, tile == 0, tile_base, tile_n, kin, kout, vin, vout, p.base, (uint32_t)p.n,
-          smem, dig);
+      onesweep_tile_ordered<K, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n,
+                                                         kin, kout, p.base, (uint32_t)p.n, smem);
     else
-      onesweep_tile_early<K, V, BITS, THREADS, KPT, false, RadixDigit, RELAX>(
-          p, tile, tile == 0, tile_base, tile_n, kin, kout, vin, vout, p.base, (uint32_t)p.n,
-          smem, dig);
+      onesweep_tile_ordered<K, BITS, THREADS, KPT, false>(p, tile, tile == 0, tile_base, tile_n,
+                                                          kin, kout, p.base, (uint32_t)p.n, smem);
   } else {
+    const V* vin = static_cast<const V*>(src ? p.vals[1] : p.vals[0]);
+    V* vout = static_cast<V*>(src ? p.vals[0] : p.vals[1]);
+    RadixDigit dig{p};
     if (tile_n == TILE)
-      onesweep_tile<K, V, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n, kin,
-                                                    kout, vin, vout, p.base, (uint32_t)p.n, smem);
+      onesweep_tile_early<K, V, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n,
+                                                          kin, kout, vin, vout, p.base,
+                                                          (uint32_t)p.n, smem, dig);
     else
-      onesweep_tile<K, V, BITS, THREADS, KPT, false>(p, tile, tile == 0, tile_base, tile_n, kin,
-                                                     kout, vin, vout, p.base, (uint32_t)p.n, smem);
+      onesweep_tile_early<K, V, BITS, THREADS, KPT, false>(p, tile, tile == 0, tile_base, tile_n,
+                                                           kin, kout, vin, vout, p.base,
+                                                           (uint32_t)p.n, smem, dig);
   }
 }
 
@@ -1008,358 +978,6 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep_first(PassParams p) 
 }
 
 // ---------------------------------------------------------------------------
-// TMA variant of the round (keys only): one thread issues bulk copies of the
-// whole tile into shared memory as soon as the tile id is known, completing on
-// an mbarrier, while the CTA clears its counters. Ranking and the reorder read
-// the keys from shared memory, so no key array lives in registers and larger
-// tiles fit without spilling. Tiles whose input is not 16-byte aligned, and
-// the ragged last tile, are loaded into the same buffer with plain loads.
-template <typename K, int BITS, int THREADS, int KPT>
-struct TmaShape {
-  using S = OnesweepShape<K, NoVal, BITS, THREADS, KPT>;
-  static constexpr size_t RAW = S::HEADER_WORDS * 4 + S::STAGE_BYTES;  // raw tile
-  static constexpr size_t BAR = RAW + sizeof(K) * S::TILE;             // mbarrier
-  static constexpr size_t SMEM = BAR + 16;
-  static constexpr uint32_t CHUNK = 16384;  // bytes per bulk copy
-};
-
-template <typename K, int BITS, int THREADS, int KPT, bool FULL>
-__device__ __forceinline__ void onesweep_tile_tma(const PassParams& p, uint32_t tile, int tile_n,
-                                                  const K* raw, K* __restrict__ kout,
-                                                  unsigned char* smem) {
-  using S = OnesweepShape<K, NoVal, BITS, THREADS, KPT>;
-  constexpr int R = S::R, WARPS = S::WARPS, DPT = S::DPT;
-  uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* s_adj = s_wcnt + WARPS * R;
-  uint32_t* s_misc = s_adj + R;
-  K* s_keys = reinterpret_cast<K*>(smem + S::HEADER_WORDS * 4);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wofs = warp * 32 * KPT + lane;
-  const bool first = tile == 0;
-  const bool publish = (int64_t)tile != p.stall_tile;
-
-  // rank straight from the shared tile (same peer-mask ranking as tile_rank)
-  uint32_t rank2[(KPT + 1) / 2];
-  {
-    uint32_t* my = s_wcnt + warp * R;
-    uint32_t* mm = reinterpret_cast<uint32_t*>(s_keys) + warp * S::MASK_BUFS * R;
-    const uint32_t ge = lanemask_ge();
-    const uint32_t bit = 1u << lane;
-    uint32_t* slot1 = mm;
-    uint32_t* slot2 = mm;
-    bool lead1 = false, lead2 = false;
-#pragma unroll
-    for (int i = 0; i < KPT; ++i) {
-      const bool valid = FULL || wofs + i * 32 < tile_n;
-      const uint32_t d = digit_of(raw[wofs + i * 32], p.shift, p.mask);
-      uint32_t* slot = mm + (i % S::MASK_BUFS) * R + d;
-      if (lead2) *slot2 = 0u;
-      if (valid) atomicOr(slot, bit);
-      __syncwarp();
-      const uint32_t peers = valid ? *slot : 0u;
-      const bool leader = valid && (peers >> lane) == 1u;
-      uint32_t after = 0;
-      if (leader) after = atomicAdd(&my[d], __popc(peers)) + __popc(peers);
-      after = __shfl_sync(kFullMask, after, (31 - __clz(peers)) & 31);
-      const uint32_t r = after - __popc(peers & ge);
-      rank2[i >> 1] = (i & 1) ? (rank2[i >> 1] | (r << 16)) : r;
-      slot2 = slot1;
-      lead2 = lead1;
-      slot1 = slot;
-      lead1 = leader;
-    }
-  }
-  __syncthreads();
-
-  uint32_t dcnt[DPT];
-  uint32_t tsum = 0;
-  const bool owner = tid < S::DTHREADS;
-  if (owner) {
-    tsum = tile_digit_counts<R, WARPS, DPT>(s_wcnt, tid, dcnt);
-    if (publish)
-#pragma unroll
-      for (int j = 0; j < DPT; ++j)
-        st_relaxed(&p.status[(size_t)tile * R + tid * DPT + j],
-                   (first ? kFlagInc : kFlagAgg) | dcnt[j]);
-  }
-  uint32_t total;
-  uint32_t run = block_exclusive_scan<THREADS>(tsum, s_misc + 1, total);
-  if (owner) {
-    uint32_t windows = 0;
-#pragma unroll
-    for (int j = 0; j < DPT; ++j) {
-      const int d = tid * DPT + j;
-      const uint32_t tstart = run;
-      run += dcnt[j];
-      uint32_t excl = 0;
-      if (!first) {
-        excl = lookback_exclusive<R, kLookbackWindow>(p.status, tile, d, p.spin_limit, p.err,
-                                                      windows);
-        if (publish) st_relaxed(&p.status[(size_t)tile * R + d], kFlagInc | (excl + dcnt[j]));
-      }
-      s_adj[d] = p.base[d] + excl - tstart;
-#pragma unroll
-      for (int w = 0; w < WARPS; ++w) s_wcnt[w * R + d] += tstart;
-    }
-  }
-  __syncthreads();
-  // reorder: raw tile -> staging area, by digit
-  {
-    const uint32_t* myofs = s_wcnt + warp * R;
-#pragma unroll
-    for (int i = 0; i < KPT; ++i) {
-      if (FULL || wofs + i * 32 < tile_n) {
-        const K k = raw[wofs + i * 32];
-        const uint32_t r = (rank2[i >> 1] >> ((i & 1) * 16)) & 0xffffu;
-        s_keys[myofs[digit_of(k, p.shift, p.mask)] + r] = k;
-      }
-    }
-  }
-  __syncthreads();
-  const NoVal nv[1] = {};
-  tile_scatter<K, NoVal, THREADS, KPT, FULL>(s_keys, nullptr, s_adj, nv, rank2,
-                                             RadixDigit{p}, tile_n, wofs, kout,
-                                             nullptr, (uint32_t)p.n, p.err);
-}
-
-template <typename K, int BITS, int THREADS, int KPT, int MINB>
-__global__ void __launch_bounds__(THREADS, MINB) k_onesweep_tma(PassParams p) {
-  using S = OnesweepShape<K, NoVal, BITS, THREADS, KPT>;
-  using T = TmaShape<K, BITS, THREADS, KPT>;
-  constexpr int R = S::R, WARPS = S::WARPS, TILE = S::TILE;
-  extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* s_misc = s_wcnt + WARPS * R + R;
-  uint32_t* s_stage = reinterpret_cast<uint32_t*>(smem + S::HEADER_WORDS * 4);
-  K* raw = reinterpret_cast<K*>(smem + T::RAW);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + T::BAR);
-  const int tid = threadIdx.x;
-  if (p.status_next)
-    for (int d = tid; d < R; d += THREADS) p.status_next[(size_t)blockIdx.x * R + d] = 0;
-  if (p.skip[p.pass]) return;  // the digit is constant: this round is the identity
-  int src = 0;
-  for (int q = 0; q < p.pass; ++q) src ^= (p.skip[q] == 0);
-  const K* kin = static_cast<const K*>(src ? p.keys[1] : p.keys[0]);
-  K* kout = static_cast<K*>(src ? p.keys[0] : p.keys[1]);
-  if (tid == 0) {
-    const uint32_t t = atomicAdd(p.counter, 1u);  // tiles in launch order
-    s_misc[0] = t;
-    const int64_t tb = (int64_t)t * TILE;
-    const K* gsrc = kin + tb;
-    const bool tma = tb + TILE <= p.n && (reinterpret_cast<uintptr_t>(gsrc) & 15) == 0;
-    s_misc[33] = tma;
-    if (tma) {
-      mbar_init(bar, 1);
-      fence_mbar_init();
-      constexpr uint32_t BYTES = sizeof(K) * TILE;
-      mbar_arrive_expect_tx(bar, BYTES);
-      for (uint32_t o = 0; o < BYTES; o += T::CHUNK)
-        bulk_copy_g2s(reinterpret_cast<char*>(raw) + o, reinterpret_cast<const char*>(gsrc) + o,
-                      min(T::CHUNK, BYTES - o), bar);
-    }
-    if (p.prefetch_tiles) {
-      const int64_t pf = ((int64_t)t + p.prefetch_tiles) * TILE;
-      prefetch_tile(kin, pf, min((int64_t)TILE, p.n - pf));
-    }
-  }
-  for (int i = tid; i < WARPS * R; i += THREADS) s_wcnt[i] = 0;
-  for (int i = tid; i < WARPS * S::MASK_BUFS * R; i += THREADS) s_stage[i] = 0;
-  __syncthreads();
-  const uint32_t tile = s_misc[0];
-  const int64_t tile_base = (int64_t)tile * TILE;
-  const int tile_n = (int)min((int64_t)TILE, p.n - tile_base);
-  if (!s_misc[33]) {  // unaligned input or the ragged last tile: plain loads into the tile buffer
-    for (int j = tid; j < tile_n; j += THREADS) raw[j] = kin[tile_base + j];
-    __syncthreads();
-    if (tile_n == TILE)
-      onesweep_tile_tma<K, BITS, THREADS, KPT, true>(p, tile, tile_n, raw, kout, smem);
-    else
-      onesweep_tile_tma<K, BITS, THREADS, KPT, false>(p, tile, tile_n, raw, kout, smem);
-    return;
-  }
-  // bounded wait for the copy (it takes microseconds; the limit is a safety net)
-  const bool arrived = mbar_wait_bounded(bar, 0, p.spin_limit);
-  if (__syncthreads_or(!arrived)) {
-    if (tid == 0) atomicOr(p.err, kErrTimeout);
-    mbar_wait_bounded(bar, 0, p.spin_limit);  // let the copy land before the CTA exits
-    return;
-  }
-  onesweep_tile_tma<K, BITS, THREADS, KPT, true>(p, tile, TILE, raw, kout, smem);
-}
-
-// ---------------------------------------------------------------------------
-// Cluster super-tiles: CL CTAs of one thread-block cluster handle CL
-// consecutive tiles (a super-tile). Each CTA ranks its tile, then stores its
-// digit counts into the leader CTA's shared memory (distributed shared memory).
-// The leader adds them up, publishes the super-tile's counts, runs ONE
-// decoupled look-back over earlier super-tiles (so the look-back chain moves
-// CL tiles per step), publishes the inclusive count and writes each CTA's
-// prefix (super-tile prefix + counts of the cluster's earlier tiles) into that
-// CTA's shared memory. Split-phase cluster barriers (arrive / wait) let every
-// CTA reorder its tile while the exchange is in flight.
-__device__ __forceinline__ void cluster_arrive() {
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void cluster_wait() {
-  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-template <typename K, typename V, int BITS, int THREADS, int KPT, int CL>
-struct ClusterShape {
-  using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
-  static constexpr size_t CCNT = S::HEADER_WORDS * 4 + S::STAGE_BYTES;  // [CL][R] counts
-  static constexpr size_t CPRE = CCNT + sizeof(uint32_t) * CL * S::R;   // [R] prefixes
-  static constexpr size_t SMEM = CPRE + sizeof(uint32_t) * S::R;
-};
-
-template <typename K, typename V, int BITS, int THREADS, int KPT, int CL, bool FULL>
-__device__ __forceinline__ void onesweep_cluster_tile(const PassParams& p, uint32_t super,
-                                                      unsigned rank, int64_t tile_base,
-                                                      int tile_n, const K* __restrict__ kin,
-                                                      K* __restrict__ kout, const V* vin, V* vout,
-                                                      unsigned char* smem) {
-  using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
-  using C = ClusterShape<K, V, BITS, THREADS, KPT, CL>;
-  constexpr int R = S::R, WARPS = S::WARPS, DPT = S::DPT;
-  constexpr bool HV = S::HV;
-  cg::cluster_group cluster = cg::this_cluster();
-  uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* s_adj = s_wcnt + WARPS * R;
-  uint32_t* s_misc = s_adj + R;
-  K* s_keys = reinterpret_cast<K*>(smem + S::HEADER_WORDS * 4);
-  V* s_vals = reinterpret_cast<V*>(smem + S::HEADER_WORDS * 4);
-  uint32_t* s_ccnt = reinterpret_cast<uint32_t*>(smem + C::CCNT);
-  uint32_t* s_cpre = reinterpret_cast<uint32_t*>(smem + C::CPRE);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wofs = warp * 32 * KPT + lane;
-  const bool leader = rank == 0;
-  const bool publish = (int64_t)super != p.stall_tile;
-
-  K key[KPT];
-  V val[HV ? KPT : 1];
-  tile_load<K, V, KPT, FULL>(kin, vin, tile_base, tile_n, wofs, key, val);
-  uint32_t rank2[(KPT + 1) / 2];
-  tile_rank<K, R, KPT, S::MASK_BUFS, FULL>(
-      key, p.shift, p.mask, tile_n, wofs, s_wcnt + warp * R,
-      reinterpret_cast<uint32_t*>(s_keys) + warp * S::MASK_BUFS * R, rank2);
-  __syncthreads();
-
-  // counts of this tile -> the leader's table; tile-local digit starts
-  uint32_t dcnt[DPT];
-  uint32_t tsum = 0;
-  const bool owner = tid < S::DTHREADS;
-  if (owner) {
-    tsum = tile_digit_counts<R, WARPS, DPT>(s_wcnt, tid, dcnt);
-    uint32_t* lc = cluster.map_shared_rank(s_ccnt, 0);
-#pragma unroll
-    for (int j = 0; j < DPT; ++j) lc[rank * R + tid * DPT + j] = dcnt[j];
-  }
-  uint32_t total;
-  uint32_t run = block_exclusive_scan<THREADS>(tsum, s_misc + 1, total);
-  uint32_t tstart[DPT];
-  if (owner) {
-#pragma unroll
-    for (int j = 0; j < DPT; ++j) {
-      const int d = tid * DPT + j;
-      tstart[j] = run;
-#pragma unroll
-      for (int w = 0; w < WARPS; ++w) s_wcnt[w * R + d] += run;
-      run += dcnt[j];
-    }
-  }
-  cluster_arrive();  // phase 2: this CTA's counts are in the leader's table
-  __syncthreads();
-  tile_reorder<K, V, KPT, FULL>(key, rank2, p.shift, p.mask, tile_n, wofs, s_wcnt + warp * R,
-                                s_keys);
-  cluster_wait();
-  if (leader && owner) {
-    uint32_t windows = 0;
-#pragma unroll
-    for (int j = 0; j < DPT; ++j) {
-      const int d = tid * DPT + j;
-      uint32_t sum = 0;
-#pragma unroll
-      for (int r = 0; r < CL; ++r) sum += s_ccnt[r * R + d];
-      uint32_t excl = 0;
-      if (super == 0) {
-        if (publish) st_relaxed(&p.status[d], kFlagInc | sum);
-      } else {
-        if (publish) st_relaxed(&p.status[(size_t)super * R + d], kFlagAgg | sum);
-        excl = lookback_exclusive<R, kLookbackWindow>(p.status, super, d, p.spin_limit, p.err,
-                                                      windows);
-        if (publish) st_relaxed(&p.status[(size_t)super * R + d], kFlagInc | (excl + sum));
-      }
-#pragma unroll
-      for (int r = 0; r < CL; ++r) {
-        cluster.map_shared_rank(s_cpre, r)[d] = excl;
-        excl += s_ccnt[r * R + d];
-      }
-    }
-  }
-  cluster_arrive();  // phase 3: every CTA's prefixes are written
-  cluster_wait();
-  if (owner) {
-#pragma unroll
-    for (int j = 0; j < DPT; ++j) {
-      const int d = tid * DPT + j;
-      s_adj[d] = p.base[d] + s_cpre[d] - tstart[j];
-    }
-  }
-  __syncthreads();
-  tile_scatter<K, V, THREADS, KPT, FULL>(s_keys, s_vals, s_adj, val, rank2,
-                                         RadixDigit{p}, tile_n, wofs, kout, vout,
-                                         (uint32_t)p.n, p.err);
-}
-
-template <typename K, typename V, int BITS, int THREADS, int KPT, int CL, int MINB>
-__global__ void __launch_bounds__(THREADS, MINB) k_onesweep_cl(PassParams p) {
-  using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
-  constexpr int R = S::R, WARPS = S::WARPS, TILE = S::TILE;
-  extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* s_misc = s_wcnt + WARPS * R + R;
-  uint32_t* s_stage = reinterpret_cast<uint32_t*>(smem + S::HEADER_WORDS * 4);
-  cg::cluster_group cluster = cg::this_cluster();
-  const unsigned rank = cluster.block_rank();
-  const int tid = threadIdx.x;
-  if (p.status_next && rank == 0)
-    for (int d = tid; d < R; d += THREADS)
-      p.status_next[(size_t)(blockIdx.x / CL) * R + d] = 0;
-  if (p.skip[p.pass]) return;  // the digit is constant: this round is the identity (all CTAs)
-
-  int src = 0;
-  for (int q = 0; q < p.pass; ++q) src ^= (p.skip[q] == 0);
-  for (int i = tid; i < WARPS * R; i += THREADS) s_wcnt[i] = 0;
-  for (int i = tid; i < WARPS * S::MASK_BUFS * R; i += THREADS) s_stage[i] = 0;
-  if (rank == 0 && tid == 0) s_misc[0] = atomicAdd(p.counter, 1u);  // super-tiles in launch order
-  // phase 1: every CTA of the cluster is running (so distributed shared memory
-  // may be used), shared memory is zeroed and the leader holds the id
-  cluster_arrive();
-  cluster_wait();
-  const uint32_t super = cluster.map_shared_rank(s_misc, 0)[0];
-  const int64_t tile_base = ((int64_t)super * CL + rank) * TILE;
-  if (p.prefetch_tiles && tid == 0) {
-    const int64_t pf = tile_base + p.prefetch_tiles * TILE;
-    const int64_t cnt = min((int64_t)TILE, p.n - pf);
-    prefetch_tile(static_cast<const K*>(src ? p.keys[1] : p.keys[0]), pf, cnt);
-    if constexpr (HasVal<V>::value)
-      prefetch_tile(static_cast<const V*>(src ? p.vals[1] : p.vals[0]), pf, cnt);
-  }
-  const int64_t left = p.n - tile_base;
-  const int tile_n = (int)(left < 0 ? 0 : (left > TILE ? TILE : left));
-  const K* kin = static_cast<const K*>(src ? p.keys[1] : p.keys[0]);
-  K* kout = static_cast<K*>(src ? p.keys[0] : p.keys[1]);
-  const V* vin = static_cast<const V*>(src ? p.vals[1] : p.vals[0]);
-  V* vout = static_cast<V*>(src ? p.vals[0] : p.vals[1]);
-  if (tile_n == TILE)
-    onesweep_cluster_tile<K, V, BITS, THREADS, KPT, CL, true>(p, super, rank, tile_base, tile_n,
-                                                              kin, kout, vin, vout, smem);
-  else
-    onesweep_cluster_tile<K, V, BITS, THREADS, KPT, CL, false>(p, super, rank, tile_base, tile_n,
-                                                               kin, kout, vin, vout, smem);
-}
-
-// ---------------------------------------------------------------------------
 // k_copy_back: after an odd number of executed rounds the sorted keys sit in
 // the alternate buffer; copy them (and payloads) home. Otherwise a no-op.
 template <typename K, typename V>
@@ -1376,22 +994,20 @@ __global__ void k_copy_back(const uint32_t* __restrict__ skip, int passes, K* ke
 }
 
 // ---------------------------------------------------------------------------
-// Host launcher for one whole sort with a given kernel shape. CL = 1: one tile
-// per CTA with a per-tile look-back (k_onesweep); CL > 1: CL-CTA cluster
-// super-tiles (k_onesweep_cl).
-template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB, int CL, bool TMA,
-          bool EARLY>
+// Host launcher for one whole sort with a given kernel shape: one tile per CTA
+// with a per-tile look-back.
+template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB>
 cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
   using L = DigitLayout<K, BITS>;
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
   constexpr int R = L::R, P = L::PASSES;
+  constexpr bool HV = HasVal<V>::value;
   const int64_t tiles = (a.n + S::TILE - 1) / S::TILE;
-  const int64_t rows = (tiles + CL - 1) / CL;  // look-back rows (tiles or super-tiles)
   cudaError_t e;
   // hist and counters are zeroed; status[0] too (later passes clear their own)
   if ((e = cudaMemsetAsync(a.hist, 0, sizeof(uint32_t) * P * R, st))) return e;
   if ((e = cudaMemsetAsync(a.counters, 0, sizeof(uint32_t) * P, st))) return e;
-  if ((e = cudaMemsetAsync(a.status[0], 0, sizeof(uint32_t) * R * rows, st))) return e;
+  if ((e = cudaMemsetAsync(a.status[0], 0, sizeof(uint32_t) * R * tiles, st))) return e;
 
   // 32 counter columns for 32-bit keys (4 passes: 128 KiB), 16 for 64-bit
   // keys (8 passes: 128 KiB); one 1024-thread CTA per SM.
@@ -1420,82 +1036,46 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
   pp.err = a.err;
   pp.spin_limit = a.spin_limit;
   pp.prefetch_tiles = a.prefetch_tiles;
-  if constexpr (CL == 1) {
-    size_t smem = EARLY ? EarlyShape<K, V, BITS, THREADS, KPT>::SMEM : S::SMEM;
-    auto kern = k_onesweep<K, V, BITS, THREADS, KPT, MINB, EARLY>;
-    if constexpr (TMA) {
-      static_assert(!HasVal<V>::value, "the TMA round is keys-only");
-      kern = k_onesweep_tma<K, BITS, THREADS, KPT, MINB>;
-      smem = TmaShape<K, BITS, THREADS, KPT>::SMEM;
-    }
-    if (smem > 48 * 1024) {
-      if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-        return e;
-    }
-    // keys only: pass 0 drops the stable rank (k_onesweep_first), unless it is traced
-    using FC = FirstCfg<K, THREADS, KPT, MINB>;
-    constexpr size_t fsmem = FirstShape<K, BITS, FC::T, FC::KP>::SMEM;
-    if constexpr (!HasVal<V>::value && fsmem > 48 * 1024) {
-      if ((e = cudaFuncSetAttribute(k_onesweep_first<K, BITS, FC::T, FC::KP, MINB>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem)))
-        return e;
-    }
-    for (int q = 0; q < P; ++q) {
-      pp.pass = q;
-      pp.shift = q * BITS;
-      pp.mask = (1u << L::width(q)) - 1;
-      pp.base = a.base + (size_t)q * R;
-      pp.status = a.status[q & 1];
-      pp.status_next = (q + 1 < P) ? a.status[(q + 1) & 1] : nullptr;
-      pp.counter = a.counters + q;
-      pp.stall_tile = (q == 0) ? a.stall_tile : -1;
-      pp.trace = (q == a.trace_pass) ? a.trace : nullptr;
-      bool launched = false;
-      if constexpr (!HasVal<V>::value) {
-        if (q == 0 && !pp.trace) {
-          timer_begin(a.timer, "k_onesweep_first", st);
-          k_onesweep_first<K, BITS, FC::T, FC::KP, MINB><<<(unsigned)tiles, FC::T, fsmem, st>>>(pp);
-          launched = true;
-        }
-      }
-      if (!launched) {
-        timer_begin(a.timer, "k_onesweep", st);
-        kern<<<(unsigned)tiles, THREADS, smem, st>>>(pp);
-      }
-      timer_end(a.timer, st);
-    }
-  } else {
-    using C = ClusterShape<K, V, BITS, THREADS, KPT, CL>;
-    auto kern = k_onesweep_cl<K, V, BITS, THREADS, KPT, CL, MINB>;
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)C::SMEM)))
+  pp.check_mode = a.check_mode;
+  // keys only: the ordered round; with payloads: early counts, peer masks
+  constexpr size_t smem = HV ? EarlyShape<K, V, BITS, THREADS, KPT>::SMEM
+                             : OrderedShape<K, BITS, THREADS, KPT>::SMEM;
+  auto kern = k_onesweep<K, V, BITS, THREADS, KPT, MINB>;
+  if (smem > 48 * 1024) {
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
       return e;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(rows * CL));
-    cfg.blockDim = dim3(THREADS);
-    cfg.dynamicSmemBytes = C::SMEM;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    for (int q = 0; q < P; ++q) {
-      pp.pass = q;
-      pp.shift = q * BITS;
-      pp.mask = (1u << L::width(q)) - 1;
-      pp.base = a.base + (size_t)q * R;
-      pp.status = a.status[q & 1];
-      pp.status_next = (q + 1 < P) ? a.status[(q + 1) & 1] : nullptr;
-      pp.counter = a.counters + q;
-      pp.stall_tile = (q == 0) ? a.stall_tile : -1;
-      pp.trace = nullptr;
-      timer_begin(a.timer, "k_onesweep", st);
-      if ((e = cudaLaunchKernelEx(&cfg, kern, pp))) return e;
-      timer_end(a.timer, st);
+  }
+  // keys only: pass 0 is the order-free round (k_onesweep_first), unless it is traced
+  using FC = FirstCfg<K, THREADS, KPT, MINB>;
+  constexpr size_t fsmem = FirstShape<K, BITS, FC::T, FC::KP>::SMEM;
+  if constexpr (!HV && fsmem > 48 * 1024) {
+    if ((e = cudaFuncSetAttribute(k_onesweep_first<K, BITS, FC::T, FC::KP, MINB>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem)))
+      return e;
+  }
+  for (int q = 0; q < P; ++q) {
+    pp.pass = q;
+    pp.shift = q * BITS;
+    pp.mask = (1u << L::width(q)) - 1;
+    pp.base = a.base + (size_t)q * R;
+    pp.status = a.status[q & 1];
+    pp.status_next = (q + 1 < P) ? a.status[(q + 1) & 1] : nullptr;
+    pp.counter = a.counters + q;
+    pp.stall_tile = (q == 0) ? a.stall_tile : -1;
+    pp.trace = (q == a.trace_pass) ? a.trace : nullptr;
+    bool launched = false;
+    if constexpr (!HV) {
+      if (q == 0 && !pp.trace) {
+        timer_begin(a.timer, "k_onesweep_first", st);
+        k_onesweep_first<K, BITS, FC::T, FC::KP, MINB><<<(unsigned)tiles, FC::T, fsmem, st>>>(pp);
+        launched = true;
+      }
     }
+    if (!launched) {
+      timer_begin(a.timer, "k_onesweep", st);
+      kern<<<(unsigned)tiles, THREADS, smem, st>>>(pp);
+    }
+    timer_end(a.timer, st);
   }
   int cblocks = (int)std::min<int64_t>((a.n + 255) / 256, (int64_t)a.num_sms * 8);
   timer_begin(a.timer, "k_copy_back", st);
@@ -1508,9 +1088,7 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
 }
 
 // MINB = CTAs that must fit on one SM (caps registers at 65536 / (THREADS * MINB)).
-// CL = CTAs per cluster super-tile (1: plain per-tile look-back).
-template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB, int CL = 1,
-          bool TMA = false, bool EARLY = false>
+template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB>
 constexpr LsdEntry lsd_entry() {
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
   return LsdEntry{(int)(8 * sizeof(K)),
@@ -1518,13 +1096,12 @@ constexpr LsdEntry lsd_entry() {
                   BITS,
                   THREADS,
                   KPT,
-                  (int64_t)S::TILE * CL,  // one look-back row per tile or super-tile
+                  (int64_t)S::TILE,  // one look-back row per tile
                   S::R,
                   DigitLayout<K, BITS>::PASSES,
                   (size_t)S::R,
                   2,
-                  &lsd_launch<K, V, BITS, THREADS, KPT, MINB, CL, TMA, EARLY>,
-                  CL};
+                  &lsd_launch<K, V, BITS, THREADS, KPT, MINB>};
 }
 
 }  // namespace isort

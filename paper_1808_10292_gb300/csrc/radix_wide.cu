@@ -558,8 +558,7 @@ constexpr LsdEntry wide_entry() {
                   (KB + BITS - 1) / BITS,
                   (size_t)1 << BITS,       // the count matrix: one row per block
                   1,                       // in one buffer
-                  &wide_launch<K, V, BITS>,
-                  1};
+                  &wide_launch<K, V, BITS>};
 }
 
 #define ISORT_WIDE_TABLES(B)                                                             \

@@ -310,6 +310,7 @@ cudaError_t gvr_launch(const GvrArgs& a, cudaStream_t st) {
   pp.stall_tile = -1;
   pp.trace = nullptr;
   pp.prefetch_tiles = (int64_t)a.num_sms * 4;
+  pp.check_mode = kCheckNormal;
   // keys only: the order-free round, in its own CTA shape (same tile)
   using FC = FirstCfg<K, THREADS, KPT, MINB>;
   constexpr bool HV = HasVal<V>::value;

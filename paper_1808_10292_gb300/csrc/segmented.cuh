@@ -19,8 +19,8 @@
 //   k_seg_onesweep  one count-sort round over the tiles of ALL radix ranges; the
 //                   look-back never crosses a range (the first tile of a range
 //                   publishes its counts as inclusive). Keys only: pass 0 is the
-//                   order-free round (onesweep_tile_first) and later passes relax
-//                   the rank in warps with few runs of equal low bits.
+//                   order-free round (onesweep_tile_first), later passes the
+//                   ordered round (onesweep_tile_ordered).
 // All passes run (4 for 32-bit keys, 8 for 64-bit): an even number, so the
 // result ends in the caller's arrays. Offsets are checked on the device; a bad
 // range is skipped and flagged in the error word.
@@ -275,6 +275,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp
   uint32_t* s_misc = FIRST ? s_wcnt + 2 * R : s_wcnt + WARPS * R + R;
   uint32_t* s_stage = reinterpret_cast<uint32_t*>(smem + E::MASKS);  // the peer masks
   const int tid = threadIdx.x;
+  // keys only, passes after the first: the ordered round (no peer masks)
+  constexpr bool ORDERED = !FIRST && !HasVal<V>::value;
   if (p.status_next)
     for (int d = tid; d < R; d += THREADS) p.status_next[(size_t)blockIdx.x * R + d] = 0;
   if (tid == 0) s_misc[0] = atomicAdd(p.counter, 1u);
@@ -282,7 +284,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp
     zero_words<THREADS>(s_wcnt, R);
   } else {
     for (int i = tid; i < WARPS * R; i += THREADS) s_wcnt[i] = 0;
-    for (int i = tid; i < WARPS * S::MASK_BUFS * R; i += THREADS) s_stage[i] = 0;
+    if constexpr (!ORDERED)
+      for (int i = tid; i < WARPS * S::MASK_BUFS * R; i += THREADS) s_stage[i] = 0;
   }
   __syncthreads();
   const uint32_t tile = s_misc[0];
@@ -310,17 +313,23 @@ __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp
                                                         kout, base, (uint32_t)len, smem, dig);
     return;
   }
-  // keys only, 32-bit keys (for 64-bit keys the extra registers of the test
-  // spill in every round, and only rounds 1 and 2 have shared low bits)
-  constexpr bool RELAX = !HasVal<V>::value && sizeof(K) == 4;
-  if (tile_n == TILE)
-    onesweep_tile_early<K, V, BITS, THREADS, KPT, true, RadixDigit, RELAX>(
-        p, tile, lt == 0, tile_base, tile_n, kin, kout, vin, vout, base, (uint32_t)len, smem,
-        dig);
-  else
-    onesweep_tile_early<K, V, BITS, THREADS, KPT, false, RadixDigit, RELAX>(
-        p, tile, lt == 0, tile_base, tile_n, kin, kout, vin, vout, base, (uint32_t)len, smem,
-        dig);
+  if constexpr (ORDERED) {
+    if (tile_n == TILE)
+      onesweep_tile_ordered<K, BITS, THREADS, KPT, true>(p, tile, lt == 0, tile_base, tile_n,
+                                                         kin, kout, base, (uint32_t)len, smem);
+    else
+      onesweep_tile_ordered<K, BITS, THREADS, KPT, false>(p, tile, lt == 0, tile_base, tile_n,
+                                                          kin, kout, base, (uint32_t)len, smem);
+  } else {
+    if (tile_n == TILE)
+      onesweep_tile_early<K, V, BITS, THREADS, KPT, true>(p, tile, lt == 0, tile_base, tile_n,
+                                                          kin, kout, vin, vout, base,
+                                                          (uint32_t)len, smem, dig);
+    else
+      onesweep_tile_early<K, V, BITS, THREADS, KPT, false>(p, tile, lt == 0, tile_base, tile_n,
+                                                           kin, kout, vin, vout, base,
+                                                           (uint32_t)len, smem, dig);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -390,7 +399,8 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
   timer_end(a.timer, st);
 
   auto kern = k_seg_onesweep<K, V, 8, THREADS, KPT, MINB>;
-  constexpr size_t SEG_SMEM = EarlyShape<K, V, 8, THREADS, KPT>::SMEM;
+  constexpr size_t SEG_SMEM = HasVal<V>::value ? EarlyShape<K, V, 8, THREADS, KPT>::SMEM
+                                               : OrderedShape<K, 8, THREADS, KPT>::SMEM;
   if (SEG_SMEM > 48 * 1024) {
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)SEG_SMEM)))
@@ -426,6 +436,7 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
   pp.stall_tile = -1;
   pp.trace = nullptr;
   pp.prefetch_tiles = 0;
+  pp.check_mode = a.check_mode;
   for (int q = 0; q < P; ++q) {
     pp.pass = q;
     pp.shift = q * 8;

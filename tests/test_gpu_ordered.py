@@ -1,0 +1,82 @@
+"""The ordered keys-only rounds: ranks from the order in which shared atomics
+serve the lanes of a warp, checked per tile, with a stable re-rank for tiles
+that fail the check. These tests drive the check and the fallback through the
+library's test hook (ISORT_DEBUG_CHECK_MODE): mode 1 sends every tile through
+the fallback, mode 2 makes the fast ranks deliberately unstable (odd lanes
+first), which the check must catch. Either way the result must equal the
+oracle's, bit for bit."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import inputs
+import oracle
+import paper_1808_10292_gb300 as isort
+from paper_1808_10292_gb300 import _lib
+
+pytestmark = pytest.mark.gpu
+
+MODES = [0, 1, 2]
+
+
+@pytest.fixture
+def check_mode():
+    def set_mode(m):
+        isort.debug_set(_lib.DEBUG_CHECK_MODE, m)
+    yield set_mode
+    isort.debug_set(_lib.DEBUG_CHECK_MODE, 0)
+
+
+def _oracle(k):
+    return oracle.radix_sort(k, radix_bits=8)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("key_bits", [32, 64])
+@pytest.mark.parametrize("dist", inputs.DISTS)
+def test_plain_sort_every_check_mode(check_mode, mode, key_bits, dist):
+    n = 3 * 8192 + 4099  # several tiles and a ragged one
+    k = inputs.keys(n, key_bits, dist, seed=11)
+    expect = _oracle(k)
+    check_mode(mode)
+    for variant in range(len(isort.tune_variants(key_bits, 0, 8))):
+        isort.tune_set(key_bits, 0, 8, variant)
+        d = torch.from_numpy(k).cuda()
+        isort.sort_keys(d, 8)
+        assert isort.stream_status() == _lib.OK
+        assert np.array_equal(d.cpu().numpy(), expect), (mode, variant)
+    isort.tune_set(key_bits, 0, 8, -1)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_segmented_every_check_mode(check_mode, mode):
+    L = inputs.segment_lengths(300, seed=12, max_log2=15)
+    off = inputs.segment_offsets(L)
+    k = inputs.keys(int(off[-1]), 32, "and4", seed=13)
+    check_mode(mode)
+    d = torch.from_numpy(k).cuda()
+    isort.sort_segmented(d, torch.from_numpy(off).cuda())
+    assert isort.stream_status() == _lib.OK
+    assert np.array_equal(d.cpu().numpy(), oracle.segmented_sort(k, off))
+
+
+def test_perturbed_ranks_fail_the_check_and_are_repaired(check_mode):
+    """With odd lanes first, a round whose rows hold equal digits with different
+    low bits is unstable; the result is still exact, so the check caught every
+    such tile (a 2^20-key uniform sort has many)."""
+    k = inputs.keys(1 << 20, 32, "uniform", seed=14)
+    check_mode(2)
+    d = torch.from_numpy(k).cuda()
+    isort.sort_keys(d, 8)
+    assert isort.stream_status() == _lib.OK
+    assert np.array_equal(d.cpu().numpy(), np.sort(k))
+
+
+def test_check_mode_argument():
+    lib = _lib.load()
+    assert lib.isort_debug_set(_lib.DEBUG_CHECK_MODE, 3) == _lib.EINVAL
+    assert lib.isort_debug_set(_lib.DEBUG_CHECK_MODE, -1) == _lib.EINVAL
+    assert lib.isort_debug_set(_lib.DEBUG_CHECK_MODE, 0) == _lib.OK

@@ -37,7 +37,7 @@ def gpu_sort(keys_np, vals_np=None, radix_bits=8):  # noqa: D401
 
 
 def edge_sizes(tile):
-    # tile edges, and super-tile edges of the cluster variants (up to 8 tiles)
+    # tile edges, and several look-back rows
     return sorted({0, 1, 2, 3, 31, 32, 33, 255, 257, tile - 1, tile, tile + 1, 2 * tile + 5,
                    5 * tile - 3, 8 * tile - 1, 8 * tile + 1, 17 * tile + 3})
 
@@ -147,10 +147,10 @@ def test_concurrent_streams_give_the_same_results():
 def test_bounded_wait_reports_timeout_and_context_survives(variant):
     """A tile that never publishes makes its successors' bounded waits give up:
     the error is latched and reported, no GPU hang, and the next sort is fine."""
-    n = 64 * 4096  # several look-back rows even for 8-tile cluster super-tiles
+    n = 64 * 4096  # many look-back rows
     k = to_dev(inputs.keys(n, 32, "uniform", seed=6))
     nv = len(isort.tune_variants(32, 0, 8))
-    isort.tune_set(32, 0, 8, variant % nv)  # the plain variant and a cluster variant
+    isort.tune_set(32, 0, 8, variant % nv)  # the default and the last variant
     isort.debug_set(_lib.DEBUG_SPIN_LIMIT, 2000)
     isort.debug_set(_lib.DEBUG_STALL_TILE, 1)
     try:
@@ -343,7 +343,7 @@ def kernels_of_one_sort(run):
 @pytest.mark.parametrize("key_bits", [32, 64])
 def test_keys_only_first_round_is_order_free_and_exact(key_bits):
     """Keys only: pass 0 runs the order-free first round (k_onesweep_first),
-    the other passes the stable round; pairs keep the stable round in pass 0.
+    the other passes the ordered round; pairs keep the stable round in pass 0.
     Either way the result is the oracle's, bit for bit."""
     n = 3 * 8192 * 5 + 77  # many tiles of every variant, a ragged tail
     k = inputs.keys(n, key_bits, "uniform", seed=31)
@@ -360,8 +360,7 @@ def test_keys_only_first_round_is_order_free_and_exact(key_bits):
         passes = key_bits // 8
         rounds = names.count("k_onesweep_first") + names.count("k_onesweep")
         assert rounds == passes, names
-        cluster = names.count("k_onesweep_first") == 0
-        assert cluster or names.index("k_onesweep_first") < names.index("k_onesweep"), names
+        assert names.index("k_onesweep_first") < names.index("k_onesweep"), names
     v = inputs.iota(n)
     t, tv = to_dev(k), to_dev(v)
     names = kernels_of_one_sort(lambda: isort.sort_pairs(t, tv, 8))
@@ -382,25 +381,48 @@ def test_keys_only_constant_low_digit(key_bits):
         assert np.array_equal(gpu_sort(k), oracle.radix_sort(k, radix_bits=8)), shift
 
 
-@pytest.mark.parametrize("low_values", [1, 3, 40])
-def test_keys_only_relaxed_warps_every_variant(low_values):
-    """Keys only, 32-bit: a round after the first lets a warp whose keys all
-    share the bits below the digit place equal digits in any order. Keys whose
-    low 8 (then 16) bits take few values make such warps common in rounds 1
-    and 2 at small n, next to warps that straddle a change of the low bits and
-    must keep order, and partial warps in the ragged last tile."""
-    n = 5 * 8192 + 1234
-    hi = inputs.keys(n, 32, "uniform", seed=41) & np.uint32(0xFFFF0000)
-    mid = (inputs.keys(n, 32, "uniform", seed=42) % np.uint32(low_values)) << np.uint32(8)
-    lo = inputs.keys(n, 32, "uniform", seed=43) % np.uint32(low_values)
+def crafted_runs(n, low_values, seed):
+    """Keys whose low 8 (then 16) bits take few values, so that rounds 1 and 2
+    see long runs of equal low bits next to warps that straddle a change of
+    them, plus bursts of up to 31 consecutive distinct low bytes (several run
+    starts in one 32-key row) and partial warps in the ragged last tile."""
+    hi = inputs.keys(n, 32, "uniform", seed=seed) & np.uint32(0xFFFF0000)
+    mid = (inputs.keys(n, 32, "uniform", seed=seed + 1) % np.uint32(low_values)) << np.uint32(8)
+    lo = inputs.keys(n, 32, "uniform", seed=seed + 2) % np.uint32(low_values)
     k = hi | mid | lo
+    for start in range(700, n - 64, 1500):
+        burst = 1 + (start // 1500) % 31
+        k[start:start + burst] = (k[start:start + burst] & np.uint32(0xFFFFFF00)) | \
+            np.arange(burst, dtype=np.uint32)
+    return k
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+@pytest.mark.parametrize("low_values", [1, 3, 40])
+def test_keys_only_ordered_rounds_crafted_runs(low_values, mode):
+    """Keys only, rounds after the first: the ordered round's check compares
+    every staged key with its successor in the key bits below the digit. Runs
+    of equal low bits, bursts of distinct ones and ragged tiles, with the fast
+    ranks as the hardware gives them (mode 0) and deliberately unstable (mode
+    2, the check must repair every failing tile); every variant and the
+    segmented form."""
+    n = 5 * 8192 + 1234
+    k = crafted_runs(n, low_values, 41)
     want = oracle.radix_sort(k, radix_bits=8)
-    for v in range(len(isort.tune_variants(32, 0, 8))):
-        isort.tune_set(32, 0, 8, v)
-        try:
-            assert np.array_equal(gpu_sort(k), want), v
-        finally:
-            isort.tune_set(32, 0, 8, -1)
+    isort.debug_set(_lib.DEBUG_CHECK_MODE, mode)
+    try:
+        for v in range(len(isort.tune_variants(32, 0, 8))):
+            isort.tune_set(32, 0, 8, v)
+            try:
+                assert np.array_equal(gpu_sort(k), want), v
+            finally:
+                isort.tune_set(32, 0, 8, -1)
+        self_check_segmented(k, n)
+    finally:
+        isort.debug_set(_lib.DEBUG_CHECK_MODE, 0)
+
+
+def self_check_segmented(k, n):
     # the segmented form on the same keys: ranges of mixed lengths
     off = np.array([0, 7, 4000, 4001, 20000, n], dtype=np.int64)
     t = to_dev(k)
