@@ -217,8 +217,8 @@ int64_t seg_btn_max(const SegConfig& c) {
 }
 
 struct SegLayout {
-  size_t err, cnt, lists, slot_first, tile_slot, seg_hist, seg_base, status0, status1, alt_k,
-      alt_v, total;
+  size_t err, cnt, lists, slot_first, tile_slot, seg_hist, seg_base, seg_skip, status0, status1,
+      alt_k, alt_v, total;
   int64_t max_tiles;
 };
 
@@ -238,6 +238,7 @@ SegLayout seg_layout(const SegConfig& c, int64_t nseg, int64_t total, int64_t bt
   L.tile_slot = off;   off = align256(off + sizeof(int32_t) * (size_t)L.max_tiles);
   L.seg_hist = off;    off = align256(off + per_slot * (size_t)nseg);
   L.seg_base = off;    off = align256(off + per_slot * (size_t)nseg);
+  L.seg_skip = off;    off = align256(off + sizeof(uint32_t) * (size_t)c.passes * nseg);
   L.status0 = off;     off = align256(off + sizeof(uint32_t) * c.radix * (size_t)L.max_tiles);
   L.status1 = off;     off = align256(off + sizeof(uint32_t) * c.radix * (size_t)L.max_tiles);
   L.alt_k = off;       off = align256(off + (size_t)total * (c.key_bits / 8));
@@ -351,6 +352,7 @@ SegArgs seg_args(const SegConfig& c, const SegLayout& L, char* b, void* keys, vo
   a.tile_slot = reinterpret_cast<int32_t*>(b + L.tile_slot);
   a.seg_hist = reinterpret_cast<uint32_t*>(b + L.seg_hist);
   a.seg_base = reinterpret_cast<uint32_t*>(b + L.seg_base);
+  a.seg_skip = reinterpret_cast<uint32_t*>(b + L.seg_skip);
   a.status[0] = reinterpret_cast<uint32_t*>(b + L.status0);
   a.status[1] = reinterpret_cast<uint32_t*>(b + L.status1);
   a.err = reinterpret_cast<uint32_t*>(b + L.err);

@@ -93,6 +93,7 @@ struct SegArgs {
   int32_t* tile_slot;    // [max_tiles] radix range (slot) of each tile
   uint32_t* seg_hist;    // [nseg][P][R]
   uint32_t* seg_base;    // [nseg][P][R]
+  uint32_t* seg_skip;    // [nseg][P] trivial passes of each radix range
   uint32_t* status[2];   // [max_tiles][R]
   uint32_t* err;
   uint32_t spin_limit;

@@ -21,9 +21,12 @@
 //                   publishes its counts as inclusive). Keys only: pass 0 is the
 //                   order-free round (onesweep_tile_first), later passes the
 //                   ordered round (onesweep_tile_ordered).
-// All passes run (4 for 32-bit keys, 8 for 64-bit): an even number, so the
-// result ends in the caller's arrays. Offsets are checked on the device; a bad
-// range is skipped and flagged in the error word.
+//   k_seg_copy_back the ranges that executed an odd number of passes end in the
+//                   alternate buffers: copied home.
+// A pass whose digit is constant on a range is skipped for that range (its
+// tiles return at once), so each range keeps its own buffer parity. Offsets
+// are checked on the device; a bad range is skipped and flagged in the error
+// word.
 #pragma once
 #include "btn.cuh"
 #include "onesweep.cuh"
@@ -230,11 +233,14 @@ __global__ void __launch_bounds__(1024) k_seg_hist(const K* __restrict__ keys,
   if (cur >= 0) flush(cur);
 }
 
-// Per radix range: exclusive digit bases (relative to the range) of every pass.
+// Per radix range: exclusive digit bases (relative to the range) of every
+// pass, and the range's trivial passes (one digit holds all its keys: the pass
+// is the identity on that range and is skipped for it).
 template <int BITS, int PASSES>
 __global__ void __launch_bounds__(1 << BITS) k_seg_scan(const uint32_t* __restrict__ cnt,
                                                        const uint32_t* __restrict__ seg_hist,
-                                                       uint32_t* __restrict__ seg_base) {
+                                                       uint32_t* __restrict__ seg_base,
+                                                       uint32_t* __restrict__ seg_skip) {
   constexpr int R = 1 << BITS;
   __shared__ uint32_t s_warp[R / 32];
   const uint32_t slot = blockIdx.x;
@@ -242,9 +248,46 @@ __global__ void __launch_bounds__(1 << BITS) k_seg_scan(const uint32_t* __restri
   for (int p = 0; p < PASSES; ++p) {
     const size_t row = ((size_t)slot * PASSES + p) * R;
     uint32_t tot;
-    seg_base[row + threadIdx.x] =
-        block_exclusive_scan<R>(seg_hist[row + threadIdx.x], s_warp, tot);
-    __syncthreads();
+    const uint32_t c = seg_hist[row + threadIdx.x];
+    seg_base[row + threadIdx.x] = block_exclusive_scan<R>(c, s_warp, tot);
+    const int trivial = __syncthreads_or(c == tot);
+    if (threadIdx.x == 0) seg_skip[(size_t)slot * PASSES + p] = trivial;
+  }
+}
+
+// Input buffer of a radix range in pass `pass`: the parity of the passes
+// executed for it before (0: the caller's arrays).
+__device__ __forceinline__ int seg_src(const uint32_t* skip_row, int pass) {
+  int src = 0;
+  for (int q = 0; q < pass; ++q) src ^= (skip_row[q] == 0);
+  return src;
+}
+
+// After the last pass: the ranges that executed an odd number of passes end in
+// the alternate buffers; copy them home (one tile per CTA iteration).
+template <typename K, typename V, int TILE>
+__global__ void __launch_bounds__(256) k_seg_copy_back(K* keys, const K* alt, V* vals,
+                                                        const V* valt,
+                                                        const int64_t* __restrict__ off,
+                                                        int64_t nseg, int64_t total,
+                                                        const int32_t* __restrict__ list,
+                                                        const uint32_t* __restrict__ cnt,
+                                                        const uint32_t* __restrict__ slot_first,
+                                                        const int32_t* __restrict__ tile_slot,
+                                                        const uint32_t* __restrict__ seg_skip,
+                                                        int passes) {
+  const int64_t T = cnt[kCntTiles];
+  for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
+    const int32_t slot = tile_slot[t];
+    if (!seg_src(seg_skip + (size_t)slot * passes, passes)) continue;
+    int64_t start, len;
+    seg_range(off, list[(size_t)kSegRadix * nseg + slot], total, start, len);
+    const int64_t lo = start + ((int64_t)t - slot_first[slot]) * TILE;
+    const int64_t hi = min(start + len, lo + TILE);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += 256) {
+      keys[i] = alt[i];
+      if constexpr (HasVal<V>::value) vals[i] = valt[i];
+    }
   }
 }
 
@@ -259,6 +302,7 @@ struct SegPassParams {
   const uint32_t* slot_first;
   const int32_t* tile_slot;
   const uint32_t* seg_base;
+  const uint32_t* seg_skip;  // [slots][passes] 1 = the pass is the identity on the range
   int passes;
 };
 
@@ -291,12 +335,14 @@ __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp
   const uint32_t tile = s_misc[0];
   if (tile >= sp.cnt[kCntTiles]) return;  // more CTAs than tiles: nothing left
   const int32_t slot = sp.tile_slot[tile];
+  const uint32_t* skip_row = sp.seg_skip + (size_t)slot * sp.passes;
+  if (skip_row[p.pass]) return;  // the digit is constant on this range
   int64_t start, len;
   seg_range(sp.off, sp.list[(size_t)kSegRadix * sp.nseg + slot], sp.total, start, len);
   const int64_t lt = (int64_t)tile - sp.slot_first[slot];  // tile index within the range
   const int64_t tile_base = start + lt * TILE;
   const int tile_n = (int)min((int64_t)TILE, len - lt * TILE);
-  const int src = p.pass & 1;  // every round runs
+  const int src = seg_src(skip_row, p.pass);
   const K* kin = static_cast<const K*>(src ? p.keys[1] : p.keys[0]);
   K* kout = static_cast<K*>(src ? p.keys[0] : p.keys[1]) + start;
   const V* vin = static_cast<const V*>(src ? p.vals[1] : p.vals[0]);
@@ -395,7 +441,7 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
   }
   timer_end(a.timer, st);
   timer_begin(a.timer, "k_seg_scan", st);
-  k_seg_scan<8, P><<<(unsigned)nslots, R, 0, st>>>(a.cnt, a.seg_hist, a.seg_base);
+  k_seg_scan<8, P><<<(unsigned)nslots, R, 0, st>>>(a.cnt, a.seg_hist, a.seg_base, a.seg_skip);
   timer_end(a.timer, st);
 
   auto kern = k_seg_onesweep<K, V, 8, THREADS, KPT, MINB>;
@@ -422,6 +468,7 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
   sp.slot_first = a.slot_first;
   sp.tile_slot = a.tile_slot;
   sp.seg_base = a.seg_base;
+  sp.seg_skip = a.seg_skip;
   sp.passes = P;
   PassParams& pp = sp.p;
   pp.keys[0] = a.keys;
@@ -457,6 +504,11 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
     kern<<<(unsigned)a.max_tiles, THREADS, SEG_SMEM, st>>>(sp);
     timer_end(a.timer, st);
   }
+  timer_begin(a.timer, "k_seg_copy_back", st);
+  k_seg_copy_back<K, V, TILE><<<a.num_sms * 8, 256, 0, st>>>(
+      keys, static_cast<const K*>(a.alt_keys), vals, static_cast<const V*>(a.alt_vals),
+      a.offsets, a.nseg, a.total, a.lists, a.cnt, a.slot_first, a.tile_slot, a.seg_skip, P);
+  timer_end(a.timer, st);
   return cudaGetLastError();
 }
 

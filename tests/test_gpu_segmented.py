@@ -90,6 +90,37 @@ def test_log_uniform_lengths(key_bits):
     assert np.array_equal(gv, ov)
 
 
+@pytest.mark.parametrize("key_bits,val_bits", [(32, 0), (32, 32), (64, 0), (64, 64)])
+def test_per_range_pass_skip(key_bits, val_bits):
+    """Ranges whose digit is constant in some passes skip those passes for
+    themselves only, so ranges end after odd and even numbers of executed
+    passes (the odd ones are copied home): low-entropy ranges (keys below
+    2^16, or a constant middle byte), all-equal ranges, a range constant in
+    every pass but one, uniform ranges, side by side in one batch."""
+    rng_len = [20000, 9000, 30000, 12000, 50000, 8193, 17000, 40000]
+    off = np.concatenate([[0], np.cumsum(rng_len)]).astype(np.int64)
+    n = int(off[-1])
+    k = inputs.keys(n, key_bits, "uniform", seed=21)
+    one = np.array(1, dtype=k.dtype)
+    seg = [k[off[i]:off[i + 1]] for i in range(len(rng_len))]
+    seg[0] &= np.array(0xFFFF, dtype=k.dtype)              # upper digits constant (zero)
+    seg[1][:] = seg[1][0]                                   # every pass trivial
+    seg[2] = (seg[2] & ~np.array(0xFF00, dtype=k.dtype)) | np.array(0x3400, dtype=k.dtype)
+    seg[3] = (seg[3] & np.array(0xFF, dtype=k.dtype)) | np.array(0x5A00, dtype=k.dtype)
+    seg[5] = (seg[5] >> np.array(8, dtype=k.dtype)) << np.array(8, dtype=k.dtype)  # digit 0 = 0
+    seg[6] = seg[6] & (one << np.array(8 * (key_bits // 8 - 1), dtype=k.dtype)) | \
+        np.array(7, dtype=k.dtype)                          # one varying bit, in the top digit
+    k = np.concatenate(seg)
+    v = inputs.iota(n, val_bits) if val_bits else None
+    status, gk, gv = run_segmented(k, off, v)
+    assert status == _lib.OK
+    want = oracle.segmented_sort(k, off, v)
+    if val_bits:
+        assert np.array_equal(gk, want[0]) and np.array_equal(gv, want[1])
+    else:
+        assert np.array_equal(gk, want)
+
+
 def test_btn_threshold_tuning_keeps_results():
     L = inputs.segment_lengths(800, seed=7, max_log2=13)
     off = inputs.segment_offsets(L)
@@ -141,9 +172,9 @@ def test_empty_and_degenerate():
 @pytest.mark.slow
 def test_full_size_20000_ranges():
     """The batched workload itself: 20,000 ranges, lengths log-uniform in [1, 2^20]
-    (about 1.5e9 uniform u32 keys), launched as the benchmark launches it.
-    Every range is checked to be sorted and to hold the same keys (sum and xor
-    per range); 300 seeded ranges are compared with the oracle element by element."""
+    (about 1.5e9 uniform u32 keys), launched as the benchmark launches it, and
+    compared with the oracle's per-range sort of the whole batch, element by
+    element."""
     L = inputs.segment_lengths(20_000, seed=1)
     off = inputs.segment_offsets(L)
     n = int(off[-1])
@@ -155,15 +186,6 @@ def test_full_size_20000_ranges():
     after = t.cpu().numpy()
     del t
     torch.cuda.empty_cache()
-    starts = off[:-1][L > 0]
-    s64a, s64b = before.astype(np.uint64), after.astype(np.uint64)
-    assert np.array_equal(np.add.reduceat(s64a, starts), np.add.reduceat(s64b, starts))
-    assert np.array_equal(np.bitwise_xor.reduceat(before, starts),
-                          np.bitwise_xor.reduceat(after, starts))
-    inside = np.ones(n - 1, dtype=bool)
-    inside[off[1:-1] - 1] = False  # pairs that straddle a range boundary
-    assert (after[1:][inside] >= after[:-1][inside]).all()
-    rng = np.random.default_rng(3)
-    for s in rng.choice(len(L), 300, replace=False):
-        a, b = off[s], off[s + 1]
-        assert np.array_equal(after[a:b], oracle.radix_sort(before[a:b]))
+    want = oracle.segmented_sort(before, off)
+    del before
+    assert np.array_equal(after, want)
