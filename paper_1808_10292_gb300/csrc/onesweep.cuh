@@ -579,41 +579,59 @@ __device__ __forceinline__ void onesweep_tile_early(const PassParams& p, uint32_
 }
 
 // Shared memory of the ordered round: the per-warp counters, digit offsets and
-// misc words, then the staging area of the tile (no peer masks).
-template <typename K, int BITS, int THREADS, int KPT>
+// misc words, the staged keys (in tile order), and with payloads the staged
+// payloads (in input order) and each staged key's input index (16 bits).
+template <typename K, typename V, int BITS, int THREADS, int KPT>
 struct OrderedShape {
-  using S = OnesweepShape<K, NoVal, BITS, THREADS, KPT>;
-  static constexpr size_t SMEM = (size_t)S::HEADER_WORDS * 4 + (size_t)S::TILE * sizeof(K);
+  using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
+  static constexpr bool HV = HasVal<V>::value;
+  static constexpr size_t KEYS = (size_t)S::HEADER_WORDS * 4;
+  static constexpr size_t VALS = KEYS + (size_t)S::TILE * sizeof(K);
+  static constexpr size_t SRC = VALS + (HV ? (size_t)S::TILE * sizeof(V) : 0);
+  static constexpr size_t SMEM = SRC + (HV ? (size_t)S::TILE * 2 : 0);
+  static_assert(S::TILE <= 65536, "input indices are kept in 16 bits");
 };
 
-// One tile of a keys-only round after the first, "ordered" form. A key's
-// stable rank among the warp's keys of its digit is the value one shared-memory
-// atomicAdd on the warp's counter of the digit returns, provided the lanes of
-// one warp instruction that hit the same counter are served in lane order and
-// successive instructions in program order -- which is what GB300 does (a probe
-// of a million 32-lane rows found no exception), but nothing in CUDA promises
-// it. So the tile checks its result instead of trusting the order: the round's
-// input is sorted by the key bits below its digit (`low`; the invariant of LSD
-// rounds on keys), hence the tile is placed acceptably iff every digit run of
-// the staged tile is non-decreasing in those bits (keys that agree on the digit
-// and the low bits may take either order: later rounds order them by their
-// higher bits, or they are equal). The write-out compares each staged key with
-// its successor; a tile that fails is ranked again stably (peers found with
-// __match_any_sync) and written out again to the same positions.
-// Per key the fast path makes three digit-indexed shared accesses (count add,
-// slot add, store) against the peer-mask round's six.
-template <typename K, int BITS, int THREADS, int KPT, bool FULL>
+// One tile of a count-sort round, "ordered" form (every round of k_onesweep;
+// the rounds after the first of a keys-only segmented sort and all rounds of a
+// segmented pair sort). A key's stable rank among the warp's keys of its digit
+// is the value one shared-memory atomicAdd on the warp's counter of the digit
+// returns, provided the lanes of one warp instruction that hit the same
+// counter are served in lane order and successive instructions in program
+// order -- which is what GB300 does (a probe of a million 32-lane rows found
+// no exception), but nothing in CUDA promises it. So the tile checks its
+// result instead of trusting the order, in the write-out, key by key against
+// the next staged key of the same digit:
+//  - keys only: the round's input is sorted by the key bits below its digit
+//    (`low`; the invariant of LSD rounds on keys), so the tile is placed
+//    acceptably iff every digit run is non-decreasing in those bits (keys that
+//    agree on the digit and the low bits may take either order: later rounds
+//    order them by their higher bits, or they are equal);
+//  - with payloads: every digit run must hold its keys in input order (the
+//    staged input indices increase), which is exact stability.
+// A tile that fails is ranked again stably (peers found with __match_any_sync)
+// and written out again to the same positions. Payloads are copied into shared
+// memory in input order (cp.async, no registers) and gathered by the staged
+// input indices at the write-out. Per key the fast path makes three
+// digit-indexed shared accesses (count add, slot add, key store; with payloads
+// also the index store and the payload gather) against the peer-mask round's six.
+template <typename K, typename V, int BITS, int THREADS, int KPT, bool FULL>
 __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint32_t tile,
                                                       bool first, int64_t tile_base, int tile_n,
                                                       const K* __restrict__ kin,
-                                                      K* __restrict__ kout, const uint32_t* base,
-                                                      uint32_t bound, unsigned char* smem) {
-  using S = OnesweepShape<K, NoVal, BITS, THREADS, KPT>;
+                                                      K* __restrict__ kout, const V* vin, V* vout,
+                                                      const uint32_t* base, uint32_t bound,
+                                                      unsigned char* smem) {
+  using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
+  using O = OrderedShape<K, V, BITS, THREADS, KPT>;
   constexpr int R = S::R, WARPS = S::WARPS, DPT = S::DPT;
+  constexpr bool HV = O::HV;
   uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);  // [WARPS][R]
   uint32_t* s_adj = s_wcnt + WARPS * R;                   // [R]
   uint32_t* s_misc = s_adj + R;                           // [64]
-  K* s_keys = reinterpret_cast<K*>(smem + S::HEADER_WORDS * 4);
+  K* s_keys = reinterpret_cast<K*>(smem + O::KEYS);
+  V* s_vals = reinterpret_cast<V*>(smem + O::VALS);          // payloads only
+  uint16_t* s_src = reinterpret_cast<uint16_t*>(smem + O::SRC);  // payloads only
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wofs = warp * 32 * KPT + lane;
   const bool publish = (int64_t)tile != p.stall_tile;
@@ -623,8 +641,14 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
   if (tid == 0) *reinterpret_cast<const K**>(s_misc + 48) = kin + tile_base;
 
   K key[KPT];
-  NoVal val[1];
-  tile_load<K, NoVal, KPT, FULL>(kin, nullptr, tile_base, tile_n, wofs, key, val);
+  NoVal nv[1];
+  tile_load<K, NoVal, KPT, FULL>(kin, nullptr, tile_base, tile_n, wofs, key, nv);
+  if constexpr (HV) {
+#pragma unroll
+    for (int i = 0; i < KPT; ++i)
+      if (FULL || wofs + i * 32 < tile_n)
+        cp_async<sizeof(V)>(&s_vals[wofs + i * 32], vin + tile_base + wofs + i * 32);
+  }
   tile_count<K, R, KPT, FULL>(key, dig, tile_n, wofs, my);
   __syncthreads();
 
@@ -656,13 +680,14 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
   __syncthreads();
 
   // place: one slot add per key
+  auto place = [&](int i, uint32_t pos) {
+    s_keys[pos] = key[i];
+    if constexpr (HV) s_src[pos] = (uint16_t)(wofs + i * 32);
+  };
   if (p.check_mode != kCheckPerturb) {
 #pragma unroll
     for (int i = 0; i < KPT; ++i)
-      if (FULL || wofs + i * 32 < tile_n) {
-        const uint32_t pos = atomicAdd(&my[dig.of(key[i], i)], 1u);
-        s_keys[pos] = key[i];
-      }
+      if (FULL || wofs + i * 32 < tile_n) place(i, atomicAdd(&my[dig.of(key[i], i)], 1u));
   } else {  // test hook: odd lanes of each row first, an order the check must reject
 #pragma unroll
     for (int i = 0; i < KPT; ++i) {
@@ -672,7 +697,7 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
       __syncwarp();
       if (valid && !(lane & 1)) pos = atomicAdd(&my[dig.of(key[i], i)], 1u);
       __syncwarp();
-      if (valid) s_keys[pos] = key[i];
+      if (valid) place(i, pos);
     }
   }
 
@@ -691,9 +716,11 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
       s_adj[d] = base[d] + excl - tstart[j];
     }
   }
+  if constexpr (HV) cp_async_wait_all();  // this thread's payload copies have landed
   __syncthreads();
 
-  // write out, checking every staged key against the next one of its run
+  // write out (payloads gathered by input index), checking every staged key
+  // against the next one of its run
   const K low = p.shift ? (K(1) << p.shift) - K(1) : K(0);
   bool bad = p.check_mode == kCheckForceFallback;
 #pragma unroll
@@ -703,13 +730,20 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
       const K kk = s_keys[j];
       const uint32_t d = dig.staged(kk, j);
       const uint32_t g = s_adj[d] + (uint32_t)j;
-      if (g < bound)
+      uint32_t src = 0;
+      if constexpr (HV) src = s_src[j];
+      if (g < bound) {
         kout[g] = kk;
-      else
+        if constexpr (HV) vout[g] = s_vals[src];
+      } else {
         atomicOr(p.err, kErrBounds);
+      }
       if (j + 1 < (FULL ? S::TILE : tile_n)) {
         const K nx = s_keys[j + 1];
-        bad |= dig.staged(nx, j + 1) == d && (nx & low) < (kk & low);
+        if constexpr (HV)
+          bad |= dig.staged(nx, j + 1) == d && s_src[j + 1] < src;
+        else
+          bad |= dig.staged(nx, j + 1) == d && (nx & low) < (kk & low);
       }
     }
   }
@@ -738,7 +772,7 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
   __syncthreads();
   // Row by row, keys re-read from the input: peers by __match_any_sync, the
   // highest peer advances the counter, ranks in lane order (slow, but this path
-  // is for tiles whose check failed).
+  // is for tiles whose check failed). Payloads stay where they are (input order).
   const uint32_t lt = lanemask_lt();
   const K* tile_in = *reinterpret_cast<const K* const*>(s_misc + 48);
   uint32_t* my_row = s_wcnt + (threadIdx.x >> 5) * R;
@@ -752,7 +786,11 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
     uint32_t old = 0;
     if (valid && (peers >> lane) == 1u) old = atomicAdd(&my_row[d], __popc(peers));
     old = __shfl_sync(kFullMask, old, 31 - __clz(peers));
-    if (valid) s_keys[old + __popc(peers & lt)] = k;
+    if (valid) {
+      const uint32_t pos = old + __popc(peers & lt);
+      s_keys[pos] = k;
+      if constexpr (HV) s_src[pos] = (uint16_t)(wofs2 + i * 32);
+    }
     __syncwarp();  // this row's counter updates precede the next row's
   }
   __syncthreads();
@@ -760,25 +798,24 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
   for (int j = tid; j < tile_n; j += THREADS) {
     const K kk = s_keys[j];
     const uint32_t g = s_adj[dig.staged(kk, j)] + (uint32_t)j;
-    if (g < bound)
+    if (g < bound) {
       kout[g] = kk;
-    else
+      if constexpr (HV) vout[g] = s_vals[s_src[j]];
+    } else {
       atomicOr(p.err, kErrBounds);
+    }
   }
 }
 
 // One count-sort round over all n keys, one tile per CTA (tile ids in launch
-// order). Keys only: the ordered round; with payloads: the early-counts round
-// with the stable peer-mask rank.
+// order), in the ordered form.
 template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
   constexpr int R = S::R, WARPS = S::WARPS, TILE = S::TILE;
-  constexpr bool ORDERED = !HasVal<V>::value;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
   uint32_t* s_misc = s_wcnt + WARPS * R + R;
-  uint32_t* s_masks = reinterpret_cast<uint32_t*>(smem + EarlyShape<K, V, BITS, THREADS, KPT>::MASKS);
   const int tid = threadIdx.x;
 
   // Rows of the next pass's look-back array are cleared here, so one memset
@@ -792,7 +829,6 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
 
   if (tid == 0) s_misc[0] = atomicAdd(p.counter, 1u);  // tiles in launch order
   zero_words<THREADS>(s_wcnt, WARPS * R);
-  if constexpr (!ORDERED) zero_words<THREADS>(s_masks, WARPS * S::MASK_BUFS * R);
   __syncthreads();
   const uint32_t tile = s_misc[0];
   const int tile_n = (int)min((int64_t)TILE, p.n - (int64_t)tile * TILE);
@@ -803,34 +839,20 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
     if constexpr (HasVal<V>::value)
       prefetch_tile(static_cast<const V*>(src ? p.vals[1] : p.vals[0]), pf, cnt);
   }
-  if (p.trace && tid == 0) {
-    p.trace[(size_t)tile * 8 + 0] = globaltimer();
-    p.trace[(size_t)tile * 8 + 7] = smid();
-  }
   // select with branches, not a dynamic index, so the parameters stay out of local memory
   const K* kin = static_cast<const K*>(src ? p.keys[1] : p.keys[0]);
   K* kout = static_cast<K*>(src ? p.keys[0] : p.keys[1]);
+  const V* vin = static_cast<const V*>(src ? p.vals[1] : p.vals[0]);
+  V* vout = static_cast<V*>(src ? p.vals[0] : p.vals[1]);
   const int64_t tile_base = (int64_t)tile * TILE;
-  if constexpr (ORDERED) {
-    if (tile_n == TILE)
-      onesweep_tile_ordered<K, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n,
-                                                         kin, kout, p.base, (uint32_t)p.n, smem);
-    else
-      onesweep_tile_ordered<K, BITS, THREADS, KPT, false>(p, tile, tile == 0, tile_base, tile_n,
-                                                          kin, kout, p.base, (uint32_t)p.n, smem);
-  } else {
-    const V* vin = static_cast<const V*>(src ? p.vals[1] : p.vals[0]);
-    V* vout = static_cast<V*>(src ? p.vals[0] : p.vals[1]);
-    RadixDigit dig{p};
-    if (tile_n == TILE)
-      onesweep_tile_early<K, V, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n,
+  if (tile_n == TILE)
+    onesweep_tile_ordered<K, V, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n,
                                                           kin, kout, vin, vout, p.base,
-                                                          (uint32_t)p.n, smem, dig);
-    else
-      onesweep_tile_early<K, V, BITS, THREADS, KPT, false>(p, tile, tile == 0, tile_base, tile_n,
+                                                          (uint32_t)p.n, smem);
+  else
+    onesweep_tile_ordered<K, V, BITS, THREADS, KPT, false>(p, tile, tile == 0, tile_base, tile_n,
                                                            kin, kout, vin, vout, p.base,
-                                                           (uint32_t)p.n, smem, dig);
-  }
+                                                           (uint32_t)p.n, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -1037,9 +1059,7 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
   pp.spin_limit = a.spin_limit;
   pp.prefetch_tiles = a.prefetch_tiles;
   pp.check_mode = a.check_mode;
-  // keys only: the ordered round; with payloads: early counts, peer masks
-  constexpr size_t smem = HV ? EarlyShape<K, V, BITS, THREADS, KPT>::SMEM
-                             : OrderedShape<K, BITS, THREADS, KPT>::SMEM;
+  constexpr size_t smem = OrderedShape<K, V, BITS, THREADS, KPT>::SMEM;
   auto kern = k_onesweep<K, V, BITS, THREADS, KPT, MINB>;
   if (smem > 48 * 1024) {
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))

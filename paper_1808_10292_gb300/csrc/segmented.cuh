@@ -306,31 +306,22 @@ struct SegPassParams {
   int passes;
 };
 
-// FIRST (keys only, pass 0): the order-free first round of onesweep_tile_first.
+// One round over the tiles of every radix range: the ordered form, or with
+// FIRST (keys only, pass 0) the order-free first round of onesweep_tile_first.
 template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB, bool FIRST = false>
 __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp) {
   static_assert(!FIRST || !HasVal<V>::value, "the order-free round is keys-only");
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
-  using E = EarlyShape<K, V, BITS, THREADS, KPT>;
   constexpr int R = S::R, WARPS = S::WARPS, TILE = S::TILE;
   const PassParams& p = sp.p;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
   uint32_t* s_misc = FIRST ? s_wcnt + 2 * R : s_wcnt + WARPS * R + R;
-  uint32_t* s_stage = reinterpret_cast<uint32_t*>(smem + E::MASKS);  // the peer masks
   const int tid = threadIdx.x;
-  // keys only, passes after the first: the ordered round (no peer masks)
-  constexpr bool ORDERED = !FIRST && !HasVal<V>::value;
   if (p.status_next)
     for (int d = tid; d < R; d += THREADS) p.status_next[(size_t)blockIdx.x * R + d] = 0;
   if (tid == 0) s_misc[0] = atomicAdd(p.counter, 1u);
-  if constexpr (FIRST) {
-    zero_words<THREADS>(s_wcnt, R);
-  } else {
-    for (int i = tid; i < WARPS * R; i += THREADS) s_wcnt[i] = 0;
-    if constexpr (!ORDERED)
-      for (int i = tid; i < WARPS * S::MASK_BUFS * R; i += THREADS) s_stage[i] = 0;
-  }
+  zero_words<THREADS>(s_wcnt, FIRST ? R : WARPS * R);
   __syncthreads();
   const uint32_t tile = s_misc[0];
   if (tile >= sp.cnt[kCntTiles]) return;  // more CTAs than tiles: nothing left
@@ -357,24 +348,15 @@ __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp
     else
       onesweep_tile_first<K, BITS, THREADS, KPT, false>(p, tile, lt == 0, tile_base, tile_n, kin,
                                                         kout, base, (uint32_t)len, smem, dig);
-    return;
-  }
-  if constexpr (ORDERED) {
-    if (tile_n == TILE)
-      onesweep_tile_ordered<K, BITS, THREADS, KPT, true>(p, tile, lt == 0, tile_base, tile_n,
-                                                         kin, kout, base, (uint32_t)len, smem);
-    else
-      onesweep_tile_ordered<K, BITS, THREADS, KPT, false>(p, tile, lt == 0, tile_base, tile_n,
-                                                          kin, kout, base, (uint32_t)len, smem);
   } else {
     if (tile_n == TILE)
-      onesweep_tile_early<K, V, BITS, THREADS, KPT, true>(p, tile, lt == 0, tile_base, tile_n,
-                                                          kin, kout, vin, vout, base,
-                                                          (uint32_t)len, smem, dig);
+      onesweep_tile_ordered<K, V, BITS, THREADS, KPT, true>(p, tile, lt == 0, tile_base, tile_n,
+                                                            kin, kout, vin, vout, base,
+                                                            (uint32_t)len, smem);
     else
-      onesweep_tile_early<K, V, BITS, THREADS, KPT, false>(p, tile, lt == 0, tile_base, tile_n,
-                                                           kin, kout, vin, vout, base,
-                                                           (uint32_t)len, smem, dig);
+      onesweep_tile_ordered<K, V, BITS, THREADS, KPT, false>(p, tile, lt == 0, tile_base,
+                                                             tile_n, kin, kout, vin, vout, base,
+                                                             (uint32_t)len, smem);
   }
 }
 
@@ -445,8 +427,7 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
   timer_end(a.timer, st);
 
   auto kern = k_seg_onesweep<K, V, 8, THREADS, KPT, MINB>;
-  constexpr size_t SEG_SMEM = HasVal<V>::value ? EarlyShape<K, V, 8, THREADS, KPT>::SMEM
-                                               : OrderedShape<K, 8, THREADS, KPT>::SMEM;
+  constexpr size_t SEG_SMEM = OrderedShape<K, V, 8, THREADS, KPT>::SMEM;
   if (SEG_SMEM > 48 * 1024) {
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)SEG_SMEM)))
