@@ -191,6 +191,7 @@ struct PassParams {
   unsigned long long* trace;  // measurement hook: per tile, phase timestamps (or null)
   int64_t prefetch_tiles;     // L2-prefetch the input of the tile this many ids ahead (0: off)
   uint32_t check_mode;        // test hook of the ordered rounds (kCheck*; 0 in normal use)
+  uint32_t byte_sel;          // radix-256 rounds: radix8_byte_sel(shift)
 };
 
 // Test hooks of the ordered keys-only rounds (onesweep_tile_ordered).
@@ -209,24 +210,37 @@ constexpr uint32_t kCheckPerturb = 2;        // odd lanes take their slots first
 //   staged(k, j)  the digit of the key at tile slot j (k = that key).
 // RadixDigit refers to the round's parameters (shift and mask stay where the
 // kernel received them instead of being copied into registers).
+// Radix-256 rounds only (8-bit digits on byte boundaries): the digit is byte
+// shift / 8 of the key, taken with one byte permute (selector p.byte_sel).
 struct RadixDigit {
   const PassParams& p;
   template <typename K>
   __device__ __forceinline__ uint32_t operator()(K k) const {
-    return digit_of(k, p.shift, p.mask);
+    if constexpr (sizeof(K) == 4) {
+      return __byte_perm((uint32_t)k, 0u, p.byte_sel);
+    } else {
+      const uint32_t w = p.shift >= 32 ? (uint32_t)(k >> 32) : (uint32_t)k;
+      return __byte_perm(w, 0u, p.byte_sel);
+    }
   }
   template <typename K, int KPT>
   __device__ __forceinline__ void prepare(const K (&)[KPT]) {}
   template <typename K>
   __device__ __forceinline__ uint32_t of(K k, int) const {
-    return digit_of(k, p.shift, p.mask);
+    return (*this)(k);
   }
   __device__ __forceinline__ void keep(uint32_t, uint32_t) const {}
   template <typename K>
   __device__ __forceinline__ uint32_t staged(K k, int) const {
-    return digit_of(k, p.shift, p.mask);
+    return (*this)(k);
   }
 };
+
+// Byte-permute selector that moves byte (shift / 8) % 4 of a word to byte 0
+// and zeroes the others (bytes 4..7 of the permute's input are the zero word).
+__host__ __device__ constexpr uint32_t radix8_byte_sel(int shift) {
+  return 0x4440u | (uint32_t)((shift >> 3) & 3);
+}
 
 // Keep DRAM busy while tiles are ranking: one thread of the CTA asks the copy
 // engine to bring the input of a tile about one wave ahead into L2, so that
@@ -1020,6 +1034,7 @@ __global__ void k_copy_back(const uint32_t* __restrict__ skip, int passes, K* ke
 // with a per-tile look-back.
 template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB>
 cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
+  static_assert(BITS == 8, "the rounds take digits as bytes (RadixDigit)");
   using L = DigitLayout<K, BITS>;
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
   constexpr int R = L::R, P = L::PASSES;
@@ -1077,6 +1092,7 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
     pp.pass = q;
     pp.shift = q * BITS;
     pp.mask = (1u << L::width(q)) - 1;
+    pp.byte_sel = radix8_byte_sel(pp.shift);
     pp.base = a.base + (size_t)q * R;
     pp.status = a.status[q & 1];
     pp.status_next = (q + 1 < P) ? a.status[(q + 1) & 1] : nullptr;

@@ -7,7 +7,9 @@ with payloads) into a batch whenever one of the CUDA streams has room, lays the
 batch out contiguously in the arena, lets each request write its data into its
 slot (the request's fill callback), and sorts the whole batch with one
 isort_segmented call -- every request is one range, so each result is exactly
-what a sort of that request alone gives. Batches on different streams overlap
+what a sort of that request alone gives. A batch of one request (a stream was
+free when it arrived and nothing else was waiting) runs the plain sort
+instead, which has less fixed cost per launch. Batches on different streams overlap
 on the device; requests that arrive while others are on the GPU join the next
 batch as soon as a stream and arena space are free. One completion thread per
 stream waits for its batches in order, stamps each request's completion time,
@@ -98,11 +100,11 @@ class SortServer:
         self.num_streams = num_streams if batching else 1
         self.streams = [torch.cuda.Stream() for _ in range(self.num_streams)]
         # per-stream workspace, bound once (no allocation while serving)
+        # (a batch of one request runs the plain sort, so both kinds must fit)
+        ws = max(workspace_size(max_batch_keys, 32, 32, 8), workspace_size(max_batch_keys, 32, 0, 8))
         if batching:
-            ws = max(segmented_workspace_size(max_batch_requests, max_batch_keys, 32, 32),
+            ws = max(ws, segmented_workspace_size(max_batch_requests, max_batch_keys, 32, 32),
                      segmented_workspace_size(max_batch_requests, max_batch_keys, 32, 0))
-        else:
-            ws = max(workspace_size(max_batch_keys, 32, 32, 8), workspace_size(max_batch_keys, 32, 0, 8))
         self.ws = [torch.empty(ws, dtype=torch.uint8, device="cuda") for _ in self.streams]
         for s, w in zip(self.streams, self.ws):
             set_workspace(w, stream=s)
@@ -249,11 +251,14 @@ class SortServer:
                 r.fill(r.keys, r.vals, stream)
                 o += r.n
                 offs.append(o)
-            if self.batching:
+            if self.batching and len(batch) > 1:
                 d_off = torch.tensor(offs, dtype=torch.int64).to("cuda", non_blocking=True)
                 sort_segmented(keys, d_off, vals)
             else:
-                for r in batch:  # sequential baseline: one plain sort per request
+                # a lone request (the common case at light load) or the sequential
+                # baseline: the plain sort, without the segmented sort's fixed
+                # cost (range classes, offsets upload)
+                for r in batch:
                     if kind:
                         sort_pairs(r.keys, r.vals, 8)
                     else:

@@ -32,9 +32,12 @@ def collect():
     return got, done
 
 
-@pytest.mark.parametrize("batching", [True, False])
-def test_each_result_alone_equals_in_the_mix(batching):
-    arrivals, sizes, payload = inputs.requests(300, seed=2, rate=20000.0, min_log2=10,
+@pytest.mark.parametrize("batching,rate", [(True, 20000.0), (False, 20000.0), (True, 400.0)])
+def test_each_result_alone_equals_in_the_mix(batching, rate):
+    """At 20,000 req/s requests queue up and share batches (segmented sorts);
+    at 400 req/s most arrive to an idle server and run alone (plain sorts)."""
+    count = 300 if rate > 1000 else 80
+    arrivals, sizes, payload = inputs.requests(count, seed=2, rate=rate, min_log2=10,
                                                max_log2=17)
     got, done = collect()
     srv = serve.SortServer(budget_bytes=256 << 20, num_streams=3, max_batch_keys=1 << 20,
@@ -42,8 +45,8 @@ def test_each_result_alone_equals_in_the_mix(batching):
     reqs = serve.drive(srv, arrivals, sizes, payload, make_fill, duration_s=1e9, done=done)
     srv.close()
     assert not srv.errors
-    assert len(got) == len(reqs) == 300
-    if batching:
+    assert len(got) == len(reqs) == count
+    if batching and rate > 1000:
         assert srv.batches < len(reqs)  # requests really were batched
     for r in reqs:
         k, v = got[r.rid]
