@@ -55,7 +55,8 @@ int num_sms() {
 }
 
 int variants(int key_bits, int val_bits, int radix_bits, const LsdEntry** out) {
-  if (radix_bits == 16 || radix_bits == 11) return wide_variants(key_bits, val_bits, radix_bits, out);
+  if (radix_bits == 16) return pr2_variants(key_bits, val_bits, out);
+  if (radix_bits == 11) return wide_variants(key_bits, val_bits, radix_bits, out);
   if (key_bits == 32) return lsd_variants_k32(val_bits, radix_bits, out);
   if (key_bits == 64) return lsd_variants_k64(val_bits, radix_bits, out);
   return 0;
@@ -155,7 +156,7 @@ struct Layout {
 
 Layout layout_for(const LsdEntry& e, int64_t n) {
   Layout L;
-  const int64_t tiles = (n + e.tile - 1) / e.tile;
+  const int64_t tiles = (n + e.tile - 1) / e.tile + e.extra_status_rows;
   size_t off = 0;
   L.err = off;       off = align256(off + 4);
   L.hist = off;      off = align256(off + sizeof(uint32_t) * e.passes * e.radix);

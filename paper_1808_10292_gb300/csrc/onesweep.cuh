@@ -192,6 +192,7 @@ struct PassParams {
   int64_t prefetch_tiles;     // L2-prefetch the input of the tile this many ids ahead (0: off)
   uint32_t check_mode;        // test hook of the ordered rounds (kCheck*; 0 in normal use)
   uint32_t byte_sel;          // radix-256 rounds: radix8_byte_sel(shift)
+  int low_shift;              // keys only: the input is sorted by bits [0, low_shift)
 };
 
 // Test hooks of the ordered keys-only rounds (onesweep_tile_ordered).
@@ -617,7 +618,9 @@ struct OrderedShape {
 // result instead of trusting the order, in the write-out, key by key against
 // the next staged key of the same digit:
 //  - keys only: the round's input is sorted by the key bits below its digit
-//    (`low`; the invariant of LSD rounds on keys), so the tile is placed
+//    (`low` = bits [0, p.low_shift); the invariant of LSD rounds on keys; a
+//    round that sorts by part of a wider digit names the bits sorted so far),
+//    so the tile is placed
 //    acceptably iff every digit run is non-decreasing in those bits (keys that
 //    agree on the digit and the low bits may take either order: later rounds
 //    order them by their higher bits, or they are equal);
@@ -735,7 +738,7 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
 
   // write out (payloads gathered by input index), checking every staged key
   // against the next one of its run
-  const K low = p.shift ? (K(1) << p.shift) - K(1) : K(0);
+  const K low = p.low_shift ? (K(1) << p.low_shift) - K(1) : K(0);
   bool bad = p.check_mode == kCheckForceFallback;
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
@@ -1093,6 +1096,7 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
     pp.shift = q * BITS;
     pp.mask = (1u << L::width(q)) - 1;
     pp.byte_sel = radix8_byte_sel(pp.shift);
+    pp.low_shift = pp.shift;
     pp.base = a.base + (size_t)q * R;
     pp.status = a.status[q & 1];
     pp.status_next = (q + 1 < P) ? a.status[(q + 1) & 1] : nullptr;

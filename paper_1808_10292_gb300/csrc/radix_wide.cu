@@ -1,24 +1,17 @@
-// Wide-radix passes: radix 65536 (the paper's PR2: 16-bit digits, two rounds
-// on 32-bit keys) and radix 2048 (11-bit digits: three rounds of 11, 11 and 10
-// bits on 32-bit keys, six on 64-bit keys).
+// Radix 2048 (11-bit digits: three rounds of 11, 11 and 10 bits on 32-bit
+// keys, six on 64-bit keys); radix 65536 is radix16.cu.
 //
 // Paper mapping (Section "SR4, PR2, PR4, BTN and OET under MBSP", Eqs. Tp,
 // Tp2): each worker counts the digits of its share of the keys, the p x r count
-// matrix is exchanged (the 2prg term, which grows with r and is why the paper
-// found PR2 slower than PR4), and every worker routes its keys to their global
-// positions. With r = 65536 a per-tile decoupled look-back would need 256 KiB
-// of status per tile (8 KiB at r = 2048, still a quarter of a tile's keys), so
-// each round here is the paper's count-sort literally: the input is read twice
-// (count, then place) and written once. A "block" is one row of the count
-// matrix: 2^19 keys at r = 65536, 2^16 keys at r = 2048.
+// matrix is exchanged (the 2prg term, which grows with r), and every worker
+// routes its keys to their global positions. A per-tile decoupled look-back
+// would need 8 KiB of status per tile at r = 2048 (a quarter of a tile's keys),
+// so each round here is the paper's count-sort literally: the input is read
+// twice (count, then place) and written once. A "block" is one row of the
+// count matrix, 2^16 keys.
 //
-//   k_count16      (r = 65536) per block, the 65536-bin digit histogram. A
-//                  2-CTA thread-block cluster holds it in distributed shared
-//                  memory: CTA r owns bins [r*32768, (r+1)*32768) as 32-bit
-//                  counters (128 KiB) and each CTA reads half of the block,
-//                  adding into the owner's shared memory (local or remote).
-//   k_count_smem   (r = 2048) per block, the histogram in one CTA's shared
-//                  memory, eight copies of the bins to spread contention.
+//   k_count_smem   per block, the histogram in one CTA's shared memory, eight
+//                  copies of the bins to spread contention.
 //   k_colscan      per digit, the exclusive prefix over blocks (the count
 //                  matrix exchange), in place, and the digit totals.
 //   k_digscan      exclusive prefix over the digit totals -> global bases;
@@ -28,32 +21,19 @@
 //                  partition by its low 8 bits, then by the rest), then each
 //                  key goes to base[d] + (earlier blocks' d-keys) + (this
 //                  block's d-keys so far) + (its rank in the sub-tile's run of
-//                  d). The per-block running offsets live in the block's row
-//                  of the matrix.
-#include <cooperative_groups.h>
-
+//                  d). The per-block running offsets live in shared memory.
 #include <algorithm>
 
 #include "common.cuh"
 #include "isort_internal.h"
 
-namespace cg = cooperative_groups;
-
 namespace isort {
 namespace {
 
-constexpr int kR16 = 65536;
-constexpr int kHalfBins = kR16 / 2;
 
 // Keys per count-matrix row (block) and kernel names, per digit width.
 template <int BITS>
 struct Wide;
-template <>
-struct Wide<16> {
-  static constexpr int64_t BLOCK_KEYS = int64_t(1) << 19;
-  static constexpr const char* COUNT = "k_count16";
-  static constexpr const char* SCATTER = "k_scatter16";
-};
 template <>
 struct Wide<11> {
   static constexpr int64_t BLOCK_KEYS = int64_t(1) << 16;
@@ -73,10 +53,6 @@ constexpr int kPadded = kSubKeys + kSubKeys / 32;
 __device__ __forceinline__ int padj(int j) { return j + (j >> 5); }
 constexpr uint32_t kNoDigit = 0x10000u;  // differs from every 16-bit digit
 
-template <typename K>
-__device__ __forceinline__ uint32_t digit16(K k, int shift) {
-  return static_cast<uint32_t>(k >> shift) & 0xffffu;
-}
 
 template <typename K>
 __device__ __forceinline__ uint32_t digit_w(K k, int shift, uint32_t mask) {
@@ -90,37 +66,6 @@ __device__ __forceinline__ int input_parity(const uint32_t* skip, int pass) {
 }
 
 // ---------------------------------------------------------------------------
-template <typename K>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kCountThreads)
-    k_count16(const K* buf0, const K* buf1, const uint32_t* skip, int pass, int64_t n, int shift,
-              uint32_t* counts) {
-  extern __shared__ __align__(16) uint32_t s_bins[];  // kHalfBins
-  cg::cluster_group cluster = cg::this_cluster();
-  const unsigned rank = cluster.block_rank();
-  for (int i = threadIdx.x; i < kHalfBins; i += kCountThreads) s_bins[i] = 0;
-  cluster.sync();  // both halves zeroed before any remote add
-  uint32_t* remote = cluster.map_shared_rank(s_bins, rank ^ 1);
-
-  const K* keys = input_parity(skip, pass) ? buf1 : buf0;
-  const int64_t block = blockIdx.x / 2;
-  const int64_t lo = block * Wide<16>::BLOCK_KEYS;
-  const int64_t hi = min(n, lo + Wide<16>::BLOCK_KEYS);
-  const int64_t len = hi - lo;
-  const int64_t half = (len + 1) / 2;
-  const int64_t my_lo = lo + (rank ? half : 0);
-  const int64_t my_hi = rank ? hi : lo + half;
-  for (int64_t i = my_lo + threadIdx.x; i < my_hi; i += kCountThreads) {
-    const uint32_t d = digit16(keys[i], shift);
-    if ((d >> 15) == rank)
-      atomicAdd(&s_bins[d & (kHalfBins - 1)], 1u);
-    else
-      atomicAdd(&remote[d & (kHalfBins - 1)], 1u);
-  }
-  cluster.sync();  // every add into my bins has landed; the partner may exit after this
-  uint32_t* row = counts + (size_t)block * kR16 + (size_t)rank * kHalfBins;
-  for (int i = threadIdx.x; i < kHalfBins; i += kCountThreads) row[i] = s_bins[i];
-}
-
 // Per block of Wide<11>::BLOCK_KEYS keys, the R-bin digit histogram in shared
 // memory (R <= 4096): warp w adds into copy w % 8 of the bins, so equal digits
 // from different warps rarely meet on one counter; the copies are summed into
@@ -496,16 +441,10 @@ cudaError_t wide_launch(const LsdArgs& a, cudaStream_t st) {
   uint32_t* total = a.hist;        // [R]
   uint32_t* base = a.base;         // [R] (one pass at a time)
   cudaError_t e;
-  const size_t count_smem = BITS == 16 ? sizeof(uint32_t) * kHalfBins : sizeof(uint32_t) * 8 * R;
-  if constexpr (BITS == 16) {
-    if ((e = cudaFuncSetAttribute(k_count16<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)count_smem)))
-      return e;
-  } else {
-    if ((e = cudaFuncSetAttribute(k_count_smem<K, R>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)count_smem)))
-      return e;
-  }
+  const size_t count_smem = sizeof(uint32_t) * 8 * R;
+  if ((e = cudaFuncSetAttribute(k_count_smem<K, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)count_smem)))
+    return e;
   const size_t sc_smem = sizeof(Scatter16Smem<K, V>) + (R <= 4096 ? sizeof(uint32_t) * R : 0);
   if ((e = cudaFuncSetAttribute(k_scatter_wide<K, V, BITS>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc_smem)))
@@ -514,14 +453,9 @@ cudaError_t wide_launch(const LsdArgs& a, cudaStream_t st) {
     const int shift = BITS * q;
     const int width = KB - shift < BITS ? KB - shift : BITS;
     timer_begin(a.timer, Wide<BITS>::COUNT, st);
-    if constexpr (BITS == 16)
-      k_count16<K><<<(unsigned)(2 * nblocks), kCountThreads, count_smem, st>>>(
-          static_cast<const K*>(a.keys), static_cast<const K*>(a.alt_keys), a.skip, q, a.n, shift,
-          counts);
-    else
-      k_count_smem<K, R><<<(unsigned)nblocks, kCountThreads, count_smem, st>>>(
-          static_cast<const K*>(a.keys), static_cast<const K*>(a.alt_keys), a.skip, q, a.n, shift,
-          (1u << width) - 1u, counts);
+    k_count_smem<K, R><<<(unsigned)nblocks, kCountThreads, count_smem, st>>>(
+        static_cast<const K*>(a.keys), static_cast<const K*>(a.alt_keys), a.skip, q, a.n, shift,
+        (1u << width) - 1u, counts);
     timer_end(a.timer, st);
     timer_begin(a.timer, "k_colscan", st);
     k_colscan<R><<<R / 32, 1024, 0, st>>>(counts, nblocks, total);
@@ -568,21 +502,17 @@ constexpr LsdEntry wide_entry() {
   static const LsdEntry kW##B##None64[] = {wide_entry<uint64_t, NoVal, B>()};            \
   static const LsdEntry kW##B##V32_64[] = {wide_entry<uint64_t, uint32_t, B>()};         \
   static const LsdEntry kW##B##V64_64[] = {wide_entry<uint64_t, uint64_t, B>()};
-ISORT_WIDE_TABLES(16)
 ISORT_WIDE_TABLES(11)
 #undef ISORT_WIDE_TABLES
 
 int wide_variants(int key_bits, int val_bits, int radix_bits, const LsdEntry** out) {
   if (val_bits != 0 && val_bits != 32 && val_bits != 64) return 0;
   const int vi = val_bits == 0 ? 0 : val_bits == 32 ? 1 : 2;
-  const LsdEntry* t16[2][3] = {{kW16None32, kW16V32_32, kW16V64_32},
-                               {kW16None64, kW16V32_64, kW16V64_64}};
   const LsdEntry* t11[2][3] = {{kW11None32, kW11V32_32, kW11V64_32},
                                {kW11None64, kW11V32_64, kW11V64_64}};
   if (key_bits != 32 && key_bits != 64) return 0;
   const int ki = key_bits == 32 ? 0 : 1;
-  if (radix_bits == 16) *out = t16[ki][vi];
-  else if (radix_bits == 11) *out = t11[ki][vi];
+  if (radix_bits == 11) *out = t11[ki][vi];
   else return 0;
   return 1;
 }

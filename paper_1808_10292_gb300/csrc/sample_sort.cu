@@ -301,6 +301,7 @@ cudaError_t gvr_launch(const GvrArgs& a, cudaStream_t st) {
   pp.shift = 0;
   pp.mask = 0xffu;
   pp.byte_sel = radix8_byte_sel(0);
+  pp.low_shift = 0;
   pp.base = a.base;
   pp.skip = a.skip;
   pp.status = a.status;

@@ -470,6 +470,7 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
     pp.shift = q * 8;
     pp.mask = (1u << L::width(q)) - 1;
     pp.byte_sel = radix8_byte_sel(pp.shift);
+    pp.low_shift = pp.shift;
     pp.status = a.status[q & 1];
     pp.status_next = (q + 1 < P) ? a.status[(q + 1) & 1] : nullptr;
     pp.counter = a.cnt + kCntPassTiles + q;

@@ -63,6 +63,32 @@ def test_segmented_every_check_mode(check_mode, mode):
     assert np.array_equal(d.cpu().numpy(), oracle.segmented_sort(k, off))
 
 
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("key_bits,val_bits", [(32, 0), (32, 32), (64, 0)])
+@pytest.mark.parametrize("dist", ["uniform", "and4", "u16", "sorted"])
+def test_radix65536_every_check_mode(check_mode, mode, key_bits, val_bits, dist):
+    """Radix 65536 routes each round in two ordered steps (high byte over all
+    keys, checked against the bits below the 16-bit digit; low byte inside
+    every bucket); both steps must survive a forced fallback and perturbed
+    ranks."""
+    n = 400_003
+    k = inputs.keys(n, key_bits, dist, seed=15)
+    check_mode(mode)
+    d = torch.from_numpy(k).cuda()
+    if val_bits:
+        v = inputs.iota(n, val_bits)
+        dv = torch.from_numpy(v).cuda()
+        isort.sort_pairs(d, dv, 16)
+        ok, ov = oracle.radix_sort(k, v, radix_bits=16)
+        assert isort.stream_status() == _lib.OK
+        assert np.array_equal(dv.cpu().numpy(), ov)
+    else:
+        isort.sort_keys(d, 16)
+        ok = _oracle(k)
+        assert isort.stream_status() == _lib.OK
+    assert np.array_equal(d.cpu().numpy(), ok)
+
+
 def test_perturbed_ranks_fail_the_check_and_are_repaired(check_mode):
     """With odd lanes first, a round whose rows hold equal digits with different
     low bits is unstable; the result is still exact, so the check caught every

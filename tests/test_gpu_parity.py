@@ -165,13 +165,13 @@ def test_bounded_wait_reports_timeout_and_context_survives(variant):
     assert np.array_equal(gpu_sort(d), np.sort(d))
 
 
-R16_BLOCK = 1 << 19  # keys per count-matrix row of the radix-65536 path
+R16_TILE = 8192  # keys per tile of the radix-65536 steps (32-bit keys alone)
 
 
 @pytest.mark.parametrize("key_bits", [32, 64])
 @pytest.mark.parametrize("dist", inputs.DISTS)
 def test_radix65536_distributions(key_bits, dist):
-    n = 1_234_567  # three count blocks (2^19 keys), many 4096-key sub-tiles, a ragged tail
+    n = 1_234_567  # 256 buckets of a few tiles each, ragged bucket ends
     k = inputs.keys(n, key_bits, dist, seed=12)
     assert np.array_equal(gpu_sort(k, radix_bits=16), oracle.radix_sort(k, radix_bits=16))
 
@@ -189,8 +189,8 @@ def test_radix65536_pairs_stable(key_bits, val_bits, dist):
 
 
 def test_radix65536_edge_sizes():
-    for n in sorted({0, 1, 2, 3, 4095, 4096, 4097, 9000, R16_BLOCK - 1, R16_BLOCK, R16_BLOCK + 1,
-                     2 * R16_BLOCK + 4097}):
+    for n in sorted({0, 1, 2, 3, 4095, 4096, 4097, 9000, R16_TILE - 1, R16_TILE, R16_TILE + 1,
+                     256 * R16_TILE + 3, 600_001}):
         k = inputs.keys(n, 32, "and4", seed=n + 3)
         v = inputs.iota(n)
         gk, gv = gpu_sort(k, v, radix_bits=16)
