@@ -13,8 +13,8 @@
 // first (most significant first inside the digit):
 //
 //   k_hist16        the 65536-bin histogram of the round's digit, one read of
-//                   the keys (a 2-CTA cluster holds the bins in distributed
-//                   shared memory).
+//                   the keys from DRAM (pairs of CTAs share a chunk, each
+//                   counting half of the bins in shared memory).
 //   k_scan16        exclusive prefix of the 65536 counts (base16), per high
 //                   byte h: the bucket [base16[h*256], base16[h*256+256]), its
 //                   tiles, and whether its low byte is constant.
@@ -27,11 +27,7 @@
 //                   16-bit digit's destination.
 // Step B of a bucket whose low byte is constant copies the bucket. Stability of
 // both steps makes the round the stable count-sort by the 16-bit digit.
-#include <cooperative_groups.h>
-
 #include "onesweep.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace isort {
 namespace {
@@ -53,26 +49,36 @@ __device__ __forceinline__ int parity_of(const uint32_t* skip, int pass) {
 
 // The 65536-bin histogram of digit16(key, shift) of all n keys of the round's
 // input buffer (the parity of the passes executed before `pass`), added into
-// hist. Cluster of 2 CTAs: CTA r owns bins [r*32768, (r+1)*32768) in its
-// shared memory; each CTA counts a grid-strided share of the keys into the
-// owner's bins (local or remote).
+// hist. CTAs 2c and 2c+1 read the same chunk c of the keys (the second read
+// mostly hits L2); CTA 2c + r counts only the digits of bin half r, in its own
+// shared memory (32768 counters, 128 KiB). Lanes whose digit equals that of
+// the first active lane are counted with one add (keys whose digit is nearly
+// constant would otherwise serialise on one counter).
 template <typename K>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kHistThreads)
+__global__ void __launch_bounds__(kHistThreads)
     k_hist16(const K* buf0, const K* buf1, const uint32_t* skip, int pass, int64_t n, int shift,
              uint32_t* hist) {
   extern __shared__ __align__(16) uint32_t s_bins[];  // kHalf16
-  cg::cluster_group cluster = cg::this_cluster();
-  const unsigned rank = cluster.block_rank();
+  const uint32_t rank = blockIdx.x & 1u;
   for (int i = threadIdx.x; i < kHalf16; i += kHistThreads) s_bins[i] = 0;
-  cluster.sync();  // both halves zeroed before any remote add
-  uint32_t* remote = cluster.map_shared_rank(s_bins, rank ^ 1);
+  __syncthreads();
   const K* keys = parity_of(skip, pass) ? buf1 : buf0;
-  const int64_t stride = (int64_t)gridDim.x * kHistThreads;
-  for (int64_t i = (int64_t)blockIdx.x * kHistThreads + threadIdx.x; i < n; i += stride) {
-    const uint32_t d = digit16(keys[i], shift);
-    atomicAdd(&((d >> 15) == rank ? s_bins : remote)[d & (kHalf16 - 1)], 1u);
-  }
-  cluster.sync();  // every add into my bins has landed
+  const int64_t chunks = gridDim.x >> 1, chunk = blockIdx.x >> 1;
+  const int64_t lo = n * chunk / chunks, hi = n * (chunk + 1) / chunks;
+  const uint32_t lane = threadIdx.x & 31;
+  count_keys(keys + lo, hi - lo, threadIdx.x, kHistThreads, [&](K k) {
+    const uint32_t d = digit16(k, shift);
+    const uint32_t m = __activemask();
+    const uint32_t first = __ffs(m) - 1;
+    const uint32_t d0 = __shfl_sync(m, d, first);
+    const uint32_t same = __ballot_sync(m, d == d0);
+    if (d != d0) {
+      if ((d >> 15) == rank) atomicAdd(&s_bins[d & (kHalf16 - 1)], 1u);
+    } else if (lane == first && (d0 >> 15) == rank) {
+      atomicAdd(&s_bins[d0 & (kHalf16 - 1)], (uint32_t)__popc(same));
+    }
+  });
+  __syncthreads();
   for (int i = threadIdx.x; i < kHalf16; i += kHistThreads) {
     const uint32_t c = s_bins[i];
     if (c) atomicAdd(&hist[rank * kHalf16 + i], c);
@@ -252,7 +258,7 @@ cudaError_t pr2_launch(const LsdArgs& a, cudaStream_t st) {
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem)))
       return e;
   }
-  const int hgrid = std::max(2, (a.num_sms / 2) * 2);  // whole clusters, one CTA per SM
+  const int hgrid = std::max(2, (a.num_sms / 2) * 2);  // pairs of CTAs, one CTA per SM
   PassParams pp;
   pp.keys[0] = a.keys;
   pp.keys[1] = a.alt_keys;
