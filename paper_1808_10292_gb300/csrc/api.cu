@@ -55,8 +55,7 @@ int num_sms() {
 }
 
 int variants(int key_bits, int val_bits, int radix_bits, const LsdEntry** out) {
-  if (radix_bits == 16) return pr2_variants(key_bits, val_bits, out);
-  if (radix_bits == 11) return wide_variants(key_bits, val_bits, radix_bits, out);
+  if (radix_bits == 16 || radix_bits == 11) return wide_variants(key_bits, val_bits, radix_bits, out);
   if (key_bits == 32) return lsd_variants_k32(val_bits, radix_bits, out);
   if (key_bits == 64) return lsd_variants_k64(val_bits, radix_bits, out);
   return 0;

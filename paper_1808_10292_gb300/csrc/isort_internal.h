@@ -63,11 +63,9 @@ struct LsdEntry {
 // Variant tables, one per key width (sort_k32.cu, sort_k64.cu).
 int lsd_variants_k32(int val_bits, int radix_bits, const LsdEntry** out);
 int lsd_variants_k64(int val_bits, int radix_bits, const LsdEntry** out);
-// Wide-radix paths (radix_wide.cu): radix_bits 16 (radix 65536) or 11 (radix
+// Wide-radix paths (wide_rounds.cu): radix_bits 16 (radix 65536) or 11 (radix
 // 2048); one entry per (key_bits, val_bits, radix_bits).
 int wide_variants(int key_bits, int val_bits, int radix_bits, const LsdEntry** out);
-// Radix 65536 (radix16.cu): one entry per (key_bits, val_bits).
-int pr2_variants(int key_bits, int val_bits, const LsdEntry** out);
 
 // ---- segmented sort (segmented.cuh) ----
 // Layout of the small counter block (uint32 words).

@@ -237,6 +237,28 @@ struct RadixDigit {
   }
 };
 
+// Any digit of at most 8 bits: bits [p.shift, p.shift + width) of the key, with
+// p.mask = 2^width - 1 (the steps of the wide-radix rounds, whose digit parts
+// need not sit on byte boundaries).
+struct ShiftMaskDigit {
+  const PassParams& p;
+  template <typename K>
+  __device__ __forceinline__ uint32_t operator()(K k) const {
+    return digit_of(k, p.shift, p.mask);
+  }
+  template <typename K, int KPT>
+  __device__ __forceinline__ void prepare(const K (&)[KPT]) {}
+  template <typename K>
+  __device__ __forceinline__ uint32_t of(K k, int) const {
+    return (*this)(k);
+  }
+  __device__ __forceinline__ void keep(uint32_t, uint32_t) const {}
+  template <typename K>
+  __device__ __forceinline__ uint32_t staged(K k, int) const {
+    return (*this)(k);
+  }
+};
+
 // Byte-permute selector that moves byte (shift / 8) % 4 of a word to byte 0
 // and zeroes the others (bytes 4..7 of the permute's input are the zero word).
 __host__ __device__ constexpr uint32_t radix8_byte_sel(int shift) {
@@ -632,7 +654,8 @@ struct OrderedShape {
 // input indices at the write-out. Per key the fast path makes three
 // digit-indexed shared accesses (count add, slot add, key store; with payloads
 // also the index store and the payload gather) against the peer-mask round's six.
-template <typename K, typename V, int BITS, int THREADS, int KPT, bool FULL>
+template <typename K, typename V, int BITS, int THREADS, int KPT, bool FULL,
+          typename DS = RadixDigit>
 __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint32_t tile,
                                                       bool first, int64_t tile_base, int tile_n,
                                                       const K* __restrict__ kin,
@@ -652,7 +675,7 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wofs = warp * 32 * KPT + lane;
   const bool publish = (int64_t)tile != p.stall_tile;
-  RadixDigit dig{p};
+  DS dig{p};
   uint32_t* my = s_wcnt + warp * R;
   // the fallback re-reads the tile's input address from here (fewer live registers)
   if (tid == 0) *reinterpret_cast<const K**>(s_misc + 48) = kin + tile_base;
@@ -825,8 +848,9 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
 }
 
 // One count-sort round over all n keys, one tile per CTA (tile ids in launch
-// order), in the ordered form.
-template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB>
+// order), in the ordered form. DS: the digit rule (bytes for radix 256).
+template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB,
+          typename DS = RadixDigit>
 __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
   constexpr int R = S::R, WARPS = S::WARPS, TILE = S::TILE;
@@ -863,13 +887,11 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
   V* vout = static_cast<V*>(src ? p.vals[0] : p.vals[1]);
   const int64_t tile_base = (int64_t)tile * TILE;
   if (tile_n == TILE)
-    onesweep_tile_ordered<K, V, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n,
-                                                          kin, kout, vin, vout, p.base,
-                                                          (uint32_t)p.n, smem);
+    onesweep_tile_ordered<K, V, BITS, THREADS, KPT, true, DS>(
+        p, tile, tile == 0, tile_base, tile_n, kin, kout, vin, vout, p.base, (uint32_t)p.n, smem);
   else
-    onesweep_tile_ordered<K, V, BITS, THREADS, KPT, false>(p, tile, tile == 0, tile_base, tile_n,
-                                                           kin, kout, vin, vout, p.base,
-                                                           (uint32_t)p.n, smem);
+    onesweep_tile_ordered<K, V, BITS, THREADS, KPT, false, DS>(
+        p, tile, tile == 0, tile_base, tile_n, kin, kout, vin, vout, p.base, (uint32_t)p.n, smem);
 }
 
 // ---------------------------------------------------------------------------

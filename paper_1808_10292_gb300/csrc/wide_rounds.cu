@@ -1,0 +1,429 @@
+// Wide radixes: 65536 (the paper's PR2: 16-bit digits, two rounds on 32-bit
+// keys, four on 64-bit keys) and 2048 (11-bit digits: 11, 11, 10 bits on
+// 32-bit keys; 5 x 11 + 9 on 64-bit keys). Section "SR4, PR2, PR4, BTN and OET
+// under MBSP", Eqs. Tp, Tp2.
+//
+// Each round is one count-sort round by a W-bit digit: the 2^W-bin digit
+// histogram, its exclusive prefix (every key's destination = the prefix of its
+// digit plus its rank among the earlier keys of that digit), and the routing of
+// every key to its destination. Routing 2^W ways at once leaves each digit's
+// run of a GPU tile at a fraction of a 32-byte sector, and the partly written
+// sectors of every tile in flight overflow the L2 (a direct 65536-way scatter
+// measured 9.5x DRAM read and write amplification; the 2048-way one 2.4x
+// write amplification and one L2 write request per key). So routing takes two
+// steps, each writing long runs, the high W - 8 bits of the digit first:
+//
+//   k_hist16 /      the 2^W-bin histogram of the round's digit, one read of the
+//   k_hist_small    keys (65536 bins: pairs of CTAs share a chunk, each
+//                   counting half of the bins; up to 4096 bins: one CTA, eight
+//                   copies of the bins).
+//   k_scan_wide     exclusive prefix of the 2^W counts (base); per high part h
+//                   (a "bucket", 2^(W-8) of them): its start base[h*256], its
+//                   tiles, and whether its low byte is constant.
+//   A: k_onesweep   an ordered round by the HIGH part over all keys (stable),
+//                   which moves every key into its bucket (bases base[h*256]).
+//   B: k_bucket     an ordered round by the LOW byte inside every bucket
+//                   (stable; tiles never straddle a bucket) with bases
+//                   base[h*256 + l]: every key lands at its digit's place.
+// Step B of a bucket whose low byte is constant copies the bucket. Stability of
+// both steps makes the round the stable count-sort by the W-bit digit.
+#include "onesweep.cuh"
+
+namespace isort {
+namespace {
+
+constexpr int kR16 = 65536;
+constexpr int kHalf16 = kR16 / 2;
+constexpr int kHistThreads = 1024;
+constexpr int kMaxBuckets = 256;
+
+__device__ __forceinline__ int parity_of(const uint32_t* skip, int pass) {
+  int src = 0;
+  for (int q = 0; q < pass; ++q) src ^= (skip[q] == 0);
+  return src;
+}
+
+// Counts one key whose digit is d into bins (via add(bin, count)), combining
+// the lanes whose digit equals that of the first active lane into one add
+// (keys whose digit is nearly constant would otherwise serialise on one bin).
+template <typename Add>
+__device__ __forceinline__ void count_digit(uint32_t d, Add&& add) {
+  const uint32_t m = __activemask();
+  const uint32_t first = __ffs(m) - 1;
+  const uint32_t d0 = __shfl_sync(m, d, first);
+  const uint32_t same = __ballot_sync(m, d == d0);
+  if (d != d0)
+    add(d, 1u);
+  else if ((threadIdx.x & 31) == first)
+    add(d0, (uint32_t)__popc(same));
+}
+
+// The 65536-bin histogram of the 16-bit digit at `shift` of all n keys of the
+// round's input buffer (the parity of the passes executed before `pass`),
+// added into hist. CTAs 2c and 2c+1 read the same chunk c of the keys (the
+// second read mostly hits L2); CTA 2c + r counts only the digits of bin half
+// r, in its own shared memory (32768 counters, 128 KiB).
+template <typename K>
+__global__ void __launch_bounds__(kHistThreads)
+    k_hist16(const K* buf0, const K* buf1, const uint32_t* skip, int pass, int64_t n, int shift,
+             uint32_t* hist) {
+  extern __shared__ __align__(16) uint32_t s_bins[];  // kHalf16
+  const uint32_t rank = blockIdx.x & 1u;
+  for (int i = threadIdx.x; i < kHalf16; i += kHistThreads) s_bins[i] = 0;
+  __syncthreads();
+  const K* keys = parity_of(skip, pass) ? buf1 : buf0;
+  const int64_t chunks = gridDim.x >> 1, chunk = blockIdx.x >> 1;
+  const int64_t lo = n * chunk / chunks, hi = n * (chunk + 1) / chunks;
+  count_keys(keys + lo, hi - lo, threadIdx.x, kHistThreads, [&](K k) {
+    count_digit(digit_of(k, shift, 0xffffu), [&](uint32_t d, uint32_t c) {
+      if ((d >> 15) == rank) atomicAdd(&s_bins[d & (kHalf16 - 1)], c);
+    });
+  });
+  __syncthreads();
+  for (int i = threadIdx.x; i < kHalf16; i += kHistThreads) {
+    const uint32_t c = s_bins[i];
+    if (c) atomicAdd(&hist[rank * kHalf16 + i], c);
+  }
+}
+
+// The BINS-bin histogram (BINS <= 4096) of the digit (k >> shift) & mask:
+// every CTA takes a chunk of the keys, warp w counting into copy w % 8 of the
+// bins, and adds the copies' sums into hist.
+template <typename K, int BINS>
+__global__ void __launch_bounds__(kHistThreads)
+    k_hist_small(const K* buf0, const K* buf1, const uint32_t* skip, int pass, int64_t n,
+                 int shift, uint32_t mask, uint32_t* hist) {
+  constexpr int COPIES = 8;
+  extern __shared__ __align__(16) uint32_t s_bins[];  // [COPIES][BINS]
+  for (int i = threadIdx.x; i < COPIES * BINS; i += kHistThreads) s_bins[i] = 0;
+  __syncthreads();
+  const K* keys = parity_of(skip, pass) ? buf1 : buf0;
+  const int64_t lo = n * blockIdx.x / gridDim.x, hi = n * (blockIdx.x + 1) / gridDim.x;
+  uint32_t* my = s_bins + ((threadIdx.x >> 5) % COPIES) * BINS;
+  count_keys(keys + lo, hi - lo, threadIdx.x, kHistThreads, [&](K k) {
+    count_digit(digit_of(k, shift, mask), [&](uint32_t d, uint32_t c) { atomicAdd(&my[d], c); });
+  });
+  __syncthreads();
+  for (int d = threadIdx.x; d < BINS; d += kHistThreads) {
+    uint32_t sum = 0;
+#pragma unroll
+    for (int c = 0; c < COPIES; ++c) sum += s_bins[c * BINS + d];
+    if (sum) atomicAdd(&hist[d], sum);
+  }
+}
+
+// Per round (BINS = 2^W bins, NB = BINS / 256 buckets): base = exclusive prefix
+// of hist; per bucket h: baseA[h] = base[h*256] (the bases of step A), its
+// first tile among step B's tiles (tile_first[0..NB], tiles of TILE keys) and
+// bucket_trivial[h] (one low byte holds all of the bucket's keys); skip[passA]
+// (one bucket holds all n keys) and skip[passA + 1] (every bucket is trivial).
+// One CTA of 1024 threads.
+template <int BINS, int TILE>
+__global__ void __launch_bounds__(1024) k_scan_wide(const uint32_t* __restrict__ hist,
+                                                    uint32_t* __restrict__ base,
+                                                    uint32_t* __restrict__ baseA,
+                                                    uint32_t* __restrict__ tile_first,
+                                                    uint32_t* __restrict__ bucket_trivial,
+                                                    uint32_t* __restrict__ skip, int passA,
+                                                    int64_t n) {
+  constexpr int PER = BINS / 1024 > 0 ? BINS / 1024 : 1;  // digits per thread
+  constexpr int NB = BINS / 256;
+  static_assert(BINS >= 256 && BINS % 256 == 0 && NB <= kMaxBuckets, "buckets of 256 digits");
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_len[NB];
+  __shared__ uint32_t s_flags[2];
+  const int t = threadIdx.x;
+  if (t < 2) s_flags[t] = 0;
+  uint32_t local = 0;
+  if (t * PER < BINS)
+    for (int j = 0; j < PER; ++j) local += hist[t * PER + j];
+  uint32_t total;
+  uint32_t run = block_exclusive_scan<1024>(local, s_warp, total);
+  if (t * PER < BINS)
+    for (int j = 0; j < PER; ++j) {
+      base[t * PER + j] = run;
+      run += hist[t * PER + j];
+    }
+  __syncthreads();  // base complete
+  if (t < NB) {
+    const uint32_t start = base[t * 256];
+    const uint32_t len = (t + 1 < NB ? base[(t + 1) * 256] : (uint32_t)n) - start;
+    uint32_t mx = 0;
+    for (int l = 0; l < 256; ++l) mx = max(mx, hist[t * 256 + l]);
+    s_len[t] = len;
+    baseA[t] = start;
+    bucket_trivial[t] = len > 0 && mx == len;
+    if ((int64_t)len == n) s_flags[0] = 1;     // step A is the identity
+    if (len > 0 && mx != len) s_flags[1] = 1;  // some bucket needs step B
+  }
+  __syncthreads();
+  if (t < 32) {  // tiles per bucket and their exclusive prefix
+    constexpr int BPL = (NB + 31) / 32;  // buckets per lane
+    uint32_t tiles[BPL], sum = 0;
+#pragma unroll
+    for (int j = 0; j < BPL; ++j) {
+      const int h = t * BPL + j;
+      tiles[j] = h < NB ? (s_len[h] + TILE - 1) / TILE : 0u;
+      sum += tiles[j];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFullMask, incl, o);
+      if (t >= o) incl += y;
+    }
+    uint32_t first = incl - sum;
+#pragma unroll
+    for (int j = 0; j < BPL; ++j) {
+      const int h = t * BPL + j;
+      if (h < NB) tile_first[h] = first;
+      first += tiles[j];
+    }
+    if (t == 31) tile_first[NB] = first;
+  }
+  if (t == 0) {
+    skip[passA] = s_flags[0];
+    skip[passA + 1] = s_flags[1] ? 0u : 1u;
+  }
+}
+
+// Step B: an ordered radix-256 round by the low byte (bits [p.shift, p.shift
+// + 8)) inside every bucket. Tile ids come in launch order; tile t belongs to
+// the bucket h with tile_first[h] <= t < tile_first[h + 1], and the look-back
+// never leaves the bucket (its first tile publishes inclusive counts).
+// Positions are absolute: the digit bases are base[h*256 + l].
+template <typename K, typename V, int THREADS, int KPT, int MINB, int NB, typename DS>
+__global__ void __launch_bounds__(THREADS, MINB)
+    k_bucket(PassParams p, const uint32_t* __restrict__ base,
+             const uint32_t* __restrict__ tile_first,
+             const uint32_t* __restrict__ bucket_trivial) {
+  using S = OnesweepShape<K, V, 8, THREADS, KPT>;
+  constexpr int R = S::R, WARPS = S::WARPS, TILE = S::TILE;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* s_misc = s_wcnt + WARPS * R + R;
+  const int tid = threadIdx.x;
+  if (p.skip[p.pass]) return;  // every bucket's low byte is constant: identity
+  const int src = parity_of(p.skip, p.pass);
+  if (tid == 0) s_misc[0] = atomicAdd(p.counter, 1u);
+  zero_words<THREADS>(s_wcnt, WARPS * R);
+  __syncthreads();
+  const uint32_t tile = s_misc[0];
+  if (tile >= tile_first[NB]) return;  // more CTAs than tiles
+  int lo = 0, hi = NB - 1;  // the last bucket whose first tile is <= tile
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile_first[mid] <= tile) lo = mid; else hi = mid - 1;
+  }
+  const int h = lo;
+  const int64_t start = base[h * 256];
+  const int64_t end = h + 1 < NB ? (int64_t)base[(h + 1) * 256] : p.n;
+  const int64_t lt = (int64_t)tile - tile_first[h];
+  const int64_t tile_base = start + lt * TILE;
+  const int tile_n = (int)min((int64_t)TILE, end - tile_base);
+  const K* kin = static_cast<const K*>(src ? p.keys[1] : p.keys[0]);
+  K* kout = static_cast<K*>(src ? p.keys[0] : p.keys[1]);
+  const V* vin = static_cast<const V*>(src ? p.vals[1] : p.vals[0]);
+  V* vout = static_cast<V*>(src ? p.vals[0] : p.vals[1]);
+  if (bucket_trivial[h]) {  // the bucket's low byte is constant: it stays in order
+    for (int j = tid; j < tile_n; j += THREADS) {
+      kout[tile_base + j] = kin[tile_base + j];
+      if constexpr (HasVal<V>::value) vout[tile_base + j] = vin[tile_base + j];
+    }
+    return;
+  }
+  if (tile_n == TILE)
+    onesweep_tile_ordered<K, V, 8, THREADS, KPT, true, DS>(p, tile, lt == 0, tile_base, tile_n,
+                                                           kin, kout, vin, vout, base + h * 256,
+                                                           (uint32_t)p.n, smem);
+  else
+    onesweep_tile_ordered<K, V, 8, THREADS, KPT, false, DS>(p, tile, lt == 0, tile_base, tile_n,
+                                                            kin, kout, vin, vout, base + h * 256,
+                                                            (uint32_t)p.n, smem);
+}
+
+// Scratch of the rounds inside the workspace: hist holds the 2^W counts, then
+// baseA[256], tile_first[257] (padded to 512) and bucket_trivial[256]; base
+// holds the prefix; status[0] the look-back rows of step A, status[1] those of
+// step B.
+struct WideScratch {
+  uint32_t *hist, *baseA, *tile_first, *bucket_trivial, *base;
+};
+
+// One round with a W-bit digit at `shift` (kernel passes 2q and 2q + 1).
+// Byte-aligned digit parts (W = 16) use the byte-permute digit rule.
+template <typename K, typename V, int THREADS, int KPT, int MINB, int W>
+cudaError_t wide_round(const LsdArgs& a, PassParams& pp, const WideScratch& w, int q, int shift,
+                       int64_t tiles, cudaStream_t st) {
+  constexpr int BINS = 1 << W, NB = BINS / 256, TILE = THREADS * KPT;
+  constexpr bool BYTES = W == 16;
+  using DS = typename std::conditional<BYTES, RadixDigit, ShiftMaskDigit>::type;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * BINS, st))) return e;
+  if constexpr (W == 16) {
+    constexpr size_t HSMEM = sizeof(uint32_t) * kHalf16;
+    if ((e = cudaFuncSetAttribute(k_hist16<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)HSMEM)))
+      return e;
+    const int grid = std::max(2, (a.num_sms / 2) * 2);  // pairs of CTAs, one CTA per SM
+    timer_begin(a.timer, "k_hist16", st);
+    k_hist16<K><<<grid, kHistThreads, HSMEM, st>>>(static_cast<const K*>(a.keys),
+                                                     static_cast<const K*>(a.alt_keys), a.skip,
+                                                     2 * q, a.n, shift, w.hist);
+  } else {
+    constexpr size_t HSMEM = sizeof(uint32_t) * 8 * BINS;
+    if ((e = cudaFuncSetAttribute(k_hist_small<K, BINS>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HSMEM)))
+      return e;
+    timer_begin(a.timer, "k_hist_wide", st);
+    k_hist_small<K, BINS><<<a.num_sms * (HSMEM <= 64 * 1024 ? 2 : 1), kHistThreads, HSMEM, st>>>(
+        static_cast<const K*>(a.keys), static_cast<const K*>(a.alt_keys), a.skip, 2 * q, a.n,
+        shift, (uint32_t)(BINS - 1), w.hist);
+  }
+  timer_end(a.timer, st);
+  timer_begin(a.timer, "k_scan_wide", st);
+  k_scan_wide<BINS, TILE><<<1, 1024, 0, st>>>(w.hist, w.base, w.baseA, w.tile_first,
+                                              w.bucket_trivial, a.skip, 2 * q, a.n);
+  timer_end(a.timer, st);
+  if ((e = cudaMemsetAsync(a.status[0], 0, sizeof(uint32_t) * 256 * tiles, st))) return e;
+  if ((e = cudaMemsetAsync(a.status[1], 0, sizeof(uint32_t) * 256 * (tiles + NB), st)))
+    return e;
+  constexpr size_t smem = OrderedShape<K, V, 8, THREADS, KPT>::SMEM;
+  auto kA = k_onesweep<K, V, 8, THREADS, KPT, MINB, DS>;
+  auto kB = k_bucket<K, V, THREADS, KPT, MINB, NB, DS>;
+  if (smem > 48 * 1024) {
+    if ((e = cudaFuncSetAttribute(kA, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+      return e;
+    if ((e = cudaFuncSetAttribute(kB, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+      return e;
+  }
+  // step A: the high W - 8 bits, over all keys (the input is sorted by bits [0, shift))
+  pp.pass = 2 * q;
+  pp.shift = shift + 8;
+  pp.mask = (uint32_t)(NB - 1);
+  pp.byte_sel = radix8_byte_sel(shift + 8);
+  pp.low_shift = shift;
+  pp.base = w.baseA;
+  pp.status = a.status[0];
+  pp.counter = a.counters + 2 * q;
+  timer_begin(a.timer, "k_wide_high", st);
+  kA<<<(unsigned)tiles, THREADS, smem, st>>>(pp);
+  timer_end(a.timer, st);
+  // step B: the low byte, inside every bucket
+  pp.pass = 2 * q + 1;
+  pp.shift = shift;
+  pp.mask = 0xffu;
+  pp.byte_sel = radix8_byte_sel(shift);
+  pp.low_shift = shift;
+  pp.base = nullptr;
+  pp.status = a.status[1];
+  pp.counter = a.counters + 2 * q + 1;
+  timer_begin(a.timer, "k_wide_low", st);
+  kB<<<(unsigned)(tiles + NB), THREADS, smem, st>>>(pp, w.base, w.tile_first, w.bucket_trivial);
+  timer_end(a.timer, st);
+  return cudaSuccess;
+}
+
+}  // namespace
+
+// One whole sort at radix 2^BITS (BITS = 16 or 11): round q takes the digit of
+// width W = min(BITS, key bits - BITS*q) at shift BITS*q; kernel passes 2q
+// (step A) and 2q + 1 (step B) share the skip and tile-counter arrays, so the
+// buffer parity follows the executed passes.
+template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB>
+cudaError_t wide_launch(const LsdArgs& a, cudaStream_t st) {
+  constexpr int KB = 8 * (int)sizeof(K), ROUNDS = (KB + BITS - 1) / BITS, P2 = 2 * ROUNDS;
+  constexpr int TILE = THREADS * KPT;
+  const int64_t tiles = (a.n + TILE - 1) / TILE;
+  WideScratch w;
+  w.hist = a.hist;
+  w.baseA = a.hist + (1 << BITS);
+  w.tile_first = w.baseA + 256;
+  w.bucket_trivial = w.tile_first + 512;
+  w.base = a.base;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(a.counters, 0, sizeof(uint32_t) * P2, st))) return e;
+  PassParams pp;
+  pp.keys[0] = a.keys;
+  pp.keys[1] = a.alt_keys;
+  pp.vals[0] = a.vals;
+  pp.vals[1] = a.alt_vals;
+  pp.n = a.n;
+  pp.skip = a.skip;
+  pp.err = a.err;
+  pp.spin_limit = a.spin_limit;
+  pp.stall_tile = -1;
+  pp.trace = nullptr;
+  pp.prefetch_tiles = a.prefetch_tiles;
+  pp.check_mode = a.check_mode;
+  pp.status_next = nullptr;
+  for (int q = 0; q < ROUNDS; ++q) {
+    const int shift = BITS * q;
+    const int width = KB - shift < BITS ? KB - shift : BITS;
+    switch (width) {
+      case 16: e = wide_round<K, V, THREADS, KPT, MINB, 16>(a, pp, w, q, shift, tiles, st); break;
+      case 11: e = wide_round<K, V, THREADS, KPT, MINB, 11>(a, pp, w, q, shift, tiles, st); break;
+      case 10: e = wide_round<K, V, THREADS, KPT, MINB, 10>(a, pp, w, q, shift, tiles, st); break;
+      case 9: e = wide_round<K, V, THREADS, KPT, MINB, 9>(a, pp, w, q, shift, tiles, st); break;
+      default: return cudaErrorInvalidValue;
+    }
+    if (e) return e;
+  }
+  const int cblocks = (int)std::min<int64_t>((a.n + 255) / 256, (int64_t)a.num_sms * 8);
+  timer_begin(a.timer, "k_copy_back", st);
+  k_copy_back<K, V><<<cblocks, 256, 0, st>>>(a.skip, P2, static_cast<K*>(a.keys),
+                                             static_cast<const K*>(a.alt_keys),
+                                             static_cast<V*>(a.vals),
+                                             static_cast<const V*>(a.alt_vals), a.n);
+  timer_end(a.timer, st);
+  return cudaGetLastError();
+}
+
+template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB>
+constexpr LsdEntry wide_entry() {
+  constexpr int KB = 8 * (int)sizeof(K);
+  LsdEntry e{KB,
+             HasVal<V>::value ? (int)(8 * sizeof(V)) : 0,
+             BITS,
+             THREADS,
+             KPT,
+             (int64_t)THREADS * KPT,
+             1 << BITS,                     // hist and base: 2^BITS words per kernel pass
+             2 * ((KB + BITS - 1) / BITS),  // kernel passes: two steps per round
+             256,                           // look-back words per tile
+             2,
+             &wide_launch<K, V, BITS, THREADS, KPT, MINB>};
+  e.extra_status_rows = kMaxBuckets;  // step B: at most one partial tile per bucket
+  return e;
+}
+
+// Shapes of the radix-256 defaults for each (key, payload) width.
+#define ISORT_WIDE_TABLES(B)                                                              \
+  static const LsdEntry kW##B##None32[] = {wide_entry<uint32_t, NoVal, B, 256, 32, 3>()};   \
+  static const LsdEntry kW##B##V32_32[] = {wide_entry<uint32_t, uint32_t, B, 256, 20, 3>()}; \
+  static const LsdEntry kW##B##V64_32[] = {wide_entry<uint32_t, uint64_t, B, 256, 16, 2>()}; \
+  static const LsdEntry kW##B##None64[] = {wide_entry<uint64_t, NoVal, B, 256, 20, 3>()};   \
+  static const LsdEntry kW##B##V32_64[] = {wide_entry<uint64_t, uint32_t, B, 256, 16, 2>()}; \
+  static const LsdEntry kW##B##V64_64[] = {wide_entry<uint64_t, uint64_t, B, 256, 12, 2>()};
+ISORT_WIDE_TABLES(16)
+ISORT_WIDE_TABLES(11)
+#undef ISORT_WIDE_TABLES
+
+int wide_variants(int key_bits, int val_bits, int radix_bits, const LsdEntry** out) {
+  if (key_bits != 32 && key_bits != 64) return 0;
+  if (val_bits != 0 && val_bits != 32 && val_bits != 64) return 0;
+  const int ki = key_bits == 32 ? 0 : 1, vi = val_bits == 0 ? 0 : val_bits == 32 ? 1 : 2;
+  const LsdEntry* t16[2][3] = {{kW16None32, kW16V32_32, kW16V64_32},
+                               {kW16None64, kW16V32_64, kW16V64_64}};
+  const LsdEntry* t11[2][3] = {{kW11None32, kW11V32_32, kW11V64_32},
+                               {kW11None64, kW11V32_64, kW11V64_64}};
+  if (radix_bits == 16)
+    *out = t16[ki][vi];
+  else if (radix_bits == 11)
+    *out = t11[ki][vi];
+  else
+    return 0;
+  return 1;
+}
+
+}  // namespace isort

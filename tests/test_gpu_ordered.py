@@ -64,13 +64,14 @@ def test_segmented_every_check_mode(check_mode, mode):
 
 
 @pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("radix_bits", [16, 11])
 @pytest.mark.parametrize("key_bits,val_bits", [(32, 0), (32, 32), (64, 0)])
 @pytest.mark.parametrize("dist", ["uniform", "and4", "u16", "sorted"])
-def test_radix65536_every_check_mode(check_mode, mode, key_bits, val_bits, dist):
-    """Radix 65536 routes each round in two ordered steps (high byte over all
-    keys, checked against the bits below the 16-bit digit; low byte inside
-    every bucket); both steps must survive a forced fallback and perturbed
-    ranks."""
+def test_wide_radix_every_check_mode(check_mode, mode, radix_bits, key_bits, val_bits, dist):
+    """Radix 65536 and 2048 route each round in two ordered steps (the high
+    part of the digit over all keys, checked against the bits below the whole
+    digit; the low byte inside every bucket); both steps must survive a forced
+    fallback and perturbed ranks."""
     n = 400_003
     k = inputs.keys(n, key_bits, dist, seed=15)
     check_mode(mode)
@@ -78,13 +79,13 @@ def test_radix65536_every_check_mode(check_mode, mode, key_bits, val_bits, dist)
     if val_bits:
         v = inputs.iota(n, val_bits)
         dv = torch.from_numpy(v).cuda()
-        isort.sort_pairs(d, dv, 16)
-        ok, ov = oracle.radix_sort(k, v, radix_bits=16)
+        isort.sort_pairs(d, dv, radix_bits)
+        ok, ov = oracle.radix_sort(k, v, radix_bits=radix_bits)
         assert isort.stream_status() == _lib.OK
         assert np.array_equal(dv.cpu().numpy(), ov)
     else:
-        isort.sort_keys(d, 16)
-        ok = _oracle(k)
+        isort.sort_keys(d, radix_bits)
+        ok = oracle.radix_sort(k, radix_bits=radix_bits)
         assert isort.stream_status() == _lib.OK
     assert np.array_equal(d.cpu().numpy(), ok)
 

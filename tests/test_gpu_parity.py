@@ -199,7 +199,7 @@ def test_radix65536_edge_sizes():
         assert np.array_equal(gv, ov), n
 
 
-R11_BLOCK = 1 << 16  # keys per count-matrix row of the radix-2048 path
+R11_BLOCK = 1 << 16  # a size scale of the radix-2048 tests (tiles, buckets, ragged ends)
 
 
 @pytest.mark.parametrize("key_bits", [32, 64])
