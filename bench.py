@@ -903,7 +903,7 @@ def run_mbsp(a):
             kt = isort.kernel_times()
             if i >= a.warmup:
                 ms.append(e0.elapsed_time(e1))
-                # the last round: stable in every warp (earlier keys-only rounds may relax)
+                # the last ordered round of the sort
                 rounds_ms += [t for k, t in kt if k == "k_onesweep"][-1:]
                 launches += len(kt)
         if isort.stream_status() != _lib.OK:
@@ -937,7 +937,7 @@ def run_mbsp(a):
                    "l2": "inputs larger than L2; restored and L2 flushed before each sort"},
         "calibration": {"hbm_gbs": peak, "peak_kind": peak_kind, "g_s_per_word": g,
                         "G_s_per_access": G, "g_over_G": cal["g_over_G"],
-                        "shared_accesses_per_key_round": mbsp.SHARED_ACCESSES_ONESWEEP,
+                        "shared_accesses_per_key_round": mbsp.SHARED_ACCESSES_ORDERED,
                         "onesweep_round_ms": base["round_ms"]},
         "predictions": rows,
         "gpu_launches": launches,

@@ -15,14 +15,13 @@ per worker, radix r, 32 / lg r rounds):
                 n_max = (1 + 1/ceil(w)) n/p + ceil(w) p    Theorem 1 (GSD)
 
 On the GPU the worker of a round is a tile (one CTA), the main memory is HBM
-and the fast memory is shared memory. A round of this library moves each key
-(and payload) once in and once out of HBM -- the upfront histogram and the
-decoupled look-back replace the paper's second read -- and touches shared
-memory a fixed number of times per key; the wide radixes keep the paper's
-count-sort structure (two reads, one write) and its 2prg count-matrix exchange
-with p = count-matrix blocks. gpu_* below give those costs in the same (g, G)
-currency; calibrate() derives g from a measured copy bandwidth and G from one
-measured round, and predict() turns the model into times for other rounds.
+and the fast memory is shared memory. A radix-256 round of this library moves
+each key (and payload) once in and once out of HBM -- the upfront histogram
+and the decoupled look-back replace the paper's second read -- and touches
+shared memory a fixed number of times per key; a wide-radix round reads the
+keys for its digit histogram and then routes them in two such rounds. gpu_*
+below give those costs in the same (g, G) currency; calibrate() derives g from
+a measured copy bandwidth and G from one measured round.
 
 Host-side arithmetic only: nothing here launches GPU work.
 """
@@ -81,22 +80,20 @@ def speedup_bound_gsd(p: int) -> float:
 
 
 # ---- the same accounting for this library's rounds --------------------------
-# Shared-memory word accesses per key of one radix-256 round (early counts):
-# count, mark, mask read, counter update (by one lane per digit group, counted
-# per key), key store, mask clear, staged read, offset read.
-SHARED_ACCESSES_ONESWEEP = 8
-# The first round of a keys-only sort keeps no order among equal digits:
-# count add, slot add (its return value is the tile slot), key store, staged
-# read, offset read.
+# Shared-memory accesses per key of one ordered round (keys only): count add,
+# slot add (its return value is the key's tile slot), key store, staged read,
+# digit-offset read, and the check's read of the next staged key.
+SHARED_ACCESSES_ORDERED = 6
+# With payloads, in addition: the input-index store and read, the check's read
+# of the next index, the payload's copy into shared memory and its gather.
+SHARED_ACCESSES_PAYLOAD = 5
+# The first round of a keys-only sort keeps no order among equal digits and
+# is not checked: count add, slot add, key store, staged read, offset read.
 SHARED_ACCESSES_FIRST = 5
-# Per key of a wide-radix scatter: two stable 8-bit partitions (mark, mask read,
-# counter, store of key and index each), the run pass (read key and index, run
-# edges) and the offset update.
-SHARED_ACCESSES_WIDE = 16
 
 
 def gpu_onesweep_round(n: float, words_per_item: float, g: float, G: float,
-                       shared: float = SHARED_ACCESSES_ONESWEEP) -> float:
+                       shared: float = SHARED_ACCESSES_ORDERED) -> float:
     """One radix-256 round: one read and one write of every key (and payload)
     word in HBM, `shared` shared-memory accesses per key."""
     return 2 * n * words_per_item * g + shared * n * G
@@ -108,50 +105,33 @@ def gpu_histogram(n: float, key_words: float, passes: int, g: float, G: float) -
 
 
 def gpu_wide_round(n: float, words_per_item: float, key_words: float, g: float, G: float,
-                   r: int, blocks: int, shared: float = SHARED_ACCESSES_WIDE) -> float:
-    """One wide-radix round: the count read (n key words + one shared add per
-    key), the count-matrix exchange 2 * blocks * r words (the paper's 2prg), and
-    the scatter (read and write every item, `shared` accesses per key)."""
-    return (n * key_words * g + n * G + 2 * blocks * r * g +
-            2 * n * words_per_item * g + shared * n * G)
+                   shared: float = SHARED_ACCESSES_ORDERED) -> float:
+    """One wide-radix round: the digit histogram (a read of the keys, one shared
+    add per key) and its two routing steps (high part over all keys, low byte
+    inside each bucket), each an ordered round that reads and writes every item.
+    The paper's count exchange (2prg) is the steps' look-back, not charged, as
+    for radix 256."""
+    return n * key_words * g + n * G + 2 * gpu_onesweep_round(n, words_per_item, g, G, shared)
 
 
-def relaxed_share(n: float, j: int, radix_bits: int = 8, warp_keys: int = 1024) -> float:
-    """Keys only, uniform keys: the share of warps of round j that place keys
-    in any order. Round 0 is order-free; round j >= 1 reads input sorted by the
-    j*radix_bits low bits, which come in runs of n / 2^(j*radix_bits) equal
-    values, and a warp of warp_keys consecutive keys relaxes when no run ends
-    inside it."""
-    if j == 0:
-        return 1.0
-    run = n / 2.0 ** (radix_bits * j)
-    return max(0.0, 1.0 - (warp_keys - 1) / run) if run >= warp_keys else 0.0
-
-
-def gpu_sort(n: float, key_bits: int, val_bits: int, r: int, g: float, G: float,
-             block_keys: int | None = None) -> float:
+def gpu_sort(n: float, key_bits: int, val_bits: int, r: int, g: float, G: float) -> float:
     """Model time of one whole sort of n keys at radix r (all rounds executed).
-    Keys only at radix 256: the first round is order-free, and for 32-bit
-    keys the warps of later rounds that share their low bits (relaxed_share,
-    uniform keys) cost what the order-free round costs."""
+    Keys only at radix 256, the first round is the order-free one."""
     kw = key_bits / 32
     w = kw + val_bits / 32
     P = rounds(key_bits, r)
+    shared = SHARED_ACCESSES_ORDERED + (SHARED_ACCESSES_PAYLOAD if val_bits else 0)
     if r == 256:
         t = gpu_histogram(n, kw, P, g, G)
         for j in range(P):
-            f = 0.0
-            if val_bits == 0 and (j == 0 or key_bits == 32):
-                f = relaxed_share(n, j)
-            shared = f * SHARED_ACCESSES_FIRST + (1 - f) * SHARED_ACCESSES_ONESWEEP
-            t += gpu_onesweep_round(n, w, g, G, shared)
+            first = j == 0 and val_bits == 0
+            t += gpu_onesweep_round(n, w, g, G, SHARED_ACCESSES_FIRST if first else shared)
         return t
-    blocks = -(-int(n) // (block_keys or (1 << 19 if r == 65536 else 1 << 16)))
-    return P * gpu_wide_round(n, w, kw, g, G, r, blocks)
+    return P * gpu_wide_round(n, w, kw, g, G, shared)
 
 
 def calibrate(hbm_gbs: float, onesweep_round_s: float, n: float, words_per_item: float = 1.0,
-              shared: float = SHARED_ACCESSES_ONESWEEP) -> dict:
+              shared: float = SHARED_ACCESSES_ORDERED) -> dict:
     """g from the measured copy bandwidth (seconds per 4-byte word, whole GPU);
     G from one measured radix-256 round, charging it the paper's additive cost
     2 n w g + shared n G. Returns {"g": g, "G": G, "g_over_G": g / G}."""

@@ -74,10 +74,10 @@ def test_rounds_and_gpu_accounting():
     # with free shared memory a radix-256 round costs its algorithmic HBM bytes
     assert mbsp.gpu_onesweep_round(n, 1, gg, 0.0) == pytest.approx(2 * n * 4 / 6784e9)
     assert mbsp.gpu_onesweep_round(n, 2, gg, 0.0) == pytest.approx(2 * n * 8 / 6784e9)
-    # the wide round's exchange term is the paper's 2prg with p = count-matrix blocks
-    base = mbsp.gpu_wide_round(n, 1, 1, gg, 0.0, 2048, 0)
-    assert mbsp.gpu_wide_round(n, 1, 1, gg, 0.0, 2048, 4096) - base == pytest.approx(
-        2 * 4096 * 2048 * gg)
+    # a wide round: its histogram read and two routing steps (3 reads, 2 writes)
+    assert mbsp.gpu_wide_round(n, 1, 1, gg, 0.0) == pytest.approx(5 * n * gg)
+    assert mbsp.gpu_sort(n, 32, 0, 65536, gg, 0.0) == pytest.approx(10 * n * gg)
+    assert mbsp.gpu_sort(n, 32, 0, 2048, gg, 0.0) == pytest.approx(15 * n * gg)
     # a whole radix-256 sort: histogram read + 4 rounds
     assert mbsp.gpu_sort(n, 32, 0, 256, gg, 0.0) == pytest.approx(9 * n * gg)
 
@@ -99,33 +99,15 @@ def test_network_ratio_limits():
     assert mbsp.network_time_ratio(64, 1.0) == pytest.approx(1.0)
 
 
-def test_gpu_sort_keys_only_first_round_is_cheaper_by_three_shared_accesses():
-    """Keys only at radix 256: the order-free first round saves the mark, the
-    mask read and the mask clear (3 shared accesses per key); pairs do not.
-    At 2^16 keys no warp of a later round shares its low bits (runs of 256
-    keys in round 1), so only round 0 is cheaper."""
-    n, g, G = 1 << 16, 2.0, 1.0
-    stable = mbsp.gpu_histogram(n, 1, 4, g, G) + 4 * mbsp.gpu_onesweep_round(n, 1, g, G)
-    assert mbsp.gpu_sort(n, 32, 0, 256, g, G) == pytest.approx(stable - 3 * n * G)
-    pairs = mbsp.gpu_histogram(n, 1, 4, g, G) + 4 * mbsp.gpu_onesweep_round(n, 2, g, G)
+def test_gpu_sort_ordered_rounds():
+    """Keys only at radix 256: the order-free first round saves the check's
+    read (5 shared accesses per key against 6); pairs run the ordered round
+    with the index and payload accesses (11) in every round."""
+    n, g, G = 1 << 20, 2.0, 1.0
+    ordered = mbsp.gpu_histogram(n, 1, 4, g, G) + 4 * mbsp.gpu_onesweep_round(n, 1, g, G)
+    assert mbsp.gpu_sort(n, 32, 0, 256, g, G) == pytest.approx(ordered - n * G)
+    pairs = mbsp.gpu_histogram(n, 1, 4, g, G) + 4 * mbsp.gpu_onesweep_round(n, 2, g, G, 11)
     assert mbsp.gpu_sort(n, 32, 32, 256, g, G) == pytest.approx(pairs)
-
-
-def test_relaxed_share_of_warps():
-    """Round 0 is order-free; at 2^28 uniform keys the low byte comes in runs
-    of 2^20 keys (almost every 1024-key warp inside one), the low 16 bits in
-    runs of 4096 (three warps in four), the low 24 bits in runs of 16 (none)."""
-    n = 1 << 28
-    assert mbsp.relaxed_share(n, 0) == 1.0
-    assert mbsp.relaxed_share(n, 1) == pytest.approx(1 - 1023 / 2**20)
-    assert mbsp.relaxed_share(n, 2) == pytest.approx(1 - 1023 / 4096)
-    assert mbsp.relaxed_share(n, 3) == 0.0
-    # 64-bit keys keep the stable rank after round 0; 32-bit keys relax
-    g, G = 2.0, 1.0
-    t32 = mbsp.gpu_sort(n, 32, 0, 256, g, G)
-    full = mbsp.gpu_histogram(n, 1, 4, g, G) + 4 * mbsp.gpu_onesweep_round(n, 1, g, G)
-    saved = 3 * n * G * (1 + mbsp.relaxed_share(n, 1) + mbsp.relaxed_share(n, 2))
-    assert t32 == pytest.approx(full - saved)
     t64 = mbsp.gpu_sort(n, 64, 0, 256, g, G)
-    full64 = mbsp.gpu_histogram(n, 2, 8, g, G) + 8 * mbsp.gpu_onesweep_round(n, 2, g, G)
-    assert t64 == pytest.approx(full64 - 3 * n * G)
+    assert t64 == pytest.approx(mbsp.gpu_histogram(n, 2, 8, g, G) +
+                                8 * mbsp.gpu_onesweep_round(n, 2, g, G) - n * G)
