@@ -449,15 +449,15 @@ def run_ours(a):
         raise RuntimeError("benchmark result is not sorted")
     del sk
 
-    # dominant kernel: the onesweep pass (radix 256), a routing step of a
-    # radix-65536 round, or the radix-2048 scatter
+    # dominant kernel: the onesweep pass (radix 256) or a routing step of a
+    # wide-radix round
     dom = max(kernel_ms, key=lambda k: sum(kernel_ms[k]))
     dom_ms = statistics.mean(kernel_ms[dom])
     bytes_per_key = (kb + vb) // 8
     # GVR: the split round, then the radix rounds; GSD: the radix rounds, then lg 16 merge rounds
     passes = -(-kb // rb) + (1 if gvr else 0) + (4 if gsd else 0)
-    if dom in ("k_onesweep", "k_pr2_high", "k_pr2_low", "k_scatter11", "k_seg_onesweep",
-               "k_gvr_split", "k_gsd_merge"):
+    if dom in ("k_onesweep", "k_wide_high", "k_wide_low", "k_seg_onesweep", "k_gvr_split",
+               "k_gsd_merge"):
         # one count-sort round: read and write every key (and payload) once
         alg_bytes = 2 * n * bytes_per_key
     else:
@@ -477,14 +477,15 @@ def run_ours(a):
                                    "achieved": alg_bytes / (f_ms / 1000.0) / 1e9,
                                    "frac": alg_bytes / (f_ms / 1000.0) / 1e9 / peak,
                                    "launches": len(kernel_ms[first])}
-    if "k_pr2_high" in kernel_ms:
-        # a radix-65536 round = histogram + scan + the two routing steps; its
+    if "k_wide_high" in kernel_ms:
+        # a wide-radix round = histogram + scan + the two routing steps; its
         # algorithmic bytes are one read and one write of every key
-        r_ms = sum(statistics.mean(kernel_ms[k]) for k in
-                   ("k_hist16", "k_scan16", "k_pr2_high", "k_pr2_low") if k in kernel_ms)
+        parts = [k for k in ("k_hist16", "k_hist_wide", "k_scan_wide", "k_wide_high", "k_wide_low")
+                 if k in kernel_ms]
+        r_ms = sum(statistics.mean(kernel_ms[k]) for k in parts)
         rb_bytes = 2 * n * bytes_per_key
-        roofline["round"] = {"kernels": "k_hist16 + k_scan16 + k_pr2_high + k_pr2_low",
-                             "avg_round_ms": r_ms, "achieved": rb_bytes / (r_ms / 1000.0) / 1e9,
+        roofline["round"] = {"kernels": " + ".join(parts), "avg_round_ms": r_ms,
+                             "achieved": rb_bytes / (r_ms / 1000.0) / 1e9,
                              "frac": rb_bytes / (r_ms / 1000.0) / 1e9 / peak}
     # whole-sort roofline by the headline formula: 2 n (w_k + w_v) per executed pass
     sort_alg_bytes = 2 * n * bytes_per_key * passes

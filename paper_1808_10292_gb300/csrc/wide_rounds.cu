@@ -134,27 +134,81 @@ __global__ void __launch_bounds__(1024) k_scan_wide(const uint32_t* __restrict__
   __shared__ uint32_t s_flags[2];
   const int t = threadIdx.x;
   if (t < 2) s_flags[t] = 0;
-  uint32_t local = 0;
-  if (t * PER < BINS)
-    for (int j = 0; j < PER; ++j) local += hist[t * PER + j];
+  // thread t owns digits [t*PER, t*PER + PER): their sum and largest count,
+  // then their exclusive prefixes (16-byte loads and stores where PER allows)
+  uint32_t local = 0, mx = 0;
+  if (t * PER < BINS) {
+    if constexpr (PER % 4 == 0) {
+      const uint4* h4 = reinterpret_cast<const uint4*>(hist + t * PER);
+#pragma unroll 4
+      for (int j = 0; j < PER / 4; ++j) {
+        const uint4 v = h4[j];
+        local += v.x + v.y + v.z + v.w;
+        mx = max(max(mx, max(v.x, v.y)), max(v.z, v.w));
+      }
+    } else {
+      for (int j = 0; j < PER; ++j) {
+        const uint32_t c = hist[t * PER + j];
+        local += c;
+        mx = max(mx, c);
+      }
+    }
+  }
   uint32_t total;
   uint32_t run = block_exclusive_scan<1024>(local, s_warp, total);
-  if (t * PER < BINS)
-    for (int j = 0; j < PER; ++j) {
-      base[t * PER + j] = run;
-      run += hist[t * PER + j];
+  const uint32_t my_start = run;  // base of this thread's first digit
+  if (t * PER < BINS) {
+    if constexpr (PER % 4 == 0) {
+      const uint4* h4 = reinterpret_cast<const uint4*>(hist + t * PER);
+      uint4* b4 = reinterpret_cast<uint4*>(base + t * PER);
+#pragma unroll 4
+      for (int j = 0; j < PER / 4; ++j) {
+        const uint4 v = h4[j];
+        uint4 o;
+        o.x = run;
+        o.y = o.x + v.x;
+        o.z = o.y + v.y;
+        o.w = o.z + v.z;
+        run = o.w + v.w;
+        b4[j] = o;
+      }
+    } else {
+      for (int j = 0; j < PER; ++j) {
+        base[t * PER + j] = run;
+        run += hist[t * PER + j];
+      }
     }
-  __syncthreads();  // base complete
-  if (t < NB) {
-    const uint32_t start = base[t * 256];
-    const uint32_t len = (t + 1 < NB ? base[(t + 1) * 256] : (uint32_t)n) - start;
-    uint32_t mx = 0;
-    for (int l = 0; l < 256; ++l) mx = max(mx, hist[t * 256 + l]);
-    s_len[t] = len;
-    baseA[t] = start;
-    bucket_trivial[t] = len > 0 && mx == len;
-    if ((int64_t)len == n) s_flags[0] = 1;     // step A is the identity
-    if (len > 0 && mx != len) s_flags[1] = 1;  // some bucket needs step B
+  }
+  // per bucket (256 digits = TPB threads): start, length, largest digit count
+  constexpr int TPB = 256 / PER;
+  uint32_t blen = local, bmax = mx;
+#pragma unroll
+  for (int o = 1; o < TPB && o < 32; o <<= 1) {
+    blen += __shfl_xor_sync(kFullMask, blen, o);
+    bmax = max(bmax, __shfl_xor_sync(kFullMask, bmax, o));
+  }
+  if constexpr (TPB > 32) {  // buckets wider than a warp: combine the warps' results
+    __shared__ uint32_t s_part[2][32];
+    if ((t & 31) == 0) {
+      s_part[0][t >> 5] = blen;
+      s_part[1][t >> 5] = bmax;
+    }
+    __syncthreads();
+    if (t % TPB == 0) {
+      blen = 0, bmax = 0;
+      for (int w = 0; w < TPB / 32; ++w) {
+        blen += s_part[0][t / 32 + w];
+        bmax = max(bmax, s_part[1][t / 32 + w]);
+      }
+    }
+  }
+  if (t % TPB == 0 && t * PER < BINS) {
+    const int h = t / TPB;
+    s_len[h] = blen;
+    baseA[h] = my_start;  // the bucket's first digit is this thread's first
+    bucket_trivial[h] = blen > 0 && bmax == blen;
+    if ((int64_t)blen == n) s_flags[0] = 1;      // step A is the identity
+    if (blen > 0 && bmax != blen) s_flags[1] = 1;  // some bucket needs step B
   }
   __syncthreads();
   if (t < 32) {  // tiles per bucket and their exclusive prefix
