@@ -174,8 +174,14 @@ __global__ void __launch_bounds__(CTA) k_seg_btn(K* __restrict__ keys, V* __rest
 // ---------------------------------------------------------------------------
 // Digit histograms of the radix ranges: CTA c walks a contiguous run of tiles,
 // counting into shared memory and flushing into seg_hist when the range
-// changes. The counters are laid out as k_hist's, [p][d][lane % LANES], so one
-// warp's atomics fall in different banks; keys are read as 16-byte vectors.
+// changes. Long spans count into counters laid out as k_hist's, [p][d][lane %
+// LANES], so one warp's atomics fall in different banks; the flush of those
+// 128 KiB then costs little next to the span. A span shorter than kSegShortSpan
+// keys counts into a compact [p][d] array instead (bank conflicts, but a flush
+// of P*R words), so that many short ranges do not pay a full flush each. Keys
+// are read as 16-byte vectors.
+constexpr int64_t kSegShortSpan = 65536;
+
 template <typename K, int BITS, int TILE, int LANES>
 __global__ void __launch_bounds__(1024) k_seg_hist(const K* __restrict__ keys,
                                                    const int64_t* __restrict__ off, int64_t nseg,
@@ -186,8 +192,9 @@ __global__ void __launch_bounds__(1024) k_seg_hist(const K* __restrict__ keys,
                                                    uint32_t* __restrict__ seg_hist) {
   using L = DigitLayout<K, BITS>;
   constexpr int R = L::R, P = L::PASSES;
-  extern __shared__ __align__(16) uint32_t s_cnt[];  // [P][R][LANES]
-  for (int i = threadIdx.x; i < P * R * LANES; i += 1024) s_cnt[i] = 0;
+  extern __shared__ __align__(16) uint32_t s_cnt[];  // [P][R][LANES], then [P][R]
+  uint32_t* s_small = s_cnt + P * R * LANES;
+  for (int i = threadIdx.x; i < P * R * (LANES + 1); i += 1024) s_cnt[i] = 0;
   const int64_t T = cnt[kCntTiles];
   const int64_t t0 = T * blockIdx.x / gridDim.x, t1 = T * (blockIdx.x + 1) / gridDim.x;
   uint32_t* my = s_cnt + (threadIdx.x & (LANES - 1));
@@ -196,9 +203,14 @@ __global__ void __launch_bounds__(1024) k_seg_hist(const K* __restrict__ keys,
     for (int p = 0; p < P; ++p)
       atomicAdd(&my[(p * R + digit_of(k, p * BITS, (1u << L::width(p)) - 1)) * LANES], 1u);
   };
+  auto count_small = [&](K k) {
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      atomicAdd(&s_small[p * R + digit_of(k, p * BITS, (1u << L::width(p)) - 1)], 1u);
+  };
   int32_t cur = -1;
   __syncthreads();
-  auto flush = [&](int32_t slot) {
+  auto flush = [&](int32_t slot) {  // the lane columns
     __syncthreads();
     for (int j = threadIdx.x; j < P * R; j += 1024) {
       uint32_t s = 0;
@@ -217,17 +229,30 @@ __global__ void __launch_bounds__(1024) k_seg_hist(const K* __restrict__ keys,
   // (long spans keep many 16-byte loads in flight per thread).
   for (int64_t t = t0; t < t1;) {
     const int32_t slot = tile_slot[t];
-    if (slot != cur) {
-      if (cur >= 0) flush(cur);
-      cur = slot;
-    }
     int64_t start, len;
     seg_range(off, list[(size_t)kSegRadix * nseg + slot], total, start, len);
     const int64_t first = slot_first[slot];
     const int64_t t_end = min(t1, first + (len + TILE - 1) / TILE);
     const int64_t lo = start + (t - first) * TILE;
     const int64_t hi = min(start + len, start + (t_end - first) * TILE);
-    count_keys(keys + lo, hi - lo, threadIdx.x, 1024, count);
+    if (hi - lo < kSegShortSpan) {
+      count_keys(keys + lo, hi - lo, threadIdx.x, 1024, count_small);
+      __syncthreads();
+      for (int j = threadIdx.x; j < P * R; j += 1024) {
+        const uint32_t c = s_small[j];
+        if (c) {
+          atomicAdd(&seg_hist[(size_t)slot * P * R + j], c);
+          s_small[j] = 0;
+        }
+      }
+      __syncthreads();
+    } else {
+      if (slot != cur) {
+        if (cur >= 0) flush(cur);
+        cur = slot;
+      }
+      count_keys(keys + lo, hi - lo, threadIdx.x, 1024, count);
+    }
     t = t_end > t ? t_end : t + 1;
   }
   if (cur >= 0) flush(cur);
@@ -414,7 +439,7 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
   timer_begin(a.timer, "k_seg_hist", st);
   {
     constexpr int LANES = sizeof(K) == 4 ? 32 : 16;  // 128 KiB of counters either way
-    constexpr size_t HSMEM = sizeof(uint32_t) * (size_t)P * R * LANES;
+    constexpr size_t HSMEM = sizeof(uint32_t) * (size_t)P * R * (LANES + 1);
     auto hk = k_seg_hist<K, 8, TILE, LANES>;
     if ((e = cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HSMEM)))
       return e;
