@@ -692,17 +692,32 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
   tile_count<K, R, KPT, FULL>(key, dig, tile_n, wofs, my);
   __syncthreads();
 
-  // per digit: the tile's count (published now), warp starts, tile starts
-  uint32_t dcnt[DPT];
+  // per digit: the tile's count (published now), warp starts, tile starts;
+  // with up to 8 warps the warp-exclusive prefixes stay in registers across
+  // the block scan (more would spill), else they go back to shared memory
+  constexpr bool WREG = WARPS <= 8;
+  uint32_t dcnt[DPT], wpre[DPT][WREG ? WARPS : 1];
   uint32_t tsum = 0;
   const bool owner = tid < S::DTHREADS;
   if (owner) {
-    tsum = tile_digit_counts<R, WARPS, DPT>(s_wcnt, tid, dcnt);
-    if (publish)
 #pragma unroll
-      for (int j = 0; j < DPT; ++j)
-        st_relaxed(&p.status[(size_t)tile * R + tid * DPT + j],
-                   (first ? kFlagInc : kFlagAgg) | dcnt[j]);
+    for (int j = 0; j < DPT; ++j) {
+      const int d = tid * DPT + j;
+      uint32_t sum = 0;
+#pragma unroll
+      for (int w = 0; w < WARPS; ++w) {
+        const uint32_t c = s_wcnt[w * R + d];
+        if constexpr (WREG)
+          wpre[j][w] = sum;
+        else
+          s_wcnt[w * R + d] = sum;
+        sum += c;
+      }
+      dcnt[j] = sum;
+      tsum += sum;
+      if (publish)
+        st_relaxed(&p.status[(size_t)tile * R + d], (first ? kFlagInc : kFlagAgg) | sum);
+    }
   }
   uint32_t total;
   uint32_t run = block_exclusive_scan<THREADS>(tsum, s_misc + 1, total);
@@ -713,7 +728,12 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
       const int d = tid * DPT + j;
       tstart[j] = run;
 #pragma unroll
-      for (int w = 0; w < WARPS; ++w) s_wcnt[w * R + d] += run;
+      for (int w = 0; w < WARPS; ++w) {
+        if constexpr (WREG)
+          s_wcnt[w * R + d] = run + wpre[j][w];
+        else
+          s_wcnt[w * R + d] += run;
+      }
       run += dcnt[j];
     }
   }

@@ -28,10 +28,21 @@ def clean_tables():
                 isort.tune_set(kb, vb, rb, -1)
 
 
+# The built-in choices (the tuner's picks on a GB300, compiled into the
+# library): 32-bit keys alone at 2^24 -> radix 256 variant 5, at 2^28 ->
+# variant 0; other widths tuned at one size -> variant 0.
+BUILTIN_K32 = {24: (8, 5), 28: (8, 0)}
+
+
 def test_defaults_without_tuning():
-    for n in (2, 1000, 1 << 20, 1 << 28, 1 << 30):
-        assert isort.resolve(n, 32, 0, 0) == (8, 0)
-        assert isort.resolve(n, 64, 32, 0) == (8, 0)
+    # nearest built-in bucket (the lower one on a tie)
+    for n, b in ((2, 24), (1000, 24), (1 << 20, 24), (1 << 26, 24), (1 << 27, 28),
+                 (1 << 28, 28), (1 << 30, 28)):
+        assert isort.resolve(n, 32, 0, 0) == BUILTIN_K32[b], n
+    for n in (2, 1 << 20, 1 << 30):
+        assert isort.resolve(n, 64, 32, 0) == (8, 0)   # no built-in entry
+        assert isort.resolve(n, 32, 32, 0) == (8, 0)
+        assert isort.resolve(n, 64, 0, 0) == (8, 0)
     assert isort.resolve(1 << 20, 32, 0, 16) == (16, 0)
     assert isort.resolve(1 << 20, 32, 0, 11) == (11, 0)
 
@@ -66,7 +77,7 @@ def test_clearing_and_bad_arguments():
     isort.tune_auto(32, 0, 20, -1)                        # clear one bucket
     assert isort.resolve(1 << 20, 32, 0, 0) == (16, 0)
     isort.tune_auto(32, 0, -1, -1)                        # clear every bucket
-    assert isort.resolve(1 << 20, 32, 0, 0) == (8, 0)
+    assert isort.resolve(1 << 20, 32, 0, 0) == BUILTIN_K32[24]   # back to the built-in
     lib = _lib.load()
     nv = len(isort.tune_variants(32, 0, 8))
     assert lib.isort_tune_auto(32, 0, 20, 8, nv) == _lib.EINVAL      # no such variant
@@ -105,7 +116,7 @@ def test_cache_keys_and_loading(tmp_path):
     path = tmp_path / "cache.json"
     path.write_text(json.dumps(cache))
     assert tune.apply_all("GPU C", path=str(path)) == {}     # nothing for this GPU: defaults stay
-    assert isort.resolve(1 << 20, 32, 0, 0) == (8, 0)
+    assert isort.resolve(1 << 20, 32, 0, 0) == BUILTIN_K32[24]
     applied = tune.apply_all("GPU A", path=str(path))
     assert applied["plain/k32/v0/b20"] == {"radix_bits": 11, "variant": 0}
     assert isort.resolve(1 << 20, 32, 0, 0) == (11, 0)
@@ -126,3 +137,12 @@ def test_shipped_cache_is_well_formed():
                 assert best["radix_bits"] in (8, 11, 16)
                 nv = len(isort.tune_variants(kb, vb, best["radix_bits"]))
                 assert 0 <= best.get("variant", 0) < nv, (gpu, key)
+
+
+def test_builtin_table_is_the_shipped_cache():
+    """The compiled-in choices are the shipped cache's GB300 winners."""
+    gpu = tune.load_cache().get("NVIDIA GB300", {})
+    plain = {tune.parse_plain_key(k): v["best"] for k, v in gpu.items() if k.startswith("plain/")}
+    assert plain
+    for (kb, vb, b), best in plain.items():
+        assert isort.resolve(1 << b, kb, vb, 0) == (best["radix_bits"], best.get("variant", 0))
