@@ -16,15 +16,16 @@
 //               counts are the same).
 //   k_scan      exclusive prefix of each pass's digit counts -> global digit
 //               bases; flags passes whose digit is constant (identity).
-//   k_onesweep  one round: load a tile, count and publish the tile's digit
-//               counts, rank each key among equal digits in input order
-//               (shared-memory peer masks + per-warp counters) straight into
-//               the reordered tile, look back over earlier tiles, write the
-//               tile out in runs. Keys-only sorts of 32-bit keys relax the rank
-//               in warps whose keys share every bit below the digit.
+//   k_onesweep  one round ("ordered" form): load a tile, count and publish
+//               the tile's digit counts, give each key its slot with one shared
+//               atomic on its warp's counter of its digit (stable when the
+//               hardware serves same-address lanes in lane order), look back
+//               over earlier tiles, write the tile out in runs while checking
+//               that every digit run is in order, and re-rank a tile that is
+//               not (onesweep_tile_ordered).
 //   k_onesweep_first  pass 0 of a keys-only sort: the same round without the
-//               stable rank (one shared atomic gives each key its slot), since
-//               the first round's input order carries no information.
+//               check (one CTA-wide counter per digit), since the first round's
+//               input order carries no information.
 //   k_copy_back copies the result home when an odd number of rounds ran.
 #pragma once
 #include <algorithm>
@@ -277,27 +278,14 @@ __device__ __forceinline__ void prefetch_tile(const T* base, int64_t first, int6
   if (bytes) prefetch_l2(a, bytes);
 }
 
-__device__ __forceinline__ uint32_t lanemask_ge() {
-  uint32_t m;
-  asm("mov.u32 %0, %%lanemask_ge;" : "=r"(m));
-  return m;
-}
-
 template <typename K, typename V, int BITS, int THREADS, int KPT>
 struct OnesweepShape {
   static constexpr int R = 1 << BITS;
   static constexpr int WARPS = THREADS / 32;
   static constexpr int TILE = THREADS * KPT;
   static constexpr bool HV = HasVal<V>::value;
-  static constexpr int STAGE_ELEM = (HV && sizeof(V) > sizeof(K)) ? sizeof(V) : sizeof(K);
-  static constexpr int MASK_BUFS = 3;  // peer-mask buffers per warp (see the rank loop)
-  // shared words: per-warp counters, output offsets, misc; then the staging area
+  // shared words before the staged tile: per-warp counters, output offsets, misc
   static constexpr int HEADER_WORDS = WARPS * R + R + 64;
-  static constexpr size_t STAGE_BYTES =
-      (size_t)TILE * STAGE_ELEM > (size_t)WARPS * MASK_BUFS * R * 4
-          ? (size_t)TILE * STAGE_ELEM
-          : (size_t)WARPS * MASK_BUFS * R * 4;
-  static constexpr size_t SMEM = HEADER_WORDS * 4 + STAGE_BYTES;
   static constexpr int DPT = R >= THREADS ? R / THREADS : 1;  // digits per owning thread
   static constexpr int DTHREADS = R >= THREADS ? THREADS : R;  // threads that own digits
   static_assert(THREADS >= R || R % THREADS == 0,
@@ -383,40 +371,14 @@ __device__ __forceinline__ void tile_load(const K* __restrict__ kin, const V* vi
   }
 }
 
-// Per digit owned by this thread: turn the per-warp counts into warp-exclusive
-// offsets and return the tile's count of the digit.
-template <int R, int WARPS, int DPT>
-__device__ __forceinline__ uint32_t tile_digit_counts(uint32_t* s_wcnt, int tid,
-                                                      uint32_t (&dcnt)[DPT]) {
-  uint32_t tsum = 0;
-#pragma unroll
-  for (int j = 0; j < DPT; ++j) {
-    const int d = tid * DPT + j;
-    uint32_t sum = 0;
-#pragma unroll
-    for (int w = 0; w < WARPS; ++w) {
-      const uint32_t c = s_wcnt[w * R + d];
-      s_wcnt[w * R + d] = sum;
-      sum += c;
-    }
-    dcnt[j] = sum;
-    tsum += sum;
-  }
-  return tsum;
-}
-
-// Write out: consecutive threads take consecutive tile slots, so each digit's
-// run lands on consecutive global addresses; every index is bounds-checked.
-// With payloads the staging area is reused for them (contains __syncthreads).
-template <typename K, typename V, int THREADS, int KPT, bool FULL, typename DS>
-__device__ __forceinline__ void tile_scatter(const K* s_keys, V* s_vals, const uint32_t* s_adj,
-                                             const V (&val)[HasVal<V>::value ? KPT : 1],
-                                             const uint32_t (&rank2)[(KPT + 1) / 2],
-                                             const DS& dig, int tile_n, int wofs, K* kout,
-                                             V* vout, uint32_t bound, uint32_t* err) {
-  constexpr bool HV = HasVal<V>::value;
+// Write out (keys only): consecutive threads take consecutive tile slots, so
+// each digit's run lands on consecutive global addresses; every index is
+// bounds-checked.
+template <typename K, int THREADS, int KPT, bool FULL, typename DS>
+__device__ __forceinline__ void tile_scatter(const K* s_keys, const uint32_t* s_adj,
+                                             const DS& dig, int tile_n, K* kout, uint32_t bound,
+                                             uint32_t* err) {
   const int tid = threadIdx.x;
-  uint32_t gpos[HV ? KPT : 1];
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
     const int j = k * THREADS + tid;
@@ -427,20 +389,6 @@ __device__ __forceinline__ void tile_scatter(const K* s_keys, V* s_vals, const u
         kout[g] = kk;
       else
         atomicOr(err, kErrBounds);
-      if constexpr (HV) gpos[k] = g;
-    }
-  }
-  if constexpr (HV) {
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < KPT; ++i)
-      if (FULL || wofs + i * 32 < tile_n)
-        s_vals[(rank2[i >> 1] >> ((i & 1) * 16)) & 0xffffu] = val[i];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < KPT; ++k) {
-      const int j = k * THREADS + tid;
-      if ((FULL || j < tile_n) && gpos[k] < bound) vout[gpos[k]] = s_vals[j];
     }
   }
 }
@@ -453,166 +401,6 @@ __device__ __forceinline__ void tile_count(const K (&key)[KPT], const DS& dig, i
 #pragma unroll
   for (int i = 0; i < KPT; ++i)
     if (FULL || wofs + i * 32 < tile_n) atomicAdd(&my[dig.of(key[i], i)], 1u);
-}
-
-// Rank and reorder in one sweep: the warp's counters already hold, per digit,
-// the tile position of the warp's first key of that digit, so the rank of a
-// key (peer masks, as in tile_rank) is its final tile position and the key is
-// written straight into the staging area. The masks live in a separate area
-// (the staging area is being filled). rank2 receives the positions.
-template <typename K, int R, int KPT, int MASK_BUFS, bool FULL, typename DS>
-__device__ __forceinline__ void tile_rank_place(const K (&key)[KPT], const DS& dig, int tile_n,
-                                                int wofs, uint32_t* my, uint32_t* mm, K* s_keys,
-                                                uint32_t (&rank2)[(KPT + 1) / 2]) {
-  static_assert(MASK_BUFS == 3, "row r marks slot array r mod 3");
-  const int lane = threadIdx.x & 31;
-  const uint32_t ge = lanemask_ge();
-  const uint32_t bit = 1u << lane;
-  auto valid_row = [&](int i) { return FULL || wofs + i * 32 < tile_n; };
-  // Software-pipelined over rows: while row i's counter update is in flight,
-  // row i+1 is marked and its peer mask read. Row r marks array r mod 3; the
-  // slot of row i-1 is cleared in step i before the barrier that precedes any
-  // mark of row i+2 (its next user), after every lane has read it (all lanes
-  // passed the barrier of row i).
-  uint32_t d = dig.of(key[0], 0);
-  uint32_t* slot = mm + d;
-  if (valid_row(0)) atomicOr(slot, bit);
-  __syncwarp();
-  uint32_t peers = valid_row(0) ? *slot : 0u;
-  uint32_t* slot_prev = mm;
-  bool lead_prev = false;
-#pragma unroll
-  for (int i = 0; i < KPT; ++i) {
-    const bool valid = valid_row(i);
-    const bool leader = valid && (peers >> lane) == 1u;
-    if (i > 0 && lead_prev) *slot_prev = 0u;  // row i-1's slot, dead now
-    uint32_t old = 0;
-    if (leader) old = atomicAdd(&my[d], __popc(peers));
-    uint32_t d_next = 0, peers_next = 0;
-    uint32_t* slot_next = mm;
-    if (i + 1 < KPT) {
-      d_next = dig.of(key[i + 1], i + 1);
-      slot_next = mm + ((i + 1) % MASK_BUFS) * R + d_next;
-      if (valid_row(i + 1)) atomicOr(slot_next, bit);
-      __syncwarp();
-      peers_next = valid_row(i + 1) ? *slot_next : 0u;
-    }
-    const uint32_t after =
-        __shfl_sync(kFullMask, old + __popc(peers), (31 - __clz(peers)) & 31);
-    const uint32_t pos = after - __popc(peers & ge);
-    if (valid) {
-      s_keys[pos] = key[i];
-      dig.keep(pos, d);
-    }
-    rank2[i >> 1] = (i & 1) ? (rank2[i >> 1] | (pos << 16)) : pos;
-    slot_prev = slot;
-    lead_prev = leader;
-    slot = slot_next;
-    peers = peers_next;
-    d = d_next;
-  }
-}
-
-// Shared-memory layout of the early-counts round: the usual header and
-// staging area, then a separate peer-mask area.
-template <typename K, typename V, int BITS, int THREADS, int KPT>
-struct EarlyShape {
-  using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
-  static constexpr size_t STAGE = (size_t)S::TILE * S::STAGE_ELEM;
-  static constexpr size_t MASKS = S::HEADER_WORDS * 4 + STAGE;
-  static constexpr size_t SMEM = MASKS + (size_t)S::WARPS * S::MASK_BUFS * S::R * 4;
-};
-
-// One tile of one count-sort round, early-counts form: count, publish the
-// tile's counts, scan, rank straight into the reordered tile, look back,
-// publish the inclusive counts, write out.
-// dig: the key -> digit rule of this round (RadixDigit for a radix round).
-template <typename K, typename V, int BITS, int THREADS, int KPT, bool FULL,
-          typename DS = RadixDigit>
-__device__ __forceinline__ void onesweep_tile_early(const PassParams& p, uint32_t tile, bool first,
-                                                    int64_t tile_base, int tile_n,
-                                                    const K* __restrict__ kin,
-                                                    K* __restrict__ kout, const V* vin, V* vout,
-                                                    const uint32_t* base, uint32_t bound,
-                                                    unsigned char* smem, DS& dig) {
-  using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
-  using E = EarlyShape<K, V, BITS, THREADS, KPT>;
-  constexpr int R = S::R, WARPS = S::WARPS, DPT = S::DPT;
-  constexpr bool HV = S::HV;
-  uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);  // [WARPS][R]
-  uint32_t* s_adj = s_wcnt + WARPS * R;                   // [R]
-  uint32_t* s_misc = s_adj + R;                           // [64]
-  K* s_keys = reinterpret_cast<K*>(smem + S::HEADER_WORDS * 4);
-  V* s_vals = reinterpret_cast<V*>(smem + S::HEADER_WORDS * 4);
-  uint32_t* s_masks = reinterpret_cast<uint32_t*>(smem + E::MASKS);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wofs = warp * 32 * KPT + lane;
-  const bool publish = (int64_t)tile != p.stall_tile;
-
-  K key[KPT];
-  V val[HV ? KPT : 1];
-  tile_load<K, V, KPT, FULL>(kin, vin, tile_base, tile_n, wofs, key, val);
-  dig.prepare(key);
-  tile_count<K, R, KPT, FULL>(key, dig, tile_n, wofs, s_wcnt + warp * R);
-  __syncthreads();
-  if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 1] = globaltimer();
-
-  // per digit: the tile's count (published now), warp offsets, tile starts
-  uint32_t dcnt[DPT];
-  uint32_t tsum = 0;
-  const bool owner = tid < S::DTHREADS;
-  if (owner) {
-    tsum = tile_digit_counts<R, WARPS, DPT>(s_wcnt, tid, dcnt);
-    if (publish)
-#pragma unroll
-      for (int j = 0; j < DPT; ++j)
-        st_relaxed(&p.status[(size_t)tile * R + tid * DPT + j],
-                   (first ? kFlagInc : kFlagAgg) | dcnt[j]);
-  }
-  uint32_t total;
-  uint32_t run = block_exclusive_scan<THREADS>(tsum, s_misc + 1, total);
-  uint32_t tstart[DPT];
-  if (owner) {
-#pragma unroll
-    for (int j = 0; j < DPT; ++j) {
-      const int d = tid * DPT + j;
-      tstart[j] = run;
-#pragma unroll
-      for (int w = 0; w < WARPS; ++w) s_wcnt[w * R + d] += run;
-      run += dcnt[j];
-    }
-  }
-  __syncthreads();
-  uint32_t rank2[(KPT + 1) / 2];
-  tile_rank_place<K, R, KPT, S::MASK_BUFS, FULL>(key, dig, tile_n, wofs, s_wcnt + warp * R,
-                                                 s_masks + warp * S::MASK_BUFS * R, s_keys,
-                                                 rank2);
-  if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 2] = globaltimer();
-
-  // look back over earlier tiles, publish the inclusive counts, output offsets
-  uint32_t windows = 0;
-  if (owner) {
-#pragma unroll
-    for (int j = 0; j < DPT; ++j) {
-      const int d = tid * DPT + j;
-      uint32_t excl = 0;
-      if (!first) {
-        excl = lookback_exclusive<R, kLookbackWindow>(p.status, tile, d, p.spin_limit, p.err,
-                                                      windows);
-        if (publish) st_relaxed(&p.status[(size_t)tile * R + d], kFlagInc | (excl + dcnt[j]));
-      }
-      s_adj[d] = base[d] + excl - tstart[j];
-    }
-  }
-  if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 6] = windows;
-  __syncthreads();
-  if (p.trace && tid == 0) {
-    p.trace[(size_t)tile * 8 + 3] = globaltimer();
-    p.trace[(size_t)tile * 8 + 4] = globaltimer();
-  }
-  tile_scatter<K, V, THREADS, KPT, FULL>(s_keys, s_vals, s_adj, val, rank2, dig, tile_n, wofs,
-                                         kout, vout, bound, p.err);
-  if (p.trace && tid == 0) p.trace[(size_t)tile * 8 + 5] = globaltimer();
 }
 
 // Shared memory of the ordered round: the per-warp counters, digit offsets and
@@ -661,7 +449,7 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
                                                       const K* __restrict__ kin,
                                                       K* __restrict__ kout, const V* vin, V* vout,
                                                       const uint32_t* base, uint32_t bound,
-                                                      unsigned char* smem) {
+                                                      unsigned char* smem, DS& dig) {
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
   using O = OrderedShape<K, V, BITS, THREADS, KPT>;
   constexpr int R = S::R, WARPS = S::WARPS, DPT = S::DPT;
@@ -675,7 +463,6 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wofs = warp * 32 * KPT + lane;
   const bool publish = (int64_t)tile != p.stall_tile;
-  DS dig{p};
   uint32_t* my = s_wcnt + warp * R;
   // the fallback re-reads the tile's input address from here (fewer live registers)
   if (tid == 0) *reinterpret_cast<const K**>(s_misc + 48) = kin + tile_base;
@@ -689,6 +476,7 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
       if (FULL || wofs + i * 32 < tile_n)
         cp_async<sizeof(V)>(&s_vals[wofs + i * 32], vin + tile_base + wofs + i * 32);
   }
+  dig.prepare(key);
   tile_count<K, R, KPT, FULL>(key, dig, tile_n, wofs, my);
   __syncthreads();
 
@@ -740,14 +528,18 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
   __syncthreads();
 
   // place: one slot add per key
-  auto place = [&](int i, uint32_t pos) {
+  auto place = [&](int i, uint32_t pos, uint32_t d) {
     s_keys[pos] = key[i];
+    dig.keep(pos, d);
     if constexpr (HV) s_src[pos] = (uint16_t)(wofs + i * 32);
   };
   if (p.check_mode != kCheckPerturb) {
 #pragma unroll
     for (int i = 0; i < KPT; ++i)
-      if (FULL || wofs + i * 32 < tile_n) place(i, atomicAdd(&my[dig.of(key[i], i)], 1u));
+      if (FULL || wofs + i * 32 < tile_n) {
+        const uint32_t d = dig.of(key[i], i);
+        place(i, atomicAdd(&my[d], 1u), d);
+      }
   } else {  // test hook: odd lanes of each row first, an order the check must reject
 #pragma unroll
     for (int i = 0; i < KPT; ++i) {
@@ -757,7 +549,7 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
       __syncwarp();
       if (valid && !(lane & 1)) pos = atomicAdd(&my[dig.of(key[i], i)], 1u);
       __syncwarp();
-      if (valid) place(i, pos);
+      if (valid) place(i, pos, dig.of(key[i], i));
     }
   }
 
@@ -849,6 +641,7 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
     if (valid) {
       const uint32_t pos = old + __popc(peers & lt);
       s_keys[pos] = k;
+      dig.keep(pos, d);
       if constexpr (HV) s_src[pos] = (uint16_t)(wofs2 + i * 32);
     }
     __syncwarp();  // this row's counter updates precede the next row's
@@ -906,12 +699,15 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
   const V* vin = static_cast<const V*>(src ? p.vals[1] : p.vals[0]);
   V* vout = static_cast<V*>(src ? p.vals[0] : p.vals[1]);
   const int64_t tile_base = (int64_t)tile * TILE;
+  DS dig{p};
   if (tile_n == TILE)
     onesweep_tile_ordered<K, V, BITS, THREADS, KPT, true, DS>(
-        p, tile, tile == 0, tile_base, tile_n, kin, kout, vin, vout, p.base, (uint32_t)p.n, smem);
+        p, tile, tile == 0, tile_base, tile_n, kin, kout, vin, vout, p.base, (uint32_t)p.n, smem,
+        dig);
   else
     onesweep_tile_ordered<K, V, BITS, THREADS, KPT, false, DS>(
-        p, tile, tile == 0, tile_base, tile_n, kin, kout, vin, vout, p.base, (uint32_t)p.n, smem);
+        p, tile, tile == 0, tile_base, tile_n, kin, kout, vin, vout, p.base, (uint32_t)p.n, smem,
+        dig);
 }
 
 // ---------------------------------------------------------------------------
@@ -1023,9 +819,7 @@ __device__ __forceinline__ void onesweep_tile_first(const PassParams& p, uint32_
     }
   }
   __syncthreads();
-  uint32_t rank2[(KPT + 1) / 2];
-  tile_scatter<K, NoVal, THREADS, KPT, FULL>(s_keys, nullptr, s_adj, val, rank2, dig, tile_n,
-                                             wofs, kout, nullptr, bound, p.err);
+  tile_scatter<K, THREADS, KPT, FULL>(s_keys, s_adj, dig, tile_n, kout, bound, p.err);
 }
 
 // The first round (pass 0) of a keys-only sort; a skipped pass 0 leaves the

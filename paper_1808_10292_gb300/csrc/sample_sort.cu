@@ -105,6 +105,7 @@ struct CachedSplitDigit {
     for (int i = 0; i < KPT; ++i)
       packed[i >> 2] |= bucket_in_cell(s, cell, key[i]) << ((i & 3) * 8);
   }
+  __device__ __forceinline__ uint32_t operator()(K k) const { return bucket_in_cell(s, cell, k); }
   __device__ __forceinline__ uint32_t of(K, int i) const {
     return (packed[i >> 2] >> ((i & 3) * 8)) & 0xffu;
   }
@@ -206,9 +207,10 @@ __global__ void __launch_bounds__(THREADS, MINB) k_gvr_split(PassParams p,
                                                              const K* __restrict__ split,
                                                              const uint16_t* __restrict__ cell) {
   using S = OnesweepShape<K, V, 8, THREADS, KPT>;
-  using E = EarlyShape<K, V, 8, THREADS, KPT>;
+  using O = OrderedShape<K, V, 8, THREADS, KPT>;
   // keys only: the split round is the first round over the input, so the
-  // order of keys within a bucket is free (onesweep_tile_first)
+  // order of keys within a bucket is free (onesweep_tile_first); with payloads
+  // the ordered round (stable, checked)
   constexpr bool FIRST = !HasVal<V>::value;
   constexpr int R = S::R, WARPS = S::WARPS, TILE = S::TILE;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -216,17 +218,11 @@ __global__ void __launch_bounds__(THREADS, MINB) k_gvr_split(PassParams p,
   __shared__ uint16_t s_cell[kCells];
   uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
   uint32_t* s_misc = FIRST ? s_wcnt + 2 * R : s_wcnt + WARPS * R + R;
-  uint32_t* s_masks = reinterpret_cast<uint32_t*>(smem + E::MASKS);
   const int tid = threadIdx.x;
   for (int i = tid; i < kMaxSplit; i += THREADS) s_split[i] = split[i];
   for (int i = tid; i < kCells; i += THREADS) s_cell[i] = cell[i];
   if (tid == 0) s_misc[0] = atomicAdd(p.counter, 1u);  // tiles in launch order
-  if constexpr (FIRST) {
-    zero_words<THREADS>(s_wcnt, R);
-  } else {
-    zero_words<THREADS>(s_wcnt, WARPS * R);
-    zero_words<THREADS>(s_masks, WARPS * S::MASK_BUFS * R);
-  }
+  zero_words<THREADS>(s_wcnt, FIRST ? R : WARPS * R);
   __syncthreads();
   const uint32_t tile = s_misc[0];
   const int tile_n = (int)min((int64_t)TILE, p.n - (int64_t)tile * TILE);
@@ -254,15 +250,16 @@ __global__ void __launch_bounds__(THREADS, MINB) k_gvr_split(PassParams p,
                                                      kout, p.base, (uint32_t)p.n, smem, dig);
     return;
   }
-  dig.s_slot = smem + E::SMEM;
+  dig.s_slot = smem + O::SMEM;
+  using DS = CachedSplitDigit<K, KPT>;
   if (tile_n == TILE)
-    onesweep_tile_early<K, V, 8, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n, kin,
-                                                     kout, vin, vout, p.base, (uint32_t)p.n,
-                                                     smem, dig);
+    onesweep_tile_ordered<K, V, 8, THREADS, KPT, true, DS>(p, tile, tile == 0, tile_base, tile_n,
+                                                           kin, kout, vin, vout, p.base,
+                                                           (uint32_t)p.n, smem, dig);
   else
-    onesweep_tile_early<K, V, 8, THREADS, KPT, false>(p, tile, tile == 0, tile_base, tile_n, kin,
-                                                      kout, vin, vout, p.base, (uint32_t)p.n,
-                                                      smem, dig);
+    onesweep_tile_ordered<K, V, 8, THREADS, KPT, false, DS>(p, tile, tile == 0, tile_base,
+                                                            tile_n, kin, kout, vin, vout, p.base,
+                                                            (uint32_t)p.n, smem, dig);
 }
 
 template <typename K, typename V, int THREADS, int KPT, int MINB>
@@ -320,7 +317,7 @@ cudaError_t gvr_launch(const GvrArgs& a, cudaStream_t st) {
   auto kern = k_gvr_split<K, V, CT, CK, MINB>;
   // the round's layout, then one bucket byte per tile slot
   const size_t smem =
-      (HV ? EarlyShape<K, V, 8, CT, CK>::SMEM : FirstShape<K, 8, CT, CK>::SMEM) + S::TILE;
+      (HV ? OrderedShape<K, V, 8, CT, CK>::SMEM : FirstShape<K, 8, CT, CK>::SMEM) + S::TILE;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
     return e;
   timer_begin(a.timer, "k_gvr_split", st);

@@ -377,11 +377,11 @@ __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp
     if (tile_n == TILE)
       onesweep_tile_ordered<K, V, BITS, THREADS, KPT, true>(p, tile, lt == 0, tile_base, tile_n,
                                                             kin, kout, vin, vout, base,
-                                                            (uint32_t)len, smem);
+                                                            (uint32_t)len, smem, dig);
     else
       onesweep_tile_ordered<K, V, BITS, THREADS, KPT, false>(p, tile, lt == 0, tile_base,
                                                              tile_n, kin, kout, vin, vout, base,
-                                                             (uint32_t)len, smem);
+                                                             (uint32_t)len, smem, dig);
   }
 }
 

@@ -286,14 +286,15 @@ __global__ void __launch_bounds__(THREADS, MINB)
     }
     return;
   }
+  DS dig{p};
   if (tile_n == TILE)
     onesweep_tile_ordered<K, V, 8, THREADS, KPT, true, DS>(p, tile, lt == 0, tile_base, tile_n,
                                                            kin, kout, vin, vout, base + h * 256,
-                                                           (uint32_t)p.n, smem);
+                                                           (uint32_t)p.n, smem, dig);
   else
     onesweep_tile_ordered<K, V, 8, THREADS, KPT, false, DS>(p, tile, lt == 0, tile_base, tile_n,
                                                             kin, kout, vin, vout, base + h * 256,
-                                                            (uint32_t)p.n, smem);
+                                                            (uint32_t)p.n, smem, dig);
 }
 
 // Scratch of the rounds inside the workspace: hist holds the 2^W counts, then
