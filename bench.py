@@ -401,8 +401,9 @@ def run_ours(a):
             isort.sort_keys(keys, rb)
 
     variant = None
-    if rb == 8 and not gvr and not gsd:
-        variant = isort.tune_variants(kb, vb, rb)[0]
+    if rb == 8 and not gvr and not gsd:  # the kernel shape the library resolves for this sort
+        r_bits, vi = isort.resolve(n, kb, vb, rb)
+        variant = isort.tune_variants(kb, vb, r_bits)[vi]
 
     clocks = ClockSampler(local)
     clocks.start()  # streaming before the timed region begins

@@ -247,6 +247,7 @@ def tune_segmented(key_bits: int = 32, val_bits: int = 0, btn_max_keys: int = -1
 
 def resolve(n: int, key_bits: int = 32, val_bits: int = 0, radix_bits: int = 0):
     """(radix_bits, variant) that a sort of n keys with these arguments uses."""
+    _tuned()
     rb, v = ctypes.c_int(0), ctypes.c_int(0)
     check(load().isort_tune_resolve(n, key_bits, val_bits, radix_bits, ctypes.byref(rb),
                                     ctypes.byref(v)), "isort_tune_resolve")
