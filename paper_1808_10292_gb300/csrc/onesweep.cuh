@@ -438,10 +438,10 @@ struct OrderedShape {
 //    staged input indices increase), which is exact stability.
 // A tile that fails is ranked again stably (peers found with __match_any_sync)
 // and written out again to the same positions. Payloads are copied into shared
-// memory in input order (cp.async, no registers) and gathered by the staged
-// input indices at the write-out. Per key the fast path makes three
-// digit-indexed shared accesses (count add, slot add, key store; with payloads
-// also the index store and the payload gather) against the peer-mask round's six.
+// memory in input order (one bulk copy per tile, or cp.async; no registers)
+// and gathered by the staged input indices at the write-out. Per key the fast
+// path makes three digit-indexed shared accesses (count add, slot add, key
+// store; with payloads also the index store and the payload gather).
 template <typename K, typename V, int BITS, int THREADS, int KPT, bool FULL,
           typename DS = RadixDigit>
 __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint32_t tile,
@@ -449,7 +449,12 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
                                                       const K* __restrict__ kin,
                                                       K* __restrict__ kout, const V* vin, V* vout,
                                                       const uint32_t* base, uint32_t bound,
-                                                      unsigned char* smem, DS& dig) {
+                                                      unsigned char* smem, DS& dig,
+                                                      bool bulk = false) {
+  // bulk: the kernel started one bulk copy of this (whole) tile into the
+  // staging area, and of its payloads into the staged-payload area, completing
+  // on the mbarrier at s_misc[56..57]; otherwise keys are loaded lane-striped
+  // from global memory and payloads copied by cp.async.
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
   using O = OrderedShape<K, V, BITS, THREADS, KPT>;
   constexpr int R = S::R, WARPS = S::WARPS, DPT = S::DPT;
@@ -469,16 +474,29 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
 
   K key[KPT];
   NoVal nv[1];
-  tile_load<K, NoVal, KPT, FULL>(kin, nullptr, tile_base, tile_n, wofs, key, nv);
-  if constexpr (HV) {
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_misc + 56);
+  if (FULL && bulk) {
+    if (!mbar_wait_bounded(bar, 0, p.spin_limit)) {
+      // the copy did not complete in time: flag it, and still wait (bounded)
+      // for it to land before the staging area is read or reused
+      atomicOr(p.err, kErrTimeout);
+      mbar_wait_bounded(bar, 0, p.spin_limit);
+    }
 #pragma unroll
-    for (int i = 0; i < KPT; ++i)
-      if (FULL || wofs + i * 32 < tile_n)
-        cp_async<sizeof(V)>(&s_vals[wofs + i * 32], vin + tile_base + wofs + i * 32);
+    for (int i = 0; i < KPT; ++i) key[i] = s_keys[wofs + i * 32];
+  } else {
+    tile_load<K, NoVal, KPT, FULL>(kin, nullptr, tile_base, tile_n, wofs, key, nv);
+    if constexpr (HV) {
+#pragma unroll
+      for (int i = 0; i < KPT; ++i)
+        if (FULL || wofs + i * 32 < tile_n)
+          cp_async<sizeof(V)>(&s_vals[wofs + i * 32], vin + tile_base + wofs + i * 32);
+    }
   }
   dig.prepare(key);
   tile_count<K, R, KPT, FULL>(key, dig, tile_n, wofs, my);
-  __syncthreads();
+  __syncthreads();  // every thread holds its keys: the staging area is free
+  if (FULL && bulk && tid == 0) mbar_inval(bar);  // used once; every thread has passed it
 
   // per digit: the tile's count (published now), warp starts, tile starts;
   // with up to 8 warps the warp-exclusive prefixes stay in registers across
@@ -681,10 +699,35 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
   int src = 0;  // input buffer = parity of the rounds executed before this one
   for (int q = 0; q < p.pass; ++q) src ^= (p.skip[q] == 0);
 
-  if (tid == 0) s_misc[0] = atomicAdd(p.counter, 1u);  // tiles in launch order
+  if (tid == 0) {
+    const uint32_t t = atomicAdd(p.counter, 1u);  // tiles in launch order
+    s_misc[0] = t;
+    // A whole tile at 16-byte aligned addresses comes by one bulk copy (keys
+    // into the staging area, payloads in input order into the staged-payload
+    // area): no per-key load instructions or cp.async, and with payloads one
+    // copy instead of a cp.async per payload.
+    const int64_t tb = (int64_t)t * TILE;
+    const K* k0 = static_cast<const K*>(src ? p.keys[1] : p.keys[0]) + tb;
+    const V* v0 = static_cast<const V*>(src ? p.vals[1] : p.vals[0]) + tb;
+    bool bulk = tb + TILE <= p.n && (reinterpret_cast<uintptr_t>(k0) & 15) == 0;
+    if constexpr (HasVal<V>::value) bulk = bulk && (reinterpret_cast<uintptr_t>(v0) & 15) == 0;
+    if (bulk) {
+      using O = OrderedShape<K, V, BITS, THREADS, KPT>;
+      uint64_t* bar = reinterpret_cast<uint64_t*>(s_misc + 56);
+      mbar_init(bar, 1);
+      fence_mbar_init();
+      constexpr uint32_t kb = TILE * sizeof(K);
+      constexpr uint32_t vb = HasVal<V>::value ? TILE * sizeof(V) : 0;
+      mbar_arrive_expect_tx(bar, kb + vb);
+      bulk_copy_g2s(smem + O::KEYS, k0, kb, bar);
+      if constexpr (HasVal<V>::value) bulk_copy_g2s(smem + O::VALS, v0, vb, bar);
+    }
+    s_misc[60] = bulk;
+  }
   zero_words<THREADS>(s_wcnt, WARPS * R);
   __syncthreads();
   const uint32_t tile = s_misc[0];
+  const bool bulk = s_misc[60] != 0;
   const int tile_n = (int)min((int64_t)TILE, p.n - (int64_t)tile * TILE);
   if (p.prefetch_tiles && tid == 0) {
     const int64_t pf = ((int64_t)tile + p.prefetch_tiles) * TILE;
@@ -703,7 +746,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
   if (tile_n == TILE)
     onesweep_tile_ordered<K, V, BITS, THREADS, KPT, true, DS>(
         p, tile, tile == 0, tile_base, tile_n, kin, kout, vin, vout, p.base, (uint32_t)p.n, smem,
-        dig);
+        dig, bulk);
   else
     onesweep_tile_ordered<K, V, BITS, THREADS, KPT, false, DS>(
         p, tile, tile == 0, tile_base, tile_n, kin, kout, vin, vout, p.base, (uint32_t)p.n, smem,
