@@ -543,38 +543,46 @@ def run_ours(a):
 
 
 def measure_e2e(a, n, kb, vb, rb, torch, isort, inputs, stream):
-    """keys/s through the public call with HOST buffers: every step copies its
-    input from pinned host memory to the device, sorts it, and copies the sorted
-    keys (and payloads) back. Measured two ways: one step at a time, and
-    pipelined over three device buffers on three streams, so that a step's
-    upload overlaps the earlier steps' sorts and downloads (the host link runs
-    both directions at once, so the period is bound by one direction's copy);
-    the pipelined figure is the line's e2e."""
+    """keys/s through the C-ABI call with HOST buffers: every step sorts the
+    pinned host input into a pinned host output with isort_keys_host /
+    isort_pairs_host, which copies the input to the device, sorts it and
+    copies the result back on the step's stream (the sample sorts, which have
+    no host-buffer entry point, copy with torch around isort_sample_sort /
+    isort_gsd_sort). Measured two ways: one step at a time, and pipelined over
+    three streams, so that a step's upload overlaps the earlier steps' sorts
+    and downloads (the host link runs both directions at once, so the period is
+    bound by one direction's copy); the pipelined figure is the line's e2e."""
     host_in = inputs.device_keys(n, kb, a.dist, a.seed).cpu().pin_memory()
     hv_in = inputs.device_iota(n, vb).cpu().pin_memory() if vb else None
     gvr = a.workload == "sample_2p28"
     gsd = a.workload == "gsd_2p28"
+    host_api = not (gvr or gsd)
     steps = max(8, min(a.steps, 20))
     nbuf = 3
     streams = [torch.cuda.Stream() for _ in range(nbuf)]
-    dev = [torch.empty(n, dtype=host_in.dtype, device="cuda") for _ in streams]
-    dv = [torch.empty(n, dtype=hv_in.dtype, device="cuda") if vb else None for _ in streams]
+    dev = [None if host_api else torch.empty(n, dtype=host_in.dtype, device="cuda")
+           for _ in streams]
+    dv = [torch.empty(n, dtype=hv_in.dtype, device="cuda") if vb and not host_api else None
+          for _ in streams]
     host_out = [torch.empty_like(host_in).pin_memory() for _ in streams]
     hv_out = [torch.empty_like(hv_in).pin_memory() if vb else None for _ in streams]
 
     def step(b):
+        if host_api:
+            if vb:
+                isort.sort_pairs_host(host_in, hv_in, host_out[b], hv_out[b], rb,
+                                      stream=streams[b])
+            else:
+                isort.sort_keys_host(host_in, host_out[b], rb, stream=streams[b])
+            return
         d, v = dev[b], dv[b]
         d.copy_(host_in, non_blocking=True)
         if vb:
             v.copy_(hv_in, non_blocking=True)
         if gvr:
             isort.sample_sort(d, v, buckets=256, oversample=16, seed=a.seed)
-        elif gsd:
-            isort.gsd_sort(d, v, buckets=16, oversample=4)
-        elif vb:
-            isort.sort_pairs(d, v, rb)
         else:
-            isort.sort_keys(d, rb)
+            isort.gsd_sort(d, v, buckets=16, oversample=4)
         if vb:
             hv_out[b].copy_(v, non_blocking=True)
         host_out[b].copy_(d, non_blocking=True)
@@ -608,8 +616,10 @@ def measure_e2e(a, n, kb, vb, rb, torch, isort, inputs, stream):
         if not (out[1:] >= out[:-1]).all():
             raise RuntimeError("e2e result not sorted")
     bi = n * (kb + vb) // 8
+    api = (("isort_pairs_host" if vb else "isort_keys_host") if host_api else
+           ("torch copies + isort_sample_sort" if gvr else "torch copies + isort_gsd_sort"))
     return {"value": n / (ms / 1000.0), "unit": "keys/s", "h2d_bytes_per_step": bi,
-            "d2h_bytes_per_step": bi, "ms_per_step": ms, "steps": steps,
+            "d2h_bytes_per_step": bi, "ms_per_step": ms, "steps": steps, "api": api,
             "pipelined": "three device buffers on three streams: a step's upload overlaps "
                          "the earlier steps' sorts and downloads",
             "runs_ms_per_step": runs,

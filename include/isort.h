@@ -14,8 +14,10 @@
  * their input order and payloads move with their keys.
  *
  * Conventions for every call:
- *  - keys, vals, offsets are DEVICE pointers owned by the caller; the library
- *    never frees caller memory. Sorts are in place.
+ *  - keys, vals, offsets are DEVICE pointers owned by the caller (except the
+ *    *_host calls, whose buffers are in host memory); the library never frees
+ *    caller memory. Sorts are in place (the *_host calls may also write to
+ *    separate output buffers).
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls are
  *    asynchronous: they validate arguments, enqueue kernels on `stream` and
  *    return. Argument errors are returned at once and enqueue nothing.
@@ -63,6 +65,34 @@ isort_status isort_keys(void *keys, int64_t n, int key_bits, int radix_bits, voi
  * moves with keys[i]. Same algorithm; the payload rides along every round. */
 isort_status isort_pairs(void *keys, void *vals, int64_t n, int key_bits, int val_bits,
                          int radix_bits, void *stream);
+
+/* The same sorts for keys (and payloads) held in HOST memory: keys_out[0..n)
+ * receives keys_in[0..n) in ascending order (vals_out the payloads, stably);
+ * an output may be its input (in place). Nothing is read from or written to
+ * the host buffers outside [0, n) elements.
+ *
+ * The call enqueues on `stream`: the copy of the input into the stream's
+ * workspace (which then holds n more keys, and payloads, than isort_keys
+ * needs), the sort of that device copy (as isort_keys / isort_pairs), and the
+ * copy of the result to the output buffers; it returns once this is enqueued.
+ * The output is complete when the stream has reached that point (e.g. after
+ * cudaStreamSynchronize); the input must stay unchanged, and every buffer
+ * allocated, until then. Device-side errors are latched as for isort_keys.
+ *
+ * Buffers move by cudaMemcpyAsync (the copy engines; for pageable memory the
+ * call then returns only when the copies are done, for page-locked memory at
+ * once). ISORT_DEBUG_HOST_COPY 2 moves page-locked, 16-byte aligned buffers
+ * with copy kernels instead (every SM reads or writes the host buffer through
+ * its device mapping): as fast alone, slower when several streams' sorts and
+ * copies overlap.
+ * Errors: ISORT_EINVAL for null buffers, bad widths or misaligned elements;
+ * ISORT_ENOMEM when the workspace cannot hold the device copies; otherwise as
+ * isort_keys. n = 0 does nothing; n = 1 copies the element. */
+isort_status isort_keys_host(const void *keys_in, void *keys_out, int64_t n, int key_bits,
+                             int radix_bits, void *stream);
+isort_status isort_pairs_host(const void *keys_in, const void *vals_in, void *keys_out,
+                              void *vals_out, int64_t n, int key_bits, int val_bits,
+                              int radix_bits, void *stream);
 
 /* Segmented sort: each range [offsets[s], offsets[s+1]) is sorted independently
  * (vals may be NULL, then val_bits is ignored). offsets: DEVICE int64 array of
@@ -233,13 +263,6 @@ enum {
   ISORT_DEBUG_SPIN_LIMIT = 1,
   ISORT_DEBUG_STALL_TILE = 2,
   ISORT_DEBUG_KERNEL_TIMING = 3,
-  /* value = device pointer to tiles * 8 uint64 words (0 = off): radix-256 sorts
-   * then record, for every tile of pass ISORT_DEBUG_TRACE_PASS, %globaltimer at
-   * tile start, after ranking, before and after the look-back, after the
-   * shared-memory reorder and at the end, then the look-back window count of
-   * digit 0 and the SM id. A measurement hook; it does not change results. */
-  ISORT_DEBUG_TRACE_PTR = 4,
-  ISORT_DEBUG_TRACE_PASS = 5,
   /* value = L2 prefetch distance of the radix-256 rounds in tiles (0 = off,
    * -1 = default: one wave, SMs x 4). A tuning knob; results are unchanged. */
   ISORT_DEBUG_PREFETCH_TILES = 6,
@@ -249,7 +272,13 @@ enum {
    * re-rank; value 2: the fast ranks are deliberately made unstable (odd lanes
    * first), which the check must catch; 0 = normal. Test hooks; results are
    * unchanged. */
-  ISORT_DEBUG_CHECK_MODE = 7
+  ISORT_DEBUG_CHECK_MODE = 7,
+  /* How isort_keys_host / isort_pairs_host move a buffer between host and
+   * device memory: 0 = automatic (the copy engines), 1 = copy engines
+   * (cudaMemcpyAsync), 2 = copy kernels for page-locked, 16-byte aligned
+   * buffers that the device maps at their own address (copy engines for the
+   * rest). A tuning knob; results are unchanged. */
+  ISORT_DEBUG_HOST_COPY = 8
 };
 isort_status isort_debug_set(int what, int64_t value);
 

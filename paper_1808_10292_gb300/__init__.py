@@ -1,8 +1,10 @@
 """isort: LSD radix sort of unsigned integer keys on one GB300 GPU.
 
 Thin Python face of the C-ABI library (include/isort.h). Tensors are used only
-for device memory and streams: each call passes ``data_ptr()`` and the current
-CUDA stream to the library, whose kernels do all the work. Sorting is in place.
+for memory and streams: each call passes ``data_ptr()`` and the current CUDA
+stream to the library, whose kernels do all the work. Sorting is in place on
+CUDA tensors; sort_keys_host / sort_pairs_host take CPU tensors (host memory),
+which the library copies to the device and back around the same sort.
 """
 from __future__ import annotations
 
@@ -11,8 +13,9 @@ import ctypes
 from . import _lib
 from ._lib import IsortError, check, load
 
-__all__ = ["sort_keys", "sort_pairs", "sort_segmented", "workspace_size", "set_workspace",
-           "stream_status", "release_workspaces", "IsortError", "load"]
+__all__ = ["sort_keys", "sort_pairs", "sort_keys_host", "sort_pairs_host", "sort_segmented",
+           "workspace_size", "set_workspace", "stream_status", "release_workspaces", "IsortError",
+           "load"]
 
 
 def _torch():
@@ -96,6 +99,52 @@ def sort_keys_noalloc(keys, err_word, stream=None):
     check(load().isort_keys_noalloc(keys.data_ptr(), keys.numel(), err_word.data_ptr(),
                                     _stream(stream)), "isort_keys_noalloc")
     return keys
+
+
+def _host(t, name):
+    if t.is_cuda:
+        raise ValueError(f"{name} must be a CPU tensor (host memory)")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def sort_keys_host(keys_in, keys_out=None, radix_bits: int = 0, stream=None):
+    """Sort a CPU (host-memory) uint32/uint64 tensor through isort_keys_host:
+    keys_out (default: keys_in, in place) receives the keys in ascending order.
+    The copies in and out and the sort are enqueued on the CUDA stream; the
+    result is there once the stream has reached that point (synchronize it).
+    With pinned (page-locked) tensors the call returns at once; with pageable
+    ones the copies complete before it returns."""
+    keys_out = keys_in if keys_out is None else keys_out
+    _host(keys_in, "keys_in")
+    _host(keys_out, "keys_out")
+    if keys_out.dtype != keys_in.dtype or keys_out.numel() != keys_in.numel():
+        raise ValueError("keys_out must match keys_in in dtype and size")
+    _tuned()
+    check(load().isort_keys_host(keys_in.data_ptr(), keys_out.data_ptr(), keys_in.numel(),
+                                 _bits(keys_in), radix_bits, _stream(stream)), "isort_keys_host")
+    return keys_out
+
+
+def sort_pairs_host(keys_in, vals_in, keys_out=None, vals_out=None, radix_bits: int = 0,
+                    stream=None):
+    """Stable key-value sort of CPU tensors through isort_pairs_host (outputs
+    default to the inputs, in place); stream semantics as sort_keys_host."""
+    keys_out = keys_in if keys_out is None else keys_out
+    vals_out = vals_in if vals_out is None else vals_out
+    for t, name in ((keys_in, "keys_in"), (vals_in, "vals_in"), (keys_out, "keys_out"),
+                    (vals_out, "vals_out")):
+        _host(t, name)
+    n = keys_in.numel()
+    if vals_in.numel() != n or keys_out.numel() != n or vals_out.numel() != n:
+        raise ValueError("keys and payloads must have the same number of elements")
+    if keys_out.dtype != keys_in.dtype or vals_out.dtype != vals_in.dtype:
+        raise ValueError("outputs must match the inputs' dtypes")
+    _tuned()
+    check(load().isort_pairs_host(keys_in.data_ptr(), vals_in.data_ptr(), keys_out.data_ptr(),
+                                  vals_out.data_ptr(), n, _bits(keys_in), _bits(vals_in),
+                                  radix_bits, _stream(stream)), "isort_pairs_host")
+    return keys_out, vals_out
 
 
 def sort_pairs(keys, vals, radix_bits: int = 0, stream=None):

@@ -17,8 +17,9 @@ STATUS = {0: "ISORT_OK", 1: "ISORT_EINVAL", 2: "ISORT_ENOMEM", 3: "ISORT_ECUDA",
           4: "ISORT_ETIMEOUT", 5: "ISORT_EUNSUPPORTED"}
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
 DEBUG_SPIN_LIMIT, DEBUG_STALL_TILE, DEBUG_KERNEL_TIMING = 1, 2, 3
-DEBUG_TRACE_PTR, DEBUG_TRACE_PASS, DEBUG_PREFETCH_TILES = 4, 5, 6
+DEBUG_PREFETCH_TILES = 6
 DEBUG_CHECK_MODE = 7
+DEBUG_HOST_COPY = 8
 NOALLOC_MAX_KEYS = 1 << 20
 NET_BTN, NET_OET = 0, 1
 
@@ -36,6 +37,8 @@ def _sig(lib):
     sigs = {
         "isort_keys": [vp, i64, i32, i32, vp],
         "isort_pairs": [vp, vp, i64, i32, i32, i32, vp],
+        "isort_keys_host": [vp, vp, i64, i32, i32, vp],
+        "isort_pairs_host": [vp, vp, vp, vp, i64, i32, i32, i32, vp],
         "isort_segmented": [vp, vp, vp, i64, i64, i32, i32, i32, vp],
         "isort_workspace_size": [i64, i32, i32, i32, ctypes.POINTER(sz)],
         "isort_set_workspace": [vp, sz, vp],

@@ -35,10 +35,9 @@ int64_t g_stall_tile = -1;
 std::map<int, int> g_sms;  // device -> SM count
 KernelTimer g_timer;
 bool g_timing = false;
-unsigned long long* g_trace = nullptr;
-int g_trace_pass = 0;
 int64_t g_prefetch = -1;  // L2 prefetch distance in tiles; -1: one wave (SMs x 4)
 uint32_t g_check_mode = 0;  // test hook of the ordered keys-only rounds
+int g_host_copy = 0;        // host-buffer sorts: 0 auto (copy engines), 1 copy engines, 2 kernels
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -264,16 +263,41 @@ isort_status resolve_radix(int radix_bits, int* out) {
   return ISORT_OK;
 }
 
+// Host buffers of a host-buffer sort: inputs copied to the device, results back.
+struct HostIo {
+  const void* keys_in;
+  const void* vals_in;  // null: keys only
+  void* keys_out;
+  void* vals_out;
+};
+
+// One LSD sort of device keys[0..n) (and vals). With io, keys and vals are
+// ignored: the sort runs on device copies of io's inputs, placed in the
+// stream's workspace after the sort's own layout, and writes io's outputs.
 isort_status run_lsd(void* keys, void* vals, int64_t n, int key_bits, int val_bits,
-                     int radix_bits, cudaStream_t st) {
+                     int radix_bits, cudaStream_t st, const HostIo* io = nullptr) {
   std::lock_guard<std::mutex> lock(g_mu);
   const LsdEntry* e = pick(key_bits, val_bits, radix_bits, n);
   if (!e) return ISORT_EUNSUPPORTED;
   Layout L = layout_for(*e, n);
+  const size_t kbytes = (size_t)n * (key_bits / 8), vbytes = (size_t)n * (val_bits / 8);
+  size_t total = L.total, dev_k = 0, dev_v = 0;
+  if (io) {
+    dev_k = total;
+    total = align256(dev_k + kbytes);
+    if (io->vals_in) {
+      dev_v = total;
+      total = align256(dev_v + vbytes);
+    }
+  }
   void* ws = nullptr;
-  isort_status s = acquire(st, L.total, &ws);
+  isort_status s = acquire(st, total, &ws);
   if (s != ISORT_OK) return s;
   char* b = static_cast<char*>(ws);
+  if (io) {
+    keys = b + dev_k;
+    vals = io->vals_in ? b + dev_v : nullptr;
+  }
   LsdArgs a;
   a.keys = keys;
   a.vals = vals;
@@ -291,8 +315,6 @@ isort_status run_lsd(void* keys, void* vals, int64_t n, int key_bits, int val_bi
   a.stall_tile = g_stall_tile;
   g_stall_tile = -1;  // the stall hook applies to one sort only
   a.num_sms = num_sms();
-  a.trace = g_trace;
-  a.trace_pass = g_trace_pass;
   a.prefetch_tiles = g_prefetch < 0 ? (int64_t)a.num_sms * 4 : g_prefetch;
   a.check_mode = g_check_mode;
   a.timer = nullptr;
@@ -304,7 +326,18 @@ isort_status run_lsd(void* keys, void* vals, int64_t n, int key_bits, int val_bi
     g_timer.count = 0;
     a.timer = &g_timer;
   }
-  cudaError_t ce = e->launch(a, st);
+  cudaError_t ce = cudaSuccess;
+  if (io) {
+    ce = copy_host_io(keys, io->keys_in, kbytes, true, g_host_copy, a.num_sms, a.timer, st);
+    if (ce == cudaSuccess && vals)
+      ce = copy_host_io(vals, io->vals_in, vbytes, true, g_host_copy, a.num_sms, a.timer, st);
+  }
+  if (ce == cudaSuccess) ce = e->launch(a, st);
+  if (io && ce == cudaSuccess) {
+    ce = copy_host_io(io->keys_out, keys, kbytes, false, g_host_copy, a.num_sms, a.timer, st);
+    if (ce == cudaSuccess && vals)
+      ce = copy_host_io(io->vals_out, vals, vbytes, false, g_host_copy, a.num_sms, a.timer, st);
+  }
   return ce == cudaSuccess ? ISORT_OK : ISORT_ECUDA;
 }
 
@@ -475,6 +508,56 @@ isort_status isort_pairs(void* keys, void* vals, int64_t n, int key_bits, int va
   if (!keys || !vals || !aligned(keys, key_bits / 8) || !aligned(vals, val_bits / 8))
     return ISORT_EINVAL;
   return run_lsd(keys, vals, n, key_bits, val_bits, rb, static_cast<cudaStream_t>(stream));
+}
+
+isort_status isort_keys_host(const void* keys_in, void* keys_out, int64_t n, int key_bits,
+                             int radix_bits, void* stream) {
+  isort_status s = check_widths(key_bits, 0, false);
+  if (s != ISORT_OK) return s;
+  int rb = 0;
+  if ((s = resolve_radix(radix_bits, &rb)) != ISORT_OK) return s;
+  if (n < 0) return ISORT_EINVAL;
+  if (n > kMaxN) return ISORT_EUNSUPPORTED;
+  if (n == 0) return ISORT_OK;
+  if (!keys_in || !keys_out || !aligned(keys_in, key_bits / 8) || !aligned(keys_out, key_bits / 8))
+    return ISORT_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (n == 1) {
+    if (keys_in == keys_out) return ISORT_OK;
+    return cudaMemcpyAsync(keys_out, keys_in, key_bits / 8, cudaMemcpyDefault, st) == cudaSuccess
+               ? ISORT_OK
+               : ISORT_ECUDA;
+  }
+  const HostIo io{keys_in, nullptr, keys_out, nullptr};
+  return run_lsd(nullptr, nullptr, n, key_bits, 0, rb, st, &io);
+}
+
+isort_status isort_pairs_host(const void* keys_in, const void* vals_in, void* keys_out,
+                              void* vals_out, int64_t n, int key_bits, int val_bits,
+                              int radix_bits, void* stream) {
+  isort_status s = check_widths(key_bits, val_bits, true);
+  if (s != ISORT_OK) return s;
+  int rb = 0;
+  if ((s = resolve_radix(radix_bits, &rb)) != ISORT_OK) return s;
+  if (n < 0) return ISORT_EINVAL;
+  if (n > kMaxN) return ISORT_EUNSUPPORTED;
+  if (n == 0) return ISORT_OK;
+  if (!keys_in || !keys_out || !vals_in || !vals_out || !aligned(keys_in, key_bits / 8) ||
+      !aligned(keys_out, key_bits / 8) || !aligned(vals_in, val_bits / 8) ||
+      !aligned(vals_out, val_bits / 8))
+    return ISORT_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (n == 1) {
+    if (keys_in != keys_out &&
+        cudaMemcpyAsync(keys_out, keys_in, key_bits / 8, cudaMemcpyDefault, st) != cudaSuccess)
+      return ISORT_ECUDA;
+    if (vals_in != vals_out &&
+        cudaMemcpyAsync(vals_out, vals_in, val_bits / 8, cudaMemcpyDefault, st) != cudaSuccess)
+      return ISORT_ECUDA;
+    return ISORT_OK;
+  }
+  const HostIo io{keys_in, vals_in, keys_out, vals_out};
+  return run_lsd(nullptr, nullptr, n, key_bits, val_bits, rb, st, &io);
 }
 
 isort_status isort_sample_sort(void* keys, void* vals, int64_t n, int key_bits, int val_bits,
@@ -832,18 +915,16 @@ isort_status isort_debug_set(int what, int64_t value) {
     case ISORT_DEBUG_KERNEL_TIMING:
       g_timing = value != 0;
       return ISORT_OK;
-    case ISORT_DEBUG_TRACE_PTR:
-      g_trace = reinterpret_cast<unsigned long long*>(value);
-      return ISORT_OK;
-    case ISORT_DEBUG_TRACE_PASS:
-      g_trace_pass = (int)value;
-      return ISORT_OK;
     case ISORT_DEBUG_PREFETCH_TILES:
       g_prefetch = value;
       return ISORT_OK;
     case ISORT_DEBUG_CHECK_MODE:
       if (value < 0 || value > 2) return ISORT_EINVAL;
       g_check_mode = (uint32_t)value;
+      return ISORT_OK;
+    case ISORT_DEBUG_HOST_COPY:
+      if (value < 0 || value > 2) return ISORT_EINVAL;
+      g_host_copy = (int)value;
       return ISORT_OK;
   }
   return ISORT_EINVAL;

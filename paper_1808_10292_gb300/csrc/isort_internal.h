@@ -39,13 +39,19 @@ struct LsdArgs {
   int64_t stall_tile;   // test hook (-1 = off)
   int num_sms;
   KernelTimer* timer;   // null unless kernel timing is on
-  unsigned long long* trace;  // measurement hook: per-tile phase timestamps of one pass
-  int trace_pass;
   int64_t prefetch_tiles;     // L2 prefetch distance of the rounds, in tiles (0: off)
   uint32_t check_mode;        // test hook of the ordered keys-only rounds (0: normal)
 };
 
 typedef cudaError_t (*LsdLaunchFn)(const LsdArgs&, cudaStream_t);
+
+// Copies `bytes` (a multiple of 4) between a host buffer and device memory on
+// `st` (to_device: src is the host buffer). Modes 0 and 1 use cudaMemcpyAsync;
+// mode 2 uses a copy kernel when the host buffer is page-locked, mapped into
+// the device's address space at its own address and 16-byte aligned, else
+// cudaMemcpyAsync.
+cudaError_t copy_host_io(void* dst, const void* src, size_t bytes, bool to_device, int mode,
+                         int num_sms, KernelTimer* timer, cudaStream_t st);
 
 // One compiled kernel family for (key_bits, val_bits, radix_bits, variant).
 struct LsdEntry {

@@ -116,8 +116,6 @@ extern "C" isort_status isort_keys_noalloc(void* keys, int64_t n, uint32_t* err_
   a.stall_tile = -1;
   a.num_sms = sms;
   a.timer = nullptr;
-  a.trace = nullptr;
-  a.trace_pass = -1;
   a.prefetch_tiles = (int64_t)sms * 4;
   a.check_mode = 0;
   return e.launch(a, st) == cudaSuccess ? ISORT_OK : ISORT_ECUDA;

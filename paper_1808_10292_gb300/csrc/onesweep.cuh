@@ -189,7 +189,6 @@ struct PassParams {
   uint32_t* err;
   uint32_t spin_limit;
   int64_t stall_tile;
-  unsigned long long* trace;  // measurement hook: per tile, phase timestamps (or null)
   int64_t prefetch_tiles;     // L2-prefetch the input of the tile this many ids ahead (0: off)
   uint32_t check_mode;        // test hook of the ordered rounds (kCheck*; 0 in normal use)
   uint32_t byte_sel;          // radix-256 rounds: radix8_byte_sel(shift)
@@ -962,7 +961,7 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
       return e;
   }
-  // keys only: pass 0 is the order-free round (k_onesweep_first), unless it is traced
+  // keys only: pass 0 is the order-free round (k_onesweep_first)
   using FC = FirstCfg<K, THREADS, KPT, MINB>;
   constexpr size_t fsmem = FirstShape<K, BITS, FC::T, FC::KP>::SMEM;
   if constexpr (!HV && fsmem > 48 * 1024) {
@@ -981,10 +980,9 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
     pp.status_next = (q + 1 < P) ? a.status[(q + 1) & 1] : nullptr;
     pp.counter = a.counters + q;
     pp.stall_tile = (q == 0) ? a.stall_tile : -1;
-    pp.trace = (q == a.trace_pass) ? a.trace : nullptr;
     bool launched = false;
     if constexpr (!HV) {
-      if (q == 0 && !pp.trace) {
+      if (q == 0) {
         timer_begin(a.timer, "k_onesweep_first", st);
         k_onesweep_first<K, BITS, FC::T, FC::KP, MINB><<<(unsigned)tiles, FC::T, fsmem, st>>>(pp);
         launched = true;

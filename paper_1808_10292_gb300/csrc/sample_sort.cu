@@ -307,7 +307,6 @@ cudaError_t gvr_launch(const GvrArgs& a, cudaStream_t st) {
   pp.err = a.err;
   pp.spin_limit = a.spin_limit;
   pp.stall_tile = -1;
-  pp.trace = nullptr;
   pp.prefetch_tiles = (int64_t)a.num_sms * 4;
   pp.check_mode = kCheckNormal;
   // keys only: the order-free round, in its own CTA shape (same tile)

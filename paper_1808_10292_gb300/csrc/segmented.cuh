@@ -487,7 +487,6 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
   pp.err = a.err;
   pp.spin_limit = a.spin_limit;
   pp.stall_tile = -1;
-  pp.trace = nullptr;
   pp.prefetch_tiles = 0;
   pp.check_mode = a.check_mode;
   for (int q = 0; q < P; ++q) {

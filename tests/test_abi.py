@@ -51,6 +51,24 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.isort_keys(None, 1, 64, 8, None) == _lib.OK   # one key: no-op
     assert lib.isort_pairs(dummy, None, 10, 32, 32, 8, None) == _lib.EINVAL
     assert lib.isort_pairs(dummy, dummy, 10, 32, 16, 8, None) == _lib.EINVAL
+    # host-buffer entry points: the same checks, no device work for n <= 1 in place
+    assert lib.isort_keys_host(dummy, dummy, 10, 16, 8, None) == _lib.EINVAL
+    assert lib.isort_keys_host(None, dummy, 10, 32, 8, None) == _lib.EINVAL
+    assert lib.isort_keys_host(dummy, None, 10, 32, 8, None) == _lib.EINVAL
+    assert lib.isort_keys_host(ctypes.c_void_p(258), dummy, 10, 32, 8, None) == _lib.EINVAL
+    assert lib.isort_keys_host(dummy, dummy, -1, 32, 8, None) == _lib.EINVAL
+    assert lib.isort_keys_host(dummy, dummy, (1 << 30) + 1, 32, 8, None) == _lib.EUNSUPPORTED
+    assert lib.isort_keys_host(dummy, dummy, 10, 32, 12, None) == _lib.EUNSUPPORTED
+    assert lib.isort_keys_host(None, None, 0, 32, 8, None) == _lib.OK
+    assert lib.isort_keys_host(dummy, dummy, 1, 32, 8, None) == _lib.OK   # in place: nothing
+    assert lib.isort_pairs_host(dummy, None, dummy, dummy, 10, 32, 32, 8, None) == _lib.EINVAL
+    assert lib.isort_pairs_host(dummy, dummy, dummy, None, 10, 32, 32, 8, None) == _lib.EINVAL
+    assert lib.isort_pairs_host(dummy, dummy, dummy, dummy, 10, 32, 16, 8, None) == _lib.EINVAL
+    assert lib.isort_pairs_host(dummy, ctypes.c_void_p(260), dummy, dummy, 10, 32, 64, 8,
+                                None) == _lib.EINVAL                      # misaligned payloads
+    assert lib.isort_pairs_host(dummy, dummy, dummy, dummy, 1, 32, 32, 8, None) == _lib.OK
+    assert lib.isort_debug_set(_lib.DEBUG_HOST_COPY, 3) == _lib.EINVAL
+    assert lib.isort_debug_set(4, 0) == _lib.EINVAL                       # no such hook
     assert lib.isort_debug_set(99, 0) == _lib.EINVAL
     assert lib.isort_tune_segmented_network(32, 0, 2) == _lib.EINVAL    # no such network
     assert lib.isort_tune_segmented_network(16, 0, _lib.NET_OET) == _lib.EINVAL
