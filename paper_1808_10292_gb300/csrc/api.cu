@@ -151,7 +151,7 @@ const LsdEntry* pick(int key_bits, int val_bits, int radix_bits, int64_t n) {
 // Workspace layout of one LSD sort. The error word sits at offset 0 so it
 // survives from call to call on the same workspace.
 struct Layout {
-  size_t err, hist, base, skip, counters, status0, status1, alt_k, alt_v, total;
+  size_t err, hist, base, skip, counters, claim, status0, status1, alt_k, alt_v, total;
 };
 
 Layout layout_for(const LsdEntry& e, int64_t n) {
@@ -163,6 +163,7 @@ Layout layout_for(const LsdEntry& e, int64_t n) {
   L.base = off;      off = align256(off + sizeof(uint32_t) * e.passes * e.radix);
   L.skip = off;      off = align256(off + sizeof(uint32_t) * e.passes);
   L.counters = off;  off = align256(off + sizeof(uint32_t) * e.passes);
+  L.claim = off;     off = align256(off + sizeof(uint32_t) * e.radix);
   L.status0 = off;   off = align256(off + sizeof(uint32_t) * e.status_words_per_tile * tiles);
   L.status1 = off;
   if (e.status_buffers > 1)
@@ -218,7 +219,8 @@ int64_t seg_btn_max(const SegConfig& c) {
 }
 
 struct SegLayout {
-  size_t err, cnt, lists, slot_first, tile_slot, seg_hist, seg_base, seg_skip, status0, status1,
+  size_t err, cnt, lists, slot_first, tile_slot, seg_hist, seg_base, seg_skip, seg_claim, status0,
+      status1,
       alt_k, alt_v, total;
   int64_t max_tiles;
 };
@@ -240,6 +242,7 @@ SegLayout seg_layout(const SegConfig& c, int64_t nseg, int64_t total, int64_t bt
   L.seg_hist = off;    off = align256(off + per_slot * (size_t)nseg);
   L.seg_base = off;    off = align256(off + per_slot * (size_t)nseg);
   L.seg_skip = off;    off = align256(off + sizeof(uint32_t) * (size_t)c.passes * nseg);
+  L.seg_claim = off;   off = align256(off + sizeof(uint32_t) * (size_t)c.radix * nseg);
   L.status0 = off;     off = align256(off + sizeof(uint32_t) * c.radix * (size_t)L.max_tiles);
   L.status1 = off;     off = align256(off + sizeof(uint32_t) * c.radix * (size_t)L.max_tiles);
   L.alt_k = off;       off = align256(off + (size_t)total * (c.key_bits / 8));
@@ -308,6 +311,7 @@ isort_status run_lsd(void* keys, void* vals, int64_t n, int key_bits, int val_bi
   a.base = reinterpret_cast<uint32_t*>(b + L.base);
   a.skip = reinterpret_cast<uint32_t*>(b + L.skip);
   a.counters = reinterpret_cast<uint32_t*>(b + L.counters);
+  a.claim = reinterpret_cast<uint32_t*>(b + L.claim);
   a.status[0] = reinterpret_cast<uint32_t*>(b + L.status0);
   a.status[1] = reinterpret_cast<uint32_t*>(b + L.status1);
   a.err = reinterpret_cast<uint32_t*>(b + L.err);
@@ -388,6 +392,7 @@ SegArgs seg_args(const SegConfig& c, const SegLayout& L, char* b, void* keys, vo
   a.seg_hist = reinterpret_cast<uint32_t*>(b + L.seg_hist);
   a.seg_base = reinterpret_cast<uint32_t*>(b + L.seg_base);
   a.seg_skip = reinterpret_cast<uint32_t*>(b + L.seg_skip);
+  a.seg_claim = reinterpret_cast<uint32_t*>(b + L.seg_claim);
   a.status[0] = reinterpret_cast<uint32_t*>(b + L.status0);
   a.status[1] = reinterpret_cast<uint32_t*>(b + L.status1);
   a.err = reinterpret_cast<uint32_t*>(b + L.err);
@@ -410,7 +415,7 @@ SegArgs seg_args(const SegConfig& c, const SegLayout& L, char* b, void* keys, vo
 // at offset 0), then the bucketed copy of the input and the split round's arrays.
 struct GvrLayout {
   SegLayout seg;
-  size_t out_k, out_v, split, cell, hist, base, skip, counter, status, offsets, total;
+  size_t out_k, out_v, split, cell, hist, base, skip, counter, status, claim, offsets, total;
 };
 
 GvrLayout gvr_layout(const SegConfig& c, int64_t n, int buckets) {
@@ -427,6 +432,7 @@ GvrLayout gvr_layout(const SegConfig& c, int64_t n, int buckets) {
   G.skip = off;     off = align256(off + sizeof(uint32_t));
   G.counter = off;  off = align256(off + sizeof(uint32_t));
   G.status = off;   off = align256(off + sizeof(uint32_t) * 256 * (size_t)tiles);
+  G.claim = off;    off = align256(off + 256 * sizeof(uint32_t));
   G.offsets = off;  off = align256(off + sizeof(int64_t) * (size_t)(buckets + 1));
   G.total = off;
   return G;
@@ -596,6 +602,7 @@ isort_status isort_sample_sort(void* keys, void* vals, int64_t n, int key_bits, 
   g.skip = reinterpret_cast<uint32_t*>(b + G.skip);
   g.counter = reinterpret_cast<uint32_t*>(b + G.counter);
   g.status = reinterpret_cast<uint32_t*>(b + G.status);
+  g.claim = reinterpret_cast<uint32_t*>(b + G.claim);
   g.offsets = reinterpret_cast<int64_t*>(b + G.offsets);
   g.counts_out = bucket_counts;
   g.err = sa.err;

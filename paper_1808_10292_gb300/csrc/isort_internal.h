@@ -33,6 +33,8 @@ struct LsdArgs {
   uint32_t* base;       // workspace: passes * R global digit bases
   uint32_t* skip;       // workspace: passes flags (1 = trivial pass)
   uint32_t* counters;   // workspace: passes tile-id counters (zeroed by the launcher)
+  uint32_t* claim;      // workspace: R output cursors of the order-free first round (keys
+                        // only; zeroed by the launcher), or null: that round looks back
   uint32_t* status[2];  // workspace: tiles * R look-back words each
   uint32_t* err;        // workspace: latched device error word
   uint32_t spin_limit;  // polls before a wait gives up
@@ -101,6 +103,7 @@ struct SegArgs {
   uint32_t* seg_hist;    // [nseg][P][R]
   uint32_t* seg_base;    // [nseg][P][R]
   uint32_t* seg_skip;    // [nseg][P] trivial passes of each radix range
+  uint32_t* seg_claim;   // [nseg][R] keys only: the first round's output cursors per range
   uint32_t* status[2];   // [max_tiles][R]
   uint32_t* err;
   uint32_t spin_limit;
@@ -136,7 +139,8 @@ struct GvrArgs {
   uint32_t* base;        // [256] bucket bases
   uint32_t* skip;        // [1]
   uint32_t* counter;     // [1] tile-id counter
-  uint32_t* status;      // [tiles][256] look-back words
+  uint32_t* status;      // [tiles][256] look-back words (payloads only)
+  uint32_t* claim;       // [256] keys only: the split round's output cursors
   int64_t* offsets;      // [buckets + 1] bucket offsets for the segmented sort
   uint32_t* counts_out;  // [buckets] caller's copy of the bucket counts, or nullptr
   uint32_t* err;

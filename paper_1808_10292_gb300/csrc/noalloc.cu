@@ -80,14 +80,15 @@ extern "C" isort_status isort_keys_noalloc(void* keys, int64_t n, uint32_t* err_
     sms = g_sms[dev];
   }
 
-  // Carve the array: histograms, bases, flags, counters, the two look-back
-  // arrays, the alternate key buffer.
+  // Carve the array: histograms, bases, flags, counters, the first round's
+  // output cursors, the two look-back arrays, the alternate key buffer.
   const int64_t tiles = (n + e.tile - 1) / e.tile;
   size_t off = 0;
   const size_t hist = off;     off = align256(off + sizeof(uint32_t) * e.passes * e.radix);
   const size_t bases = off;    off = align256(off + sizeof(uint32_t) * e.passes * e.radix);
   const size_t skip = off;     off = align256(off + sizeof(uint32_t) * e.passes);
   const size_t counters = off; off = align256(off + sizeof(uint32_t) * e.passes);
+  const size_t claim = off;    off = align256(off + sizeof(uint32_t) * e.radix);
   const size_t status0 = off;  off = align256(off + sizeof(uint32_t) * e.status_words_per_tile * tiles);
   const size_t status1 = off;  off = align256(off + sizeof(uint32_t) * e.status_words_per_tile * tiles);
   const size_t alt = off;      off = align256(off + sizeof(uint32_t) * (size_t)n);
@@ -96,8 +97,9 @@ extern "C" isort_status isort_keys_noalloc(void* keys, int64_t n, uint32_t* err_
   char* b = static_cast<char*>(base);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // The array keeps the previous call's contents. The launcher clears the
-  // histograms, the tile counters and the first look-back array; every other
-  // piece is written before it is read.
+  // histograms, the tile counters and the first round's cursors (and the first
+  // look-back array when the first round looks back); every other piece is
+  // written before it is read.
 
   LsdArgs a;
   a.keys = keys;
@@ -109,6 +111,7 @@ extern "C" isort_status isort_keys_noalloc(void* keys, int64_t n, uint32_t* err_
   a.base = reinterpret_cast<uint32_t*>(b + bases);
   a.skip = reinterpret_cast<uint32_t*>(b + skip);
   a.counters = reinterpret_cast<uint32_t*>(b + counters);
+  a.claim = reinterpret_cast<uint32_t*>(b + claim);
   a.status[0] = reinterpret_cast<uint32_t*>(b + status0);
   a.status[1] = reinterpret_cast<uint32_t*>(b + status1);
   a.err = err_out;

@@ -137,10 +137,13 @@ __global__ void __launch_bounds__(THREADS) k_hist(const K* __restrict__ keys, in
 // ---------------------------------------------------------------------------
 // k_scan: block p turns hist[p][0..R) into exclusive prefix sums base[p][..]
 // and sets skip[p] when one digit holds all n keys.
+// Also zeroes `claim` (R words, or null): the output cursors of the order-free
+// first round (onesweep_tile_first), which start from the bases.
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS) k_scan(const uint32_t* __restrict__ hist,
                                                   uint32_t* __restrict__ base,
-                                                  uint32_t* __restrict__ skip, int R, int64_t n) {
+                                                  uint32_t* __restrict__ skip, int R, int64_t n,
+                                                  uint32_t* __restrict__ claim) {
   __shared__ uint32_t s_warp[THREADS / 32];
   __shared__ uint32_t s_trivial;
   const int p = blockIdx.x;
@@ -171,6 +174,8 @@ __global__ void __launch_bounds__(THREADS) k_scan(const uint32_t* __restrict__ h
     }
   }
   if (threadIdx.x == 0) skip[p] = s_trivial;
+  if (claim && p == 0)
+    for (int d = threadIdx.x; d < R; d += THREADS) claim[d] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -186,6 +191,8 @@ struct PassParams {
   uint32_t* status;       // [tiles][R] this pass's look-back words, zeroed
   uint32_t* status_next;  // [tiles][R] zeroed here for the next pass, or null
   uint32_t* counter;      // this pass's tile-id counter, zeroed
+  uint32_t* claim;        // [R] order-free first round: per-digit output cursors, zeroed
+                          // (null: that round uses the look-back too)
   uint32_t* err;
   uint32_t spin_limit;
   int64_t stall_tile;
@@ -784,14 +791,19 @@ struct FirstShape {
   static constexpr size_t SMEM = (size_t)HEADER_WORDS * 4 + (size_t)S::TILE * sizeof(K);
 };
 
-// Arguments as for onesweep_tile_early (keys only).
+// Arguments as for onesweep_tile_ordered (keys only). With `claim` (R words
+// starting at zero before the round) a tile takes each digit's output range
+// with one global atomic add of its count on the digit's cursor, instead of a
+// look-back over earlier tiles: the round is order-free, so the tiles' runs of
+// a digit may lie in any order, and no tile waits on another. Without it the
+// tile publishes its counts and looks back like the ordered round.
 template <typename K, int BITS, int THREADS, int KPT, bool FULL, typename DS = RadixDigit>
 __device__ __forceinline__ void onesweep_tile_first(const PassParams& p, uint32_t tile, bool first,
                                                     int64_t tile_base, int tile_n,
                                                     const K* __restrict__ kin,
                                                     K* __restrict__ kout, const uint32_t* base,
                                                     uint32_t bound, unsigned char* smem,
-                                                    DS& dig) {
+                                                    DS& dig, uint32_t* claim = nullptr) {
   using S = OnesweepShape<K, NoVal, BITS, THREADS, KPT>;
   using F = FirstShape<K, BITS, THREADS, KPT>;
   constexpr int R = S::R, DPT = S::DPT;
@@ -812,7 +824,7 @@ __device__ __forceinline__ void onesweep_tile_first(const PassParams& p, uint32_
     if (FULL || wofs + i * 32 < tile_n) atomicAdd(&s_slot[dig.of(key[i], i)], 1u);
   __syncthreads();
 
-  uint32_t dcnt[DPT];
+  uint32_t dcnt[DPT], claimed[DPT];
   uint32_t tsum = 0;
   const bool owner = tid < S::DTHREADS;
   if (owner) {
@@ -820,9 +832,13 @@ __device__ __forceinline__ void onesweep_tile_first(const PassParams& p, uint32_
     for (int j = 0; j < DPT; ++j) {
       dcnt[j] = s_slot[tid * DPT + j];
       tsum += dcnt[j];
-      if (publish)
+      claimed[j] = 0;
+      if (claim) {  // the add returns before it is needed (after the placement)
+        if (dcnt[j]) claimed[j] = atomicAdd(&claim[tid * DPT + j], dcnt[j]);
+      } else if (publish) {
         st_relaxed(&p.status[(size_t)tile * R + tid * DPT + j],
                    (first ? kFlagInc : kFlagAgg) | dcnt[j]);
+      }
     }
   }
   uint32_t total;
@@ -851,8 +867,8 @@ __device__ __forceinline__ void onesweep_tile_first(const PassParams& p, uint32_
 #pragma unroll
     for (int j = 0; j < DPT; ++j) {
       const int d = tid * DPT + j;
-      uint32_t excl = 0;
-      if (!first) {
+      uint32_t excl = claimed[j];
+      if (!claim && !first) {
         excl = lookback_exclusive<R, kLookbackWindow>(p.status, tile, d, p.spin_limit, p.err,
                                                       windows);
         if (publish) st_relaxed(&p.status[(size_t)tile * R + d], kFlagInc | (excl + dcnt[j]));
@@ -888,10 +904,12 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep_first(PassParams p) 
   RadixDigit dig{p};
   if (tile_n == TILE)
     onesweep_tile_first<K, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n, kin,
-                                                     kout, p.base, (uint32_t)p.n, smem, dig);
+                                                     kout, p.base, (uint32_t)p.n, smem, dig,
+                                                     p.claim);
   else
     onesweep_tile_first<K, BITS, THREADS, KPT, false>(p, tile, tile == 0, tile_base, tile_n, kin,
-                                                      kout, p.base, (uint32_t)p.n, smem, dig);
+                                                      kout, p.base, (uint32_t)p.n, smem, dig,
+                                                      p.claim);
 }
 
 // ---------------------------------------------------------------------------
@@ -925,7 +943,9 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
   // hist and counters are zeroed; status[0] too (later passes clear their own)
   if ((e = cudaMemsetAsync(a.hist, 0, sizeof(uint32_t) * P * R, st))) return e;
   if ((e = cudaMemsetAsync(a.counters, 0, sizeof(uint32_t) * P, st))) return e;
-  if ((e = cudaMemsetAsync(a.status[0], 0, sizeof(uint32_t) * R * tiles, st))) return e;
+  // status[0] serves pass 0 only when that pass looks back (payloads: every
+  // round is ordered); later passes clear their successor's rows themselves
+  if (HV && (e = cudaMemsetAsync(a.status[0], 0, sizeof(uint32_t) * R * tiles, st))) return e;
 
   // 32 counter columns for 32-bit keys (4 passes: 128 KiB), 16 for 64-bit
   // keys (8 passes: 128 KiB); one 1024-thread CTA per SM.
@@ -941,7 +961,7 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
   hk<<<hblocks, HT, HS::SMEM, st>>>(static_cast<const K*>(a.keys), a.n, a.hist);
   timer_end(a.timer, st);
   timer_begin(a.timer, "k_scan", st);
-  k_scan<256><<<P, 256, 0, st>>>(a.hist, a.base, a.skip, R, a.n);
+  k_scan<256><<<P, 256, 0, st>>>(a.hist, a.base, a.skip, R, a.n, HV ? nullptr : a.claim);
   timer_end(a.timer, st);
 
   PassParams pp;
@@ -979,7 +999,9 @@ cudaError_t lsd_launch(const LsdArgs& a, cudaStream_t st) {
     pp.status = a.status[q & 1];
     pp.status_next = (q + 1 < P) ? a.status[(q + 1) & 1] : nullptr;
     pp.counter = a.counters + q;
-    pp.stall_tile = (q == 0) ? a.stall_tile : -1;
+    pp.claim = (!HV && q == 0) ? a.claim : nullptr;
+    // the stall hook applies to the first round with a look-back
+    pp.stall_tile = (q == (HV ? 0 : 1)) ? a.stall_tile : -1;
     bool launched = false;
     if constexpr (!HV) {
       if (q == 0) {

@@ -10,9 +10,11 @@
 //   k_gvr_scan    bucket bases (the round's digit bases), the int64 bucket
 //                 offsets for the segmented sort, the caller's bucket counts.
 //   k_gvr_split   one count-sort round with digit = bucket: the radix-256
-//                 round's tile machinery (early counts, look-back, scatter)
-//                 with the bucket as the digit. Stable, so payloads keep input
-//                 order inside a bucket.
+//                 round's tile machinery with the bucket as the digit. With
+//                 payloads the ordered round (early counts, look-back,
+//                 scatter; stable, so payloads keep input order inside a
+//                 bucket); keys only the order-free round, whose tiles take
+//                 their bucket ranges from per-bucket cursors.
 // The buckets are then sorted independently by the segmented sort (the
 // paper's step 4 sorts each with SR4); that part lives in api.cu.
 #include "segmented.cuh"
@@ -185,13 +187,15 @@ __global__ void __launch_bounds__(256) k_gvr_scan(const uint32_t* __restrict__ h
                                                   int64_t n, uint32_t* __restrict__ base,
                                                   int64_t* __restrict__ offsets,
                                                   uint32_t* __restrict__ counts_out,
-                                                  uint32_t* __restrict__ skip) {
+                                                  uint32_t* __restrict__ skip,
+                                                  uint32_t* __restrict__ claim) {
   __shared__ uint32_t s_warp[8];
   const int b = threadIdx.x;
   const uint32_t c = b < buckets ? hist[b] : 0u;
   uint32_t tot;
   const uint32_t start = block_exclusive_scan<256>(c, s_warp, tot);
   base[b] = start;
+  if (claim) claim[b] = 0;  // the keys-only split round's cursors
   if (b < buckets) {
     offsets[b] = start;
     if (counts_out) counts_out[b] = c;
@@ -244,10 +248,12 @@ __global__ void __launch_bounds__(THREADS, MINB) k_gvr_split(PassParams p,
     dig.s_slot = smem + FirstShape<K, 8, THREADS, KPT>::SMEM;
     if (tile_n == TILE)
       onesweep_tile_first<K, 8, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n, kin,
-                                                    kout, p.base, (uint32_t)p.n, smem, dig);
+                                                    kout, p.base, (uint32_t)p.n, smem, dig,
+                                                    p.claim);
     else
       onesweep_tile_first<K, 8, THREADS, KPT, false>(p, tile, tile == 0, tile_base, tile_n, kin,
-                                                     kout, p.base, (uint32_t)p.n, smem, dig);
+                                                     kout, p.base, (uint32_t)p.n, smem, dig,
+                                                     p.claim);
     return;
   }
   dig.s_slot = smem + O::SMEM;
@@ -270,7 +276,10 @@ cudaError_t gvr_launch(const GvrArgs& a, cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(a.hist, 0, sizeof(uint32_t) * R, st))) return e;
   if ((e = cudaMemsetAsync(a.counter, 0, sizeof(uint32_t), st))) return e;
-  if ((e = cudaMemsetAsync(a.status, 0, sizeof(uint32_t) * R * tiles, st))) return e;
+  // keys only, the split round takes its ranges from cursors and needs no look-back words
+  if (HasVal<V>::value &&
+      (e = cudaMemsetAsync(a.status, 0, sizeof(uint32_t) * R * tiles, st)))
+    return e;
   const K* keys = static_cast<const K*>(a.keys);
   K* split = static_cast<K*>(a.split);
 
@@ -285,7 +294,8 @@ cudaError_t gvr_launch(const GvrArgs& a, cudaStream_t st) {
   k_gvr_hist<K><<<hblocks, 1024, 0, st>>>(keys, a.n, split, cell, a.hist);
   timer_end(a.timer, st);
   timer_begin(a.timer, "k_gvr_scan", st);
-  k_gvr_scan<<<1, 256, 0, st>>>(a.hist, a.buckets, a.n, a.base, a.offsets, a.counts_out, a.skip);
+  k_gvr_scan<<<1, 256, 0, st>>>(a.hist, a.buckets, a.n, a.base, a.offsets, a.counts_out, a.skip,
+                                HasVal<V>::value ? nullptr : a.claim);
   timer_end(a.timer, st);
 
   PassParams pp;
@@ -307,6 +317,7 @@ cudaError_t gvr_launch(const GvrArgs& a, cudaStream_t st) {
   pp.err = a.err;
   pp.spin_limit = a.spin_limit;
   pp.stall_tile = -1;
+  pp.claim = HasVal<V>::value ? nullptr : a.claim;
   pp.prefetch_tiles = (int64_t)a.num_sms * 4;
   pp.check_mode = kCheckNormal;
   // keys only: the order-free round, in its own CTA shape (same tile)

@@ -260,16 +260,19 @@ __global__ void __launch_bounds__(1024) k_seg_hist(const K* __restrict__ keys,
 
 // Per radix range: exclusive digit bases (relative to the range) of every
 // pass, and the range's trivial passes (one digit holds all its keys: the pass
-// is the identity on that range and is skipped for it).
+// is the identity on that range and is skipped for it). Also zeroes the
+// range's first-round output cursors (seg_claim, keys only; null otherwise).
 template <int BITS, int PASSES>
 __global__ void __launch_bounds__(1 << BITS) k_seg_scan(const uint32_t* __restrict__ cnt,
                                                        const uint32_t* __restrict__ seg_hist,
                                                        uint32_t* __restrict__ seg_base,
-                                                       uint32_t* __restrict__ seg_skip) {
+                                                       uint32_t* __restrict__ seg_skip,
+                                                       uint32_t* __restrict__ seg_claim) {
   constexpr int R = 1 << BITS;
   __shared__ uint32_t s_warp[R / 32];
   const uint32_t slot = blockIdx.x;
   if (slot >= cnt[kCntClassLen + kSegRadix]) return;
+  if (seg_claim) seg_claim[(size_t)slot * R + threadIdx.x] = 0;
   for (int p = 0; p < PASSES; ++p) {
     const size_t row = ((size_t)slot * PASSES + p) * R;
     uint32_t tot;
@@ -328,6 +331,7 @@ struct SegPassParams {
   const int32_t* tile_slot;
   const uint32_t* seg_base;
   const uint32_t* seg_skip;  // [slots][passes] 1 = the pass is the identity on the range
+  uint32_t* seg_claim;       // [slots][R] keys only: the first round's output cursors
   int passes;
 };
 
@@ -367,12 +371,16 @@ __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp
   const uint32_t* base = sp.seg_base + ((size_t)slot * sp.passes + p.pass) * R;
   RadixDigit dig{p};
   if constexpr (FIRST) {
+    // the range's tiles take their digit ranges from the range's cursors
+    uint32_t* claim = sp.seg_claim + (size_t)slot * R;
     if (tile_n == TILE)
       onesweep_tile_first<K, BITS, THREADS, KPT, true>(p, tile, lt == 0, tile_base, tile_n, kin,
-                                                       kout, base, (uint32_t)len, smem, dig);
+                                                       kout, base, (uint32_t)len, smem, dig,
+                                                       claim);
     else
       onesweep_tile_first<K, BITS, THREADS, KPT, false>(p, tile, lt == 0, tile_base, tile_n, kin,
-                                                        kout, base, (uint32_t)len, smem, dig);
+                                                        kout, base, (uint32_t)len, smem, dig,
+                                                        claim);
   } else {
     if (tile_n == TILE)
       onesweep_tile_ordered<K, V, BITS, THREADS, KPT, true>(p, tile, lt == 0, tile_base, tile_n,
@@ -395,7 +403,10 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
   const int64_t nslots = a.nseg;
   if ((e = cudaMemsetAsync(a.cnt, 0, sizeof(uint32_t) * kCntWords, st))) return e;
   if ((e = cudaMemsetAsync(a.seg_hist, 0, sizeof(uint32_t) * nslots * P * R, st))) return e;
-  if ((e = cudaMemsetAsync(a.status[0], 0, sizeof(uint32_t) * R * a.max_tiles, st))) return e;
+  // status[0] serves pass 0 only with payloads (keys only, pass 0 takes cursors)
+  if (HasVal<V>::value &&
+      (e = cudaMemsetAsync(a.status[0], 0, sizeof(uint32_t) * R * a.max_tiles, st)))
+    return e;
   if (a.nseg == 0) return cudaGetLastError();
 
   timer_begin(a.timer, "k_seg_classify", st);
@@ -448,7 +459,8 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
   }
   timer_end(a.timer, st);
   timer_begin(a.timer, "k_seg_scan", st);
-  k_seg_scan<8, P><<<(unsigned)nslots, R, 0, st>>>(a.cnt, a.seg_hist, a.seg_base, a.seg_skip);
+  k_seg_scan<8, P><<<(unsigned)nslots, R, 0, st>>>(a.cnt, a.seg_hist, a.seg_base, a.seg_skip,
+                                                   HasVal<V>::value ? nullptr : a.seg_claim);
   timer_end(a.timer, st);
 
   auto kern = k_seg_onesweep<K, V, 8, THREADS, KPT, MINB>;
@@ -475,6 +487,7 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
   sp.tile_slot = a.tile_slot;
   sp.seg_base = a.seg_base;
   sp.seg_skip = a.seg_skip;
+  sp.seg_claim = a.seg_claim;
   sp.passes = P;
   PassParams& pp = sp.p;
   pp.keys[0] = a.keys;
@@ -487,6 +500,7 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
   pp.err = a.err;
   pp.spin_limit = a.spin_limit;
   pp.stall_tile = -1;
+  pp.claim = nullptr;
   pp.prefetch_tiles = 0;
   pp.check_mode = a.check_mode;
   for (int q = 0; q < P; ++q) {

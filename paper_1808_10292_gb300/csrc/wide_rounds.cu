@@ -408,6 +408,7 @@ cudaError_t wide_launch(const LsdArgs& a, cudaStream_t st) {
   pp.err = a.err;
   pp.spin_limit = a.spin_limit;
   pp.stall_tile = -1;
+  pp.claim = nullptr;
   pp.prefetch_tiles = a.prefetch_tiles;
   pp.check_mode = a.check_mode;
   pp.status_next = nullptr;
