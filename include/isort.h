@@ -256,9 +256,11 @@ isort_status isort_tune_resolve(int64_t n, int key_bits, int val_bits, int radix
 
 /* Test hooks. isort_debug_set(ISORT_DEBUG_SPIN_LIMIT, k): bounded waits give up
  * after k polls (0 restores the default). isort_debug_set(ISORT_DEBUG_STALL_TILE,
- * t): in pass 0 of the next radix-256 sort, tile t never publishes its counts
- * so its successors' waits run out (-1 = off; the sort's output is then garbage
- * and isort_stream_status reports ISORT_ETIMEOUT). */
+ * t): in the first round with a look-back of the next radix-256 sort (pass 1
+ * of a keys-only sort, whose order-free pass 0 needs none; pass 0 with
+ * payloads), tile t never publishes its counts so its successors' waits run
+ * out (-1 = off; the sort's output is then garbage and isort_stream_status
+ * reports ISORT_ETIMEOUT). */
 enum {
   ISORT_DEBUG_SPIN_LIMIT = 1,
   ISORT_DEBUG_STALL_TILE = 2,
