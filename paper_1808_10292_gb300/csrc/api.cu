@@ -163,7 +163,8 @@ Layout layout_for(const LsdEntry& e, int64_t n) {
   L.base = off;      off = align256(off + sizeof(uint32_t) * e.passes * e.radix);
   L.skip = off;      off = align256(off + sizeof(uint32_t) * e.passes);
   L.counters = off;  off = align256(off + sizeof(uint32_t) * e.passes);
-  L.claim = off;     off = align256(off + sizeof(uint32_t) * e.radix);
+  // the first round's cursors: R (plus 256 for a wide radix's two order-free steps)
+  L.claim = off;     off = align256(off + sizeof(uint32_t) * (e.radix + 256));
   L.status0 = off;   off = align256(off + sizeof(uint32_t) * e.status_words_per_tile * tiles);
   L.status1 = off;
   if (e.status_buffers > 1)

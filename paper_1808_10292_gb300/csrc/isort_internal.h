@@ -33,8 +33,8 @@ struct LsdArgs {
   uint32_t* base;       // workspace: passes * R global digit bases
   uint32_t* skip;       // workspace: passes flags (1 = trivial pass)
   uint32_t* counters;   // workspace: passes tile-id counters (zeroed by the launcher)
-  uint32_t* claim;      // workspace: R output cursors of the order-free first round (keys
-                        // only; zeroed by the launcher), or null: that round looks back
+  uint32_t* claim;      // workspace: R (+256) output cursors of the order-free first round
+                        // (keys only; zeroed by the launchers), or null: it looks back
   uint32_t* status[2];  // workspace: tiles * R look-back words each
   uint32_t* err;        // workspace: latched device error word
   uint32_t spin_limit;  // polls before a wait gives up

@@ -882,7 +882,9 @@ __device__ __forceinline__ void onesweep_tile_first(const PassParams& p, uint32_
 
 // The first round (pass 0) of a keys-only sort; a skipped pass 0 leaves the
 // first executed round to the stable kernel.
-template <typename K, int BITS, int THREADS, int KPT, int MINB>
+// DS: the digit rule (bytes for radix 256; a digit part for the first routing
+// step of a wide radix).
+template <typename K, int BITS, int THREADS, int KPT, int MINB, typename DS = RadixDigit>
 __global__ void __launch_bounds__(THREADS, MINB) k_onesweep_first(PassParams p) {
   using S = OnesweepShape<K, NoVal, BITS, THREADS, KPT>;
   constexpr int R = S::R, TILE = S::TILE;
@@ -901,15 +903,15 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep_first(PassParams p) 
   const K* kin = static_cast<const K*>(p.keys[0]);
   K* kout = static_cast<K*>(p.keys[1]);
   const int64_t tile_base = (int64_t)tile * TILE;
-  RadixDigit dig{p};
+  DS dig{p};
   if (tile_n == TILE)
-    onesweep_tile_first<K, BITS, THREADS, KPT, true>(p, tile, tile == 0, tile_base, tile_n, kin,
-                                                     kout, p.base, (uint32_t)p.n, smem, dig,
-                                                     p.claim);
+    onesweep_tile_first<K, BITS, THREADS, KPT, true, DS>(p, tile, tile == 0, tile_base, tile_n,
+                                                         kin, kout, p.base, (uint32_t)p.n, smem,
+                                                         dig, p.claim);
   else
-    onesweep_tile_first<K, BITS, THREADS, KPT, false>(p, tile, tile == 0, tile_base, tile_n, kin,
-                                                      kout, p.base, (uint32_t)p.n, smem, dig,
-                                                      p.claim);
+    onesweep_tile_first<K, BITS, THREADS, KPT, false, DS>(p, tile, tile == 0, tile_base, tile_n,
+                                                          kin, kout, p.base, (uint32_t)p.n, smem,
+                                                          dig, p.claim);
 }
 
 // ---------------------------------------------------------------------------

@@ -21,7 +21,10 @@
 //                   (a "bucket", 2^(W-8) of them): its start base[h*256], its
 //                   tiles, and whether its low byte is constant.
 //   A: k_onesweep   an ordered round by the HIGH part over all keys (stable),
-//                   which moves every key into its bucket (bases base[h*256]).
+//                   which moves every key into its bucket (bases base[h*256]);
+//                   in round 0 of a keys-only sort, whose input order carries
+//                   nothing, the order-free k_onesweep_first (output ranges
+//                   from per-bucket cursors, no look-back).
 //   B: k_bucket     an ordered round by the LOW byte inside every bucket
 //                   (stable; tiles never straddle a bucket) with bases
 //                   base[h*256 + l]: every key lands at its digit's place.
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(1024) k_scan_wide(const uint32_t* __restrict__
                                                     uint32_t* __restrict__ tile_first,
                                                     uint32_t* __restrict__ bucket_trivial,
                                                     uint32_t* __restrict__ skip, int passA,
-                                                    int64_t n) {
+                                                    int64_t n, uint32_t* __restrict__ claim) {
   constexpr int PER = BINS / 1024 > 0 ? BINS / 1024 : 1;  // digits per thread
   constexpr int NB = BINS / 256;
   static_assert(BINS >= 256 && BINS % 256 == 0 && NB <= kMaxBuckets, "buckets of 256 digits");
@@ -134,6 +137,10 @@ __global__ void __launch_bounds__(1024) k_scan_wide(const uint32_t* __restrict__
   __shared__ uint32_t s_flags[2];
   const int t = threadIdx.x;
   if (t < 2) s_flags[t] = 0;
+  // keys only, round 0: the cursors of the order-free steps, claim[0, BINS)
+  // for step B's digits and claim[BINS, BINS + 256) for step A's buckets
+  if (claim)
+    for (int j = t; j < BINS + 256; j += 1024) claim[j] = 0;
   // thread t owns digits [t*PER, t*PER + PER): their sum and largest count,
   // then their exclusive prefixes (16-byte loads and stores where PER allows)
   uint32_t local = 0, mx = 0;
@@ -297,6 +304,57 @@ __global__ void __launch_bounds__(THREADS, MINB)
                                                             (uint32_t)p.n, smem, dig);
 }
 
+// Step B of round 0 of a keys-only sort (order-free, as step A there): the
+// tiles of bucket h take their digits' ranges from the cursors claim[h*256 +
+// l] (zeroed by k_scan_wide) instead of looking back; CTA shape of the
+// order-free round (THREADS x KPT, the same tile as the ordered step).
+template <typename K, int THREADS, int KPT, int MINB, int NB, typename DS>
+__global__ void __launch_bounds__(THREADS, MINB)
+    k_bucket_first(PassParams p, const uint32_t* __restrict__ base,
+                   const uint32_t* __restrict__ tile_first,
+                   const uint32_t* __restrict__ bucket_trivial) {
+  using S = OnesweepShape<K, NoVal, 8, THREADS, KPT>;
+  constexpr int R = S::R, TILE = S::TILE;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* s_slot = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* s_misc = s_slot + 2 * R;
+  const int tid = threadIdx.x;
+  if (p.skip[p.pass]) return;
+  const int src = parity_of(p.skip, p.pass);
+  if (tid == 0) s_misc[0] = atomicAdd(p.counter, 1u);
+  zero_words<THREADS>(s_slot, R);
+  __syncthreads();
+  const uint32_t tile = s_misc[0];
+  if (tile >= tile_first[NB]) return;  // more CTAs than tiles
+  int lo = 0, hi = NB - 1;  // the last bucket whose first tile is <= tile
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile_first[mid] <= tile) lo = mid; else hi = mid - 1;
+  }
+  const int h = lo;
+  const int64_t start = base[h * 256];
+  const int64_t end = h + 1 < NB ? (int64_t)base[(h + 1) * 256] : p.n;
+  const int64_t lt = (int64_t)tile - tile_first[h];
+  const int64_t tile_base = start + lt * TILE;
+  const int tile_n = (int)min((int64_t)TILE, end - tile_base);
+  const K* kin = static_cast<const K*>(src ? p.keys[1] : p.keys[0]);
+  K* kout = static_cast<K*>(src ? p.keys[0] : p.keys[1]);
+  if (bucket_trivial[h]) {  // the bucket's low byte is constant: copy it
+    for (int j = tid; j < tile_n; j += THREADS) kout[tile_base + j] = kin[tile_base + j];
+    return;
+  }
+  DS dig{p};
+  uint32_t* claim = p.claim + h * 256;
+  if (tile_n == TILE)
+    onesweep_tile_first<K, 8, THREADS, KPT, true, DS>(p, tile, lt == 0, tile_base, tile_n, kin,
+                                                      kout, base + h * 256, (uint32_t)p.n, smem,
+                                                      dig, claim);
+  else
+    onesweep_tile_first<K, 8, THREADS, KPT, false, DS>(p, tile, lt == 0, tile_base, tile_n, kin,
+                                                       kout, base + h * 256, (uint32_t)p.n, smem,
+                                                       dig, claim);
+}
+
 // Scratch of the rounds inside the workspace: hist holds the 2^W counts, then
 // baseA[256], tile_first[257] (padded to 512) and bucket_trivial[256]; base
 // holds the prefix; status[0] the look-back rows of step A, status[1] those of
@@ -337,11 +395,16 @@ cudaError_t wide_round(const LsdArgs& a, PassParams& pp, const WideScratch& w, i
   }
   timer_end(a.timer, st);
   timer_begin(a.timer, "k_scan_wide", st);
+  // keys only, round 0: step A is order-free and takes its bucket ranges from
+  // cursors (zeroed by k_scan_wide) instead of looking back
+  const bool free0 = !HasVal<V>::value && q == 0;
   k_scan_wide<BINS, TILE><<<1, 1024, 0, st>>>(w.hist, w.base, w.baseA, w.tile_first,
-                                              w.bucket_trivial, a.skip, 2 * q, a.n);
+                                              w.bucket_trivial, a.skip, 2 * q, a.n,
+                                              free0 ? a.claim : nullptr);
   timer_end(a.timer, st);
-  if ((e = cudaMemsetAsync(a.status[0], 0, sizeof(uint32_t) * 256 * tiles, st))) return e;
-  if ((e = cudaMemsetAsync(a.status[1], 0, sizeof(uint32_t) * 256 * (tiles + NB), st)))
+  if (!free0 && (e = cudaMemsetAsync(a.status[0], 0, sizeof(uint32_t) * 256 * tiles, st)))
+    return e;
+  if (!free0 && (e = cudaMemsetAsync(a.status[1], 0, sizeof(uint32_t) * 256 * (tiles + NB), st)))
     return e;
   constexpr size_t smem = OrderedShape<K, V, 8, THREADS, KPT>::SMEM;
   auto kA = k_onesweep<K, V, 8, THREADS, KPT, MINB, DS>;
@@ -362,7 +425,22 @@ cudaError_t wide_round(const LsdArgs& a, PassParams& pp, const WideScratch& w, i
   pp.status = a.status[0];
   pp.counter = a.counters + 2 * q;
   timer_begin(a.timer, "k_wide_high", st);
-  kA<<<(unsigned)tiles, THREADS, smem, st>>>(pp);
+  bool launched = false;
+  if constexpr (!HasVal<V>::value) {
+    if (free0) {
+      using FC = FirstCfg<K, THREADS, KPT, MINB>;  // the order-free round's CTA shape, same tile
+      constexpr size_t fsmem = FirstShape<K, 8, FC::T, FC::KP>::SMEM;
+      auto kF = k_onesweep_first<K, 8, FC::T, FC::KP, MINB, DS>;
+      if (fsmem > 48 * 1024 && (e = cudaFuncSetAttribute(
+                                    kF, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem)))
+        return e;
+      pp.claim = a.claim + BINS;
+      kF<<<(unsigned)tiles, FC::T, fsmem, st>>>(pp);
+      pp.claim = nullptr;
+      launched = true;
+    }
+  }
+  if (!launched) kA<<<(unsigned)tiles, THREADS, smem, st>>>(pp);
   timer_end(a.timer, st);
   // step B: the low byte, inside every bucket
   pp.pass = 2 * q + 1;
@@ -374,7 +452,24 @@ cudaError_t wide_round(const LsdArgs& a, PassParams& pp, const WideScratch& w, i
   pp.status = a.status[1];
   pp.counter = a.counters + 2 * q + 1;
   timer_begin(a.timer, "k_wide_low", st);
-  kB<<<(unsigned)(tiles + NB), THREADS, smem, st>>>(pp, w.base, w.tile_first, w.bucket_trivial);
+  launched = false;
+  if constexpr (!HasVal<V>::value) {
+    if (free0) {  // round 0, keys only: order-free inside the buckets too
+      using FC = FirstCfg<K, THREADS, KPT, MINB>;
+      constexpr size_t fsmem = FirstShape<K, 8, FC::T, FC::KP>::SMEM;
+      auto kFB = k_bucket_first<K, FC::T, FC::KP, MINB, NB, DS>;
+      if (fsmem > 48 * 1024 && (e = cudaFuncSetAttribute(
+                                    kFB, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem)))
+        return e;
+      pp.claim = a.claim;
+      kFB<<<(unsigned)(tiles + NB), FC::T, fsmem, st>>>(pp, w.base, w.tile_first,
+                                                       w.bucket_trivial);
+      pp.claim = nullptr;
+      launched = true;
+    }
+  }
+  if (!launched)
+    kB<<<(unsigned)(tiles + NB), THREADS, smem, st>>>(pp, w.base, w.tile_first, w.bucket_trivial);
   timer_end(a.timer, st);
   return cudaSuccess;
 }
