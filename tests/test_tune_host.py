@@ -29,9 +29,9 @@ def clean_tables():
 
 
 # The built-in choices (the tuner's picks on a GB300, compiled into the
-# library): 32-bit keys alone at 2^24 -> radix 256 variant 5, at 2^28 ->
-# variant 0; other widths tuned at one size -> variant 0.
-BUILTIN_K32 = {24: (8, 5), 28: (8, 0)}
+# library): 32-bit keys alone at 2^24 and 2^28 -> radix 256 variant 0; other
+# widths tuned at one size -> variant 0.
+BUILTIN_K32 = {24: (8, 0), 28: (8, 0)}
 
 
 def test_defaults_without_tuning():
