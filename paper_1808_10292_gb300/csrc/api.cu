@@ -1,7 +1,8 @@
 // C-ABI of the isort library: argument checks, per-stream workspaces, kernel
 // family selection. Every step of a sort runs in the kernels of sort_k32.cu,
-// sort_k64.cu, radix_wide.cu and segmented.cu; this file only validates, carves
-// scratch memory and enqueues.
+// sort_k64.cu (onesweep.cuh), wide_rounds.cu, segmented_k32.cu / segmented_k64.cu
+// (segmented.cuh, btn.cuh), sample_sort.cu, gsd.cu, noalloc.cu and host_io.cu;
+// this file only validates, carves scratch memory and enqueues.
 #include <atomic>
 #include <cstdio>
 #include <cstdlib>

@@ -765,23 +765,23 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(PassParams p) {
 // no earlier round, and keys with equal digits in it may land in any order
 // without changing the final (unique) sorted result. So this round drops the
 // stable rank: a key's tile slot is the return value of one shared atomic add
-// on its digit's counter (which holds the tile start of the digit after the
-// scan). Per key that is a count add, a slot add and the store into the
-// staging area, against the stable round's count, mark, mask read, counter
-// update, mask clear and store. Later rounds keep the stable rank.
-// The first round's CTA shape for a stable round of THREADS x KPT at MINB
-// CTAs per SM: the same tile (so the look-back rows match), with twice the
+// on its digit's tile-wide counter (which holds the tile start of the digit
+// after the scan), and the tile's output ranges come from per-digit cursors
+// instead of a look-back. Per key that is a count add, a slot add and the
+// store into the staging area, and no check. Later rounds rank stably.
+// The first round's CTA shape for an ordered round of THREADS x KPT at MINB
+// CTAs per SM: the same tile (so the tile counts match), with twice the
 // threads holding half the keys each where their registers fit (the keys'
 // words plus about 26 more per thread, against 65536 / (threads x MINB)).
-// The round keeps no ranks or peer masks, so it needs fewer registers than the
-// stable round; more warps per SM hide more of the load and atomic latency.
+// The round keeps no per-warp counters or warp prefixes, so it needs fewer
+// registers than the ordered round; more warps per SM hide more latency.
 template <typename K, int THREADS, int KPT, int MINB>
 struct FirstCfg {
   static constexpr bool WIDE = KPT % 2 == 0 && THREADS * 2 <= 1024 &&
                                (KPT / 2) * (int)(sizeof(K) / 4) + 26 <= 65536 / (2 * THREADS * MINB);
   static constexpr int T = WIDE ? THREADS * 2 : THREADS;
   static constexpr int KP = WIDE ? KPT / 2 : KPT;
-  static_assert(T * KP == THREADS * KPT, "same tile as the stable round");
+  static_assert(T * KP == THREADS * KPT, "same tile as the ordered round");
 };
 
 template <typename K, int BITS, int THREADS, int KPT>
@@ -881,7 +881,7 @@ __device__ __forceinline__ void onesweep_tile_first(const PassParams& p, uint32_
 }
 
 // The first round (pass 0) of a keys-only sort; a skipped pass 0 leaves the
-// first executed round to the stable kernel.
+// first executed round to the ordered kernel.
 // DS: the digit rule (bytes for radix 256; a digit part for the first routing
 // step of a wide radix).
 template <typename K, int BITS, int THREADS, int KPT, int MINB, typename DS = RadixDigit>
