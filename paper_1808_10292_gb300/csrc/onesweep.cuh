@@ -781,7 +781,7 @@ struct FirstCfg {
                                (KPT / 2) * (int)(sizeof(K) / 4) + 26 <= 65536 / (2 * THREADS * MINB);
   static constexpr int T = WIDE ? THREADS * 2 : THREADS;
   static constexpr int KP = WIDE ? KPT / 2 : KPT;
-  static_assert(T * KP == THREADS * KPT, "same tile as the ordered round");
+  static_assert(T * KP == THREADS * KPT, "same tile as the stable round");
 };
 
 template <typename K, int BITS, int THREADS, int KPT>
