@@ -72,8 +72,7 @@ isort_status isort_pairs(void *keys, void *vals, int64_t n, int key_bits, int va
  * the host buffers outside [0, n) elements.
  *
  * The call enqueues on `stream`: the copy of the input into the stream's
- * workspace (which then holds n more keys, and payloads, than isort_keys
- * needs), the sort of that device copy (as isort_keys / isort_pairs), and the
+ * workspace, the sort of that device copy (as isort_keys / isort_pairs), and the
  * copy of the result to the output buffers; it returns once this is enqueued.
  * The output is complete when the stream has reached that point (e.g. after
  * cudaStreamSynchronize); the input must stay unchanged, and every buffer
@@ -85,9 +84,12 @@ isort_status isort_pairs(void *keys, void *vals, int64_t n, int key_bits, int va
  * with copy kernels instead (every SM reads or writes the host buffer through
  * its device mapping): as fast alone, slower when several streams' sorts and
  * copies overlap.
+ * Workspace: isort_workspace_size(n, key_bits, val_bits, radix_bits) plus the
+ * device copies, each rounded up to 256 bytes: n * key_bits / 8 (and
+ * n * val_bits / 8 for pairs).
  * Errors: ISORT_EINVAL for null buffers, bad widths or misaligned elements;
- * ISORT_ENOMEM when the workspace cannot hold the device copies; otherwise as
- * isort_keys. n = 0 does nothing; n = 1 copies the element. */
+ * ISORT_ENOMEM when a bound workspace cannot hold the device copies;
+ * otherwise as isort_keys. n = 0 does nothing; n = 1 copies the element. */
 isort_status isort_keys_host(const void *keys_in, void *keys_out, int64_t n, int key_bits,
                              int radix_bits, void *stream);
 isort_status isort_pairs_host(const void *keys_in, const void *vals_in, void *keys_out,

@@ -142,16 +142,43 @@ def test_binding_rejects_device_tensors():
         isort.sort_keys_host(torch.zeros(8, dtype=torch.uint32), torch.zeros(9, dtype=torch.uint32))
 
 
-def test_workspace_too_small_for_the_device_copies():
-    """A bound workspace that holds isort_keys' needs but not the device copies
-    of the host buffers: ENOMEM, nothing enqueued."""
-    n = 1 << 16
+def _round256(x):
+    return (x + 255) // 256 * 256
+
+
+@pytest.mark.parametrize("val_bits", [0, 32])
+def test_bound_workspace_size_for_host_sorts(val_bits):
+    """The header's size: isort_workspace_size plus the device copies rounded
+    up to 256 bytes. A bound workspace of exactly that size sorts; one that
+    holds only isort_keys' needs returns ENOMEM and enqueues nothing."""
+    n = (1 << 16) + 3
     s = torch.cuda.Stream()
-    ws = torch.empty(isort.workspace_size(n, 32, 0, 8), dtype=torch.uint8, device="cuda")
-    isort.set_workspace(ws, stream=s)
+    base = isort.workspace_size(n, 32, val_bits, 8)
+    exact = base + _round256(n * 4) + (_round256(n * val_bits // 8) if val_bits else 0)
+    k = inputs.keys(n, 32, "uniform", seed=25)
+    v = inputs.iota(n, 32)
     try:
-        k = _host_tensor(inputs.keys(n, 32, "uniform", seed=25), True)
+        ws = torch.empty(base, dtype=torch.uint8, device="cuda")
+        isort.set_workspace(ws, stream=s)
+        hk = _host_tensor(k, True)
         with pytest.raises(isort.IsortError):
-            isort.sort_keys_host(k, radix_bits=8, stream=s)
+            if val_bits:
+                isort.sort_pairs_host(hk, _host_tensor(v, True), radix_bits=8, stream=s)
+            else:
+                isort.sort_keys_host(hk, radix_bits=8, stream=s)
+        assert np.array_equal(hk.numpy(), k)  # nothing was enqueued
+        ws = torch.empty(exact, dtype=torch.uint8, device="cuda")
+        isort.set_workspace(ws, stream=s)
+        hv = _host_tensor(v, True)
+        if val_bits:
+            isort.sort_pairs_host(hk, hv, radix_bits=8, stream=s)
+        else:
+            isort.sort_keys_host(hk, radix_bits=8, stream=s)
+        s.synchronize()
+        assert isort.stream_status(s) == _lib.OK
+        ok, ov = oracle.radix_sort(k, v, radix_bits=8)
+        assert np.array_equal(hk.numpy(), ok)
+        if val_bits:
+            assert np.array_equal(hv.numpy(), ov)
     finally:
         isort.set_workspace(None, stream=s)
