@@ -902,6 +902,10 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep_first(PassParams p) 
   const int tile_n = (int)min((int64_t)TILE, p.n - (int64_t)tile * TILE);
   const K* kin = static_cast<const K*>(p.keys[0]);
   K* kout = static_cast<K*>(p.keys[1]);
+  if (p.prefetch_tiles && tid == 0) {  // the tile one wave ahead into L2, as the ordered round
+    const int64_t pf = ((int64_t)tile + p.prefetch_tiles) * TILE;
+    prefetch_tile(kin, pf, min((int64_t)TILE, p.n - pf));
+  }
   const int64_t tile_base = (int64_t)tile * TILE;
   DS dig{p};
   if (tile_n == TILE)
