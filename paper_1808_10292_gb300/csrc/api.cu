@@ -221,8 +221,8 @@ int64_t seg_btn_max(const SegConfig& c) {
 }
 
 struct SegLayout {
-  size_t err, cnt, lists, slot_first, tile_slot, seg_hist, seg_base, seg_skip, seg_claim, status0,
-      status1,
+  size_t err, cnt, lists, slot_first, tile_slot, seg_hist, seg_base, seg_skip, seg_claim, tile_info,
+      status0, status1,
       alt_k, alt_v, total;
   int64_t max_tiles;
 };
@@ -245,6 +245,7 @@ SegLayout seg_layout(const SegConfig& c, int64_t nseg, int64_t total, int64_t bt
   L.seg_base = off;    off = align256(off + per_slot * (size_t)nseg);
   L.seg_skip = off;    off = align256(off + sizeof(uint32_t) * (size_t)c.passes * nseg);
   L.seg_claim = off;   off = align256(off + sizeof(uint32_t) * (size_t)c.radix * nseg);
+  L.tile_info = off;   off = align256(off + sizeof(uint64_t) * (size_t)L.max_tiles);
   L.status0 = off;     off = align256(off + sizeof(uint32_t) * c.radix * (size_t)L.max_tiles);
   L.status1 = off;     off = align256(off + sizeof(uint32_t) * c.radix * (size_t)L.max_tiles);
   L.alt_k = off;       off = align256(off + (size_t)total * (c.key_bits / 8));
@@ -395,6 +396,7 @@ SegArgs seg_args(const SegConfig& c, const SegLayout& L, char* b, void* keys, vo
   a.seg_base = reinterpret_cast<uint32_t*>(b + L.seg_base);
   a.seg_skip = reinterpret_cast<uint32_t*>(b + L.seg_skip);
   a.seg_claim = reinterpret_cast<uint32_t*>(b + L.seg_claim);
+  a.tile_info = reinterpret_cast<uint64_t*>(b + L.tile_info);
   a.status[0] = reinterpret_cast<uint32_t*>(b + L.status0);
   a.status[1] = reinterpret_cast<uint32_t*>(b + L.status1);
   a.err = reinterpret_cast<uint32_t*>(b + L.err);

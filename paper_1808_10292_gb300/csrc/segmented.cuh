@@ -261,18 +261,28 @@ __global__ void __launch_bounds__(1024) k_seg_hist(const K* __restrict__ keys,
 // Per radix range: exclusive digit bases (relative to the range) of every
 // pass, and the range's trivial passes (one digit holds all its keys: the pass
 // is the identity on that range and is skipped for it). Also zeroes the
-// range's first-round output cursors (seg_claim, keys only; null otherwise).
-template <int BITS, int PASSES>
+// range's first-round output cursors (seg_claim, keys only; null otherwise)
+// and writes, for each of its tiles, where the tile's keys start, how many
+// there are, and in each pass which buffer holds them and whether the pass is
+// skipped (tile_info, read by the rounds to prefetch a tile one wave ahead).
+template <int BITS, int PASSES, int TILE>
 __global__ void __launch_bounds__(1 << BITS) k_seg_scan(const uint32_t* __restrict__ cnt,
                                                        const uint32_t* __restrict__ seg_hist,
                                                        uint32_t* __restrict__ seg_base,
                                                        uint32_t* __restrict__ seg_skip,
-                                                       uint32_t* __restrict__ seg_claim) {
+                                                       uint32_t* __restrict__ seg_claim,
+                                                       const int64_t* __restrict__ off,
+                                                       int64_t nseg, int64_t total,
+                                                       const int32_t* __restrict__ list,
+                                                       const uint32_t* __restrict__ slot_first,
+                                                       uint64_t* __restrict__ tile_info) {
+  static_assert(PASSES <= 8 && TILE < 16384, "tile_info packs keys, parity and skip bits");
   constexpr int R = 1 << BITS;
   __shared__ uint32_t s_warp[R / 32];
   const uint32_t slot = blockIdx.x;
   if (slot >= cnt[kCntClassLen + kSegRadix]) return;
   if (seg_claim) seg_claim[(size_t)slot * R + threadIdx.x] = 0;
+  uint32_t skips = 0;
   for (int p = 0; p < PASSES; ++p) {
     const size_t row = ((size_t)slot * PASSES + p) * R;
     uint32_t tot;
@@ -280,6 +290,22 @@ __global__ void __launch_bounds__(1 << BITS) k_seg_scan(const uint32_t* __restri
     seg_base[row + threadIdx.x] = block_exclusive_scan<R>(c, s_warp, tot);
     const int trivial = __syncthreads_or(c == tot);
     if (threadIdx.x == 0) seg_skip[(size_t)slot * PASSES + p] = trivial;
+    skips |= (uint32_t)trivial << p;
+  }
+  uint32_t parity = 0, src = 0;  // bit p: the buffer holding the range's keys before pass p
+  for (int p = 0; p < PASSES; ++p) {
+    parity |= src << p;
+    src ^= ((skips >> p) & 1u) ^ 1u;
+  }
+  int64_t start, len;
+  seg_range(off, list[(size_t)kSegRadix * nseg + slot], total, start, len);
+  const int64_t tiles = (len + TILE - 1) / TILE, first = slot_first[slot];
+  for (int64_t lt = threadIdx.x; lt < tiles; lt += R) {
+    const int64_t at = start + lt * TILE;
+    // past 2^34 keys the word cannot hold the start: 0 keys, no prefetch
+    const int64_t n = at < (int64_t(1) << 34) ? min((int64_t)TILE, len - lt * TILE) : 0;
+    tile_info[first + lt] = (uint64_t)(n ? at : 0) | ((uint64_t)n << 34) |
+                            ((uint64_t)parity << 48) | ((uint64_t)skips << 56);
   }
 }
 
@@ -332,6 +358,7 @@ struct SegPassParams {
   const uint32_t* seg_base;
   const uint32_t* seg_skip;  // [slots][passes] 1 = the pass is the identity on the range
   uint32_t* seg_claim;       // [slots][R] keys only: the first round's output cursors
+  const uint64_t* tile_info;  // [tiles] first key | keys << 34 | parity << 48 | skip << 56
   int passes;
 };
 
@@ -357,6 +384,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp
   const int32_t slot = sp.tile_slot[tile];
   const uint32_t* skip_row = sp.seg_skip + (size_t)slot * sp.passes;
   if (skip_row[p.pass]) return;  // the digit is constant on this range
+  // The tile one wave ahead: thread 0 copies its tile_info word to shared
+  // memory now (cp.async: no register, no wait) and prefetches its keys into
+  // L2 when this tile is done.
+  uint64_t* s_pf = reinterpret_cast<uint64_t*>(s_misc + 62);
+  const uint32_t ahead = tile + (uint32_t)p.prefetch_tiles;
+  const bool prefetch = tid == 0 && p.prefetch_tiles && ahead < sp.cnt[kCntTiles];
+  if (prefetch) cp_async<8>(s_pf, sp.tile_info + ahead);
   int64_t start, len;
   seg_range(sp.off, sp.list[(size_t)kSegRadix * sp.nseg + slot], sp.total, start, len);
   const int64_t lt = (int64_t)tile - sp.slot_first[slot];  // tile index within the range
@@ -390,6 +424,18 @@ __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp
       onesweep_tile_ordered<K, V, BITS, THREADS, KPT, false>(p, tile, lt == 0, tile_base,
                                                              tile_n, kin, kout, vin, vout, base,
                                                              (uint32_t)len, smem, dig);
+  }
+  if (prefetch) {
+    cp_async_wait_all();
+    const uint64_t w = *s_pf;
+    const int64_t at = (int64_t)(w & ((uint64_t(1) << 34) - 1));
+    const int64_t n = (int64_t)((w >> 34) & 0x3fff);
+    if (!((w >> (56 + p.pass)) & 1) && n && at + n <= sp.total) {
+      const int s = (int)((w >> (48 + p.pass)) & 1);  // the buffer holding that tile now
+      prefetch_tile(static_cast<const K*>(s ? p.keys[1] : p.keys[0]), at, n);
+      if constexpr (HasVal<V>::value)
+        prefetch_tile(static_cast<const V*>(s ? p.vals[1] : p.vals[0]), at, n);
+    }
   }
 }
 
@@ -459,8 +505,9 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
   }
   timer_end(a.timer, st);
   timer_begin(a.timer, "k_seg_scan", st);
-  k_seg_scan<8, P><<<(unsigned)nslots, R, 0, st>>>(a.cnt, a.seg_hist, a.seg_base, a.seg_skip,
-                                                   HasVal<V>::value ? nullptr : a.seg_claim);
+  k_seg_scan<8, P, TILE><<<(unsigned)nslots, R, 0, st>>>(
+      a.cnt, a.seg_hist, a.seg_base, a.seg_skip, HasVal<V>::value ? nullptr : a.seg_claim,
+      a.offsets, a.nseg, a.total, a.lists, a.slot_first, a.tile_info);
   timer_end(a.timer, st);
 
   auto kern = k_seg_onesweep<K, V, 8, THREADS, KPT, MINB>;
@@ -488,6 +535,7 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
   sp.seg_base = a.seg_base;
   sp.seg_skip = a.seg_skip;
   sp.seg_claim = a.seg_claim;
+  sp.tile_info = a.tile_info;
   sp.passes = P;
   PassParams& pp = sp.p;
   pp.keys[0] = a.keys;
@@ -501,7 +549,7 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
   pp.spin_limit = a.spin_limit;
   pp.stall_tile = -1;
   pp.claim = nullptr;
-  pp.prefetch_tiles = 0;
+  pp.prefetch_tiles = (int64_t)a.num_sms * 4;  // one wave of tiles ahead
   pp.check_mode = a.check_mode;
   for (int q = 0; q < P; ++q) {
     pp.pass = q;
