@@ -479,11 +479,16 @@ def run_ours(a):
                                    "frac": alg_bytes / (f_ms / 1000.0) / 1e9 / peak,
                                    "launches": len(kernel_ms[first])}
     if "k_wide_high" in kernel_ms:
-        # a wide-radix round = histogram + scan + the two routing steps; its
+        # a wide-radix round = histogram + scans + the two routing steps (radix
+        # 65536: plus its share of the one byte-histogram read per sort); its
         # algorithmic bytes are one read and one write of every key
-        parts = [k for k in ("k_hist16", "k_hist_wide", "k_scan_wide", "k_wide_high", "k_wide_low")
-                 if k in kernel_ms]
+        parts = [k for k in ("k_hist_wide", "k_scan_high", "k_bucket_hist", "k_scan_wide",
+                             "k_wide_high", "k_wide_low") if k in kernel_ms]
         r_ms = sum(statistics.mean(kernel_ms[k]) for k in parts)
+        if "k_hist" in kernel_ms:
+            rounds = -(-kb // rb)
+            r_ms += sum(kernel_ms["k_hist"]) / len(kernel_ms["k_wide_high"])
+            parts.append(f"k_hist / {rounds}")
         rb_bytes = 2 * n * bytes_per_key
         roofline["round"] = {"kernels": " + ".join(parts), "avg_round_ms": r_ms,
                              "achieved": rb_bytes / (r_ms / 1000.0) / 1e9,

@@ -13,10 +13,15 @@
 // write amplification and one L2 write request per key). So routing takes two
 // steps, each writing long runs, the high W - 8 bits of the digit first:
 //
-//   k_hist16 /      the 2^W-bin histogram of the round's digit, one read of the
-//   k_hist_small    keys (65536 bins: pairs of CTAs share a chunk, each
-//                   counting half of the bins; up to 4096 bins: one CTA, eight
-//                   copies of the bins).
+//   histogram of    radix 2048: k_hist_small, the 2048-bin histogram of the
+//   the digit       round's digit (eight copies of the bins per CTA), then
+//                   k_scan_wide. Radix 65536: the buckets are the digit's high
+//                   byte, whose counts come from one k_hist read of all keys
+//                   before round 0 (every byte's 256 bins), scanned by
+//                   k_scan_high into step A's bases; the 65536 digit counts are
+//                   taken after step A, when each bucket's keys sit together
+//                   (k_bucket_hist: 256 lane-private bins per bucket slice),
+//                   then k_scan_wide.
 //   k_scan_wide     exclusive prefix of the 2^W counts (base); per high part h
 //                   (a "bucket", 2^(W-8) of them): its start base[h*256], its
 //                   tiles, and whether its low byte is constant.
@@ -35,8 +40,6 @@
 namespace isort {
 namespace {
 
-constexpr int kR16 = 65536;
-constexpr int kHalf16 = kR16 / 2;
 constexpr int kHistThreads = 1024;
 constexpr int kMaxBuckets = 256;
 
@@ -59,34 +62,6 @@ __device__ __forceinline__ void count_digit(uint32_t d, Add&& add) {
     add(d, 1u);
   else if ((threadIdx.x & 31) == first)
     add(d0, (uint32_t)__popc(same));
-}
-
-// The 65536-bin histogram of the 16-bit digit at `shift` of all n keys of the
-// round's input buffer (the parity of the passes executed before `pass`),
-// added into hist. CTAs 2c and 2c+1 read the same chunk c of the keys (the
-// second read mostly hits L2); CTA 2c + r counts only the digits of bin half
-// r, in its own shared memory (32768 counters, 128 KiB).
-template <typename K>
-__global__ void __launch_bounds__(kHistThreads)
-    k_hist16(const K* buf0, const K* buf1, const uint32_t* skip, int pass, int64_t n, int shift,
-             uint32_t* hist) {
-  extern __shared__ __align__(16) uint32_t s_bins[];  // kHalf16
-  const uint32_t rank = blockIdx.x & 1u;
-  for (int i = threadIdx.x; i < kHalf16; i += kHistThreads) s_bins[i] = 0;
-  __syncthreads();
-  const K* keys = parity_of(skip, pass) ? buf1 : buf0;
-  const int64_t chunks = gridDim.x >> 1, chunk = blockIdx.x >> 1;
-  const int64_t lo = n * chunk / chunks, hi = n * (chunk + 1) / chunks;
-  count_keys(keys + lo, hi - lo, threadIdx.x, kHistThreads, [&](K k) {
-    count_digit(digit_of(k, shift, 0xffffu), [&](uint32_t d, uint32_t c) {
-      if ((d >> 15) == rank) atomicAdd(&s_bins[d & (kHalf16 - 1)], c);
-    });
-  });
-  __syncthreads();
-  for (int i = threadIdx.x; i < kHalf16; i += kHistThreads) {
-    const uint32_t c = s_bins[i];
-    if (c) atomicAdd(&hist[rank * kHalf16 + i], c);
-  }
 }
 
 // The BINS-bin histogram (BINS <= 4096) of the digit (k >> shift) & mask:
@@ -112,6 +87,77 @@ __global__ void __launch_bounds__(kHistThreads)
 #pragma unroll
     for (int c = 0; c < COPIES; ++c) sum += s_bins[c * BINS + d];
     if (sum) atomicAdd(&hist[d], sum);
+  }
+}
+
+// Radix 65536, per round before step A: the 256 buckets are the values of the
+// digit's high byte, whose counts come from one read of all keys before round
+// 0 (hist8: one 256-bin histogram per byte, k_hist). Exclusive prefix of the
+// row -> baseA (step A's bases), the buckets' first tiles for step B, skip[passA]
+// (the high byte is constant: step A is the identity), and step A's cursors
+// zeroed when it runs order-free (claimA, or null).
+template <int TILE>
+__global__ void __launch_bounds__(256) k_scan_high(const uint32_t* __restrict__ row, int64_t n,
+                                                   uint32_t* __restrict__ baseA,
+                                                   uint32_t* __restrict__ tile_first,
+                                                   uint32_t* __restrict__ skip, int passA,
+                                                   uint32_t* __restrict__ claimA) {
+  __shared__ uint32_t s_warp[8];
+  const int h = threadIdx.x;
+  const uint32_t c = row[h];
+  uint32_t total;
+  baseA[h] = block_exclusive_scan<256>(c, s_warp, total);
+  const int trivial = __syncthreads_or((int64_t)c == n);
+  const uint32_t tiles = (c + TILE - 1) / TILE;
+  __syncthreads();  // s_warp is reused
+  const uint32_t first = block_exclusive_scan<256>(tiles, s_warp, total);
+  tile_first[h] = first;
+  if (h == 255) tile_first[256] = first + tiles;
+  if (claimA) claimA[h] = 0;
+  if (h == 0) skip[passA] = trivial;
+}
+
+// Radix 65536, per round after step A: the keys of bucket h (high byte) sit
+// together at [baseA[h], baseA[h + 1]); count the low byte of every key into
+// hist[h*256 + l]. CTA c takes the slice [n*c/C, n*(c+1)/C) and counts each
+// bucket's part of it in lane-private columns (lane l of every warp counts
+// into column l: no bank conflicts), adding the 256 sums to hist when it
+// leaves the bucket. One read of the keys with conflict-free shared atomics,
+// in place of a 65536-bin histogram.
+constexpr int kBucketHistThreads = 1024;
+template <typename K>
+__global__ void __launch_bounds__(kBucketHistThreads, 2)
+    k_bucket_hist(const K* buf0, const K* buf1, const uint32_t* skip, int passB, int64_t n,
+                  int shift, const uint32_t* __restrict__ baseA, uint32_t* __restrict__ hist) {
+  __shared__ __align__(16) uint32_t s_cnt[256 * 32];  // [low byte][lane]
+  __shared__ uint32_t s_start[257];
+  const int t = threadIdx.x, lane = t & 31;
+  const K* keys = parity_of(skip, passB) ? buf1 : buf0;
+  for (int h = t; h < 256; h += kBucketHistThreads) s_start[h] = baseA[h];
+  if (t == 0) s_start[256] = (uint32_t)n;
+  const int64_t hi = n * (blockIdx.x + 1) / gridDim.x;
+  int64_t lo = n * blockIdx.x / gridDim.x;
+  __syncthreads();
+  int b = 0;  // the bucket holding key lo: the last h with s_start[h] <= lo
+  for (int step = 128; step; step >>= 1)
+    if ((int64_t)s_start[b + step] <= lo) b += step;
+  while (lo < hi) {
+    while ((int64_t)s_start[b + 1] <= lo) ++b;  // skip empty buckets
+    const int64_t end = min(hi, (int64_t)s_start[b + 1]);
+    for (int i = t; i < 256 * 32 / 4; i += kBucketHistThreads)
+      reinterpret_cast<uint4*>(s_cnt)[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    count_keys(keys + lo, end - lo, t, kBucketHistThreads,
+               [&](K k) { atomicAdd(&s_cnt[digit_of(k, shift, 0xffu) * 32 + lane], 1u); });
+    __syncthreads();
+    if (t < 256) {
+      uint32_t sum = 0;
+#pragma unroll 8
+      for (int j = 0; j < 32; ++j) sum += s_cnt[t * 32 + ((j + t) & 31)];
+      if (sum) atomicAdd(&hist[b * 256 + t], sum);
+    }
+    __syncthreads();
+    lo = end;
   }
 }
 
@@ -361,6 +407,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
 // step B.
 struct WideScratch {
   uint32_t *hist, *baseA, *tile_first, *bucket_trivial, *base;
+  uint32_t* hist8;  // radix 65536: the 256-bin histogram of every key byte (k_hist)
 };
 
 // One round with a W-bit digit at `shift` (kernel passes 2q and 2q + 1).
@@ -372,17 +419,18 @@ cudaError_t wide_round(const LsdArgs& a, PassParams& pp, const WideScratch& w, i
   constexpr bool BYTES = W == 16;
   using DS = typename std::conditional<BYTES, RadixDigit, ShiftMaskDigit>::type;
   cudaError_t e;
+  // keys only, round 0: both steps are order-free and take their ranges from
+  // cursors instead of looking back
+  const bool free0 = !HasVal<V>::value && q == 0;
   if ((e = cudaMemsetAsync(w.hist, 0, sizeof(uint32_t) * BINS, st))) return e;
   if constexpr (W == 16) {
-    constexpr size_t HSMEM = sizeof(uint32_t) * kHalf16;
-    if ((e = cudaFuncSetAttribute(k_hist16<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)HSMEM)))
-      return e;
-    const int grid = std::max(2, (a.num_sms / 2) * 2);  // pairs of CTAs, one CTA per SM
-    timer_begin(a.timer, "k_hist16", st);
-    k_hist16<K><<<grid, kHistThreads, HSMEM, st>>>(static_cast<const K*>(a.keys),
-                                                     static_cast<const K*>(a.alt_keys), a.skip,
-                                                     2 * q, a.n, shift, w.hist);
+    // step A's bases and step B's bucket tiles from the high byte's histogram;
+    // the 65536 digit counts are taken after step A (k_bucket_hist)
+    timer_begin(a.timer, "k_scan_high", st);
+    k_scan_high<TILE><<<1, 256, 0, st>>>(w.hist8 + (size_t)(2 * q + 1) * 256, a.n, w.baseA,
+                                         w.tile_first, a.skip, 2 * q,
+                                         free0 ? a.claim + BINS : nullptr);
+    timer_end(a.timer, st);
   } else {
     constexpr size_t HSMEM = sizeof(uint32_t) * 8 * BINS;
     if ((e = cudaFuncSetAttribute(k_hist_small<K, BINS>,
@@ -392,16 +440,13 @@ cudaError_t wide_round(const LsdArgs& a, PassParams& pp, const WideScratch& w, i
     k_hist_small<K, BINS><<<a.num_sms * (HSMEM <= 64 * 1024 ? 2 : 1), kHistThreads, HSMEM, st>>>(
         static_cast<const K*>(a.keys), static_cast<const K*>(a.alt_keys), a.skip, 2 * q, a.n,
         shift, (uint32_t)(BINS - 1), w.hist);
+    timer_end(a.timer, st);
+    timer_begin(a.timer, "k_scan_wide", st);
+    k_scan_wide<BINS, TILE><<<1, 1024, 0, st>>>(w.hist, w.base, w.baseA, w.tile_first,
+                                                w.bucket_trivial, a.skip, 2 * q, a.n,
+                                                free0 ? a.claim : nullptr);
+    timer_end(a.timer, st);
   }
-  timer_end(a.timer, st);
-  timer_begin(a.timer, "k_scan_wide", st);
-  // keys only, round 0: step A is order-free and takes its bucket ranges from
-  // cursors (zeroed by k_scan_wide) instead of looking back
-  const bool free0 = !HasVal<V>::value && q == 0;
-  k_scan_wide<BINS, TILE><<<1, 1024, 0, st>>>(w.hist, w.base, w.baseA, w.tile_first,
-                                              w.bucket_trivial, a.skip, 2 * q, a.n,
-                                              free0 ? a.claim : nullptr);
-  timer_end(a.timer, st);
   if (!free0 && (e = cudaMemsetAsync(a.status[0], 0, sizeof(uint32_t) * 256 * tiles, st)))
     return e;
   if (!free0 && (e = cudaMemsetAsync(a.status[1], 0, sizeof(uint32_t) * 256 * (tiles + NB), st)))
@@ -442,6 +487,19 @@ cudaError_t wide_round(const LsdArgs& a, PassParams& pp, const WideScratch& w, i
   }
   if (!launched) kA<<<(unsigned)tiles, THREADS, smem, st>>>(pp);
   timer_end(a.timer, st);
+  if constexpr (W == 16) {
+    // the low byte's counts per bucket, from step A's output, then the prefix
+    timer_begin(a.timer, "k_bucket_hist", st);
+    k_bucket_hist<K><<<a.num_sms * 2, kBucketHistThreads, 0, st>>>(
+        static_cast<const K*>(a.keys), static_cast<const K*>(a.alt_keys), a.skip, 2 * q + 1, a.n,
+        shift, w.baseA, w.hist);
+    timer_end(a.timer, st);
+    timer_begin(a.timer, "k_scan_wide", st);
+    k_scan_wide<BINS, TILE><<<1, 1024, 0, st>>>(w.hist, w.base, w.baseA, w.tile_first,
+                                                w.bucket_trivial, a.skip, 2 * q, a.n,
+                                                free0 ? a.claim : nullptr);
+    timer_end(a.timer, st);
+  }
   // step B: the low byte, inside every bucket
   pp.pass = 2 * q + 1;
   pp.shift = shift;
@@ -490,9 +548,27 @@ cudaError_t wide_launch(const LsdArgs& a, cudaStream_t st) {
   w.baseA = a.hist + (1 << BITS);
   w.tile_first = w.baseA + 256;
   w.bucket_trivial = w.tile_first + 512;
+  w.hist8 = w.bucket_trivial + 256;
   w.base = a.base;
   cudaError_t e;
   if ((e = cudaMemsetAsync(a.counters, 0, sizeof(uint32_t) * P2, st))) return e;
+  if constexpr (BITS == 16) {
+    // the 256-bin histogram of every key byte, one read of the input: the
+    // buckets (high bytes of the digits) of every round
+    constexpr int P8 = KB / 8;
+    constexpr int LANES = sizeof(K) == 4 ? 32 : 16;
+    using HS = HistShape<K, 8, kHistThreads, LANES>;
+    if ((e = cudaMemsetAsync(w.hist8, 0, sizeof(uint32_t) * P8 * 256, st))) return e;
+    auto hk = k_hist<K, 8, kHistThreads, LANES>;
+    if ((e = cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)HS::SMEM)))
+      return e;
+    const int64_t want = (a.n / Vec16<K>::N + kHistThreads * 4 - 1) / (kHistThreads * 4);
+    const int hblocks = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)a.num_sms);
+    timer_begin(a.timer, "k_hist", st);
+    hk<<<hblocks, kHistThreads, HS::SMEM, st>>>(static_cast<const K*>(a.keys), a.n, w.hist8);
+    timer_end(a.timer, st);
+  }
   PassParams pp;
   pp.keys[0] = a.keys;
   pp.keys[1] = a.alt_keys;

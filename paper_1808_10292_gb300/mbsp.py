@@ -19,7 +19,8 @@ and the fast memory is shared memory. A radix-256 round of this library moves
 each key (and payload) once in and once out of HBM -- the upfront histogram
 and the decoupled look-back replace the paper's second read -- and touches
 shared memory a fixed number of times per key; a wide-radix round reads the
-keys for its digit histogram and then routes them in two such rounds. gpu_*
+keys for its digit histogram and then routes them in two such rounds (at
+radix 65536 after one more read of the keys before round 0, for the buckets). gpu_*
 below give those costs in the same (g, G) currency; calibrate() derives g from
 a measured copy bandwidth and G from one measured round.
 
@@ -127,7 +128,10 @@ def gpu_sort(n: float, key_bits: int, val_bits: int, r: int, g: float, G: float)
             first = j == 0 and val_bits == 0
             t += gpu_onesweep_round(n, w, g, G, SHARED_ACCESSES_FIRST if first else shared)
         return t
-    return P * gpu_wide_round(n, w, kw, g, G, shared)
+    # radix 65536: the buckets of every round (the digits' high bytes) come
+    # from one byte-histogram read of the keys before round 0
+    t = gpu_histogram(n, kw, key_bits // 8, g, G) if r == 65536 else 0.0
+    return t + P * gpu_wide_round(n, w, kw, g, G, shared)
 
 
 def calibrate(hbm_gbs: float, onesweep_round_s: float, n: float, words_per_item: float = 1.0,
