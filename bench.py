@@ -482,7 +482,7 @@ def run_ours(a):
         # a wide-radix round = histogram + scans + the two routing steps (radix
         # 65536: plus its share of the one byte-histogram read per sort); its
         # algorithmic bytes are one read and one write of every key
-        parts = [k for k in ("k_hist_wide", "k_scan_high", "k_bucket_hist", "k_scan_wide",
+        parts = [k for k in ("k_hist_wide", "k_scan_high", "k_bucket_hist", "k_scan_buckets", "k_scan_wide",
                              "k_wide_high", "k_wide_low") if k in kernel_ms]
         r_ms = sum(statistics.mean(kernel_ms[k]) for k in parts)
         if "k_hist" in kernel_ms:

@@ -21,10 +21,12 @@
 //                   k_scan_high into step A's bases; the 65536 digit counts are
 //                   taken after step A, when each bucket's keys sit together
 //                   (k_bucket_hist: 256 lane-private bins per bucket slice),
-//                   then k_scan_wide.
-//   k_scan_wide     exclusive prefix of the 2^W counts (base); per high part h
-//                   (a "bucket", 2^(W-8) of them): its start base[h*256], its
-//                   tiles, and whether its low byte is constant.
+//                   then k_scan_buckets (one CTA per bucket: the bucket's
+//                   start from step A plus the prefix of its 256 counts).
+//   k_scan_wide     radix 2048: exclusive prefix of the 2^W counts (base); per
+//                   high part h (a "bucket", 2^(W-8) of them): its start
+//                   base[h*256], its tiles, and whether its low byte is
+//                   constant.
 //   A: k_onesweep   an ordered round by the HIGH part over all keys (stable),
 //                   which moves every key into its bucket (bases base[h*256]);
 //                   in round 0 of a keys-only sort, whose input order carries
@@ -94,8 +96,10 @@ __global__ void __launch_bounds__(kHistThreads)
 // digit's high byte, whose counts come from one read of all keys before round
 // 0 (hist8: one 256-bin histogram per byte, k_hist). Exclusive prefix of the
 // row -> baseA (step A's bases), the buckets' first tiles for step B, skip[passA]
-// (the high byte is constant: step A is the identity), and step A's cursors
-// zeroed when it runs order-free (claimA, or null).
+// (the high byte is constant: step A is the identity), skip[passA + 1] = 1
+// (step B is needed: cleared by k_scan_buckets once a bucket's low byte is
+// seen to vary), and step A's cursors zeroed when it runs order-free (claimA,
+// or null).
 template <int TILE>
 __global__ void __launch_bounds__(256) k_scan_high(const uint32_t* __restrict__ row, int64_t n,
                                                    uint32_t* __restrict__ baseA,
@@ -114,7 +118,10 @@ __global__ void __launch_bounds__(256) k_scan_high(const uint32_t* __restrict__ 
   tile_first[h] = first;
   if (h == 255) tile_first[256] = first + tiles;
   if (claimA) claimA[h] = 0;
-  if (h == 0) skip[passA] = trivial;
+  if (h == 0) {
+    skip[passA] = trivial;
+    skip[passA + 1] = 1;
+  }
 }
 
 // Radix 65536, per round after step A: the keys of bucket h (high byte) sit
@@ -158,6 +165,33 @@ __global__ void __launch_bounds__(kBucketHistThreads, 2)
     }
     __syncthreads();
     lo = end;
+  }
+}
+
+// Radix 65536, per round after k_bucket_hist: CTA h scans bucket h's 256
+// low-byte counts, so that base[h*256 + l] = baseA[h] + (the bucket's keys
+// with a smaller low byte); bucket_trivial[h] = one low byte holds all of the
+// bucket's keys, and a bucket whose low byte varies clears skip[passB]
+// (preset to 1 by k_scan_high). With claim (keys only, round 0), the bucket's
+// 256 cursors of the order-free step B are zeroed. The buckets' bases are
+// known from step A, so the 256 scans are independent: one CTA per bucket.
+__global__ void __launch_bounds__(256) k_scan_buckets(const uint32_t* __restrict__ hist,
+                                                      const uint32_t* __restrict__ baseA,
+                                                      uint32_t* __restrict__ base,
+                                                      uint32_t* __restrict__ bucket_trivial,
+                                                      uint32_t* __restrict__ skip, int passB,
+                                                      uint32_t* __restrict__ claim) {
+  __shared__ uint32_t s_warp[8];
+  const int h = blockIdx.x, l = threadIdx.x;
+  const uint32_t c = hist[h * 256 + l];
+  uint32_t len;
+  const uint32_t excl = block_exclusive_scan<256>(c, s_warp, len);
+  base[h * 256 + l] = baseA[h] + excl;
+  if (claim) claim[h * 256 + l] = 0;
+  const int one = __syncthreads_or(len > 0 && c == len);
+  if (l == 0) {
+    bucket_trivial[h] = one;
+    if (len > 0 && !one) skip[passB] = 0;
   }
 }
 
@@ -494,10 +528,9 @@ cudaError_t wide_round(const LsdArgs& a, PassParams& pp, const WideScratch& w, i
         static_cast<const K*>(a.keys), static_cast<const K*>(a.alt_keys), a.skip, 2 * q + 1, a.n,
         shift, w.baseA, w.hist);
     timer_end(a.timer, st);
-    timer_begin(a.timer, "k_scan_wide", st);
-    k_scan_wide<BINS, TILE><<<1, 1024, 0, st>>>(w.hist, w.base, w.baseA, w.tile_first,
-                                                w.bucket_trivial, a.skip, 2 * q, a.n,
-                                                free0 ? a.claim : nullptr);
+    timer_begin(a.timer, "k_scan_buckets", st);
+    k_scan_buckets<<<NB, 256, 0, st>>>(w.hist, w.baseA, w.base, w.bucket_trivial, a.skip,
+                                       2 * q + 1, free0 ? a.claim : nullptr);
     timer_end(a.timer, st);
   }
   // step B: the low byte, inside every bucket
