@@ -403,6 +403,7 @@ SegArgs seg_args(const SegConfig& c, const SegLayout& L, char* b, void* keys, vo
   a.spin_limit = g_spin_limit;
   a.num_sms = num_sms();
   a.check_mode = g_check_mode;
+  a.agg_top = 0;
   a.timer = nullptr;
   if (g_timing) {
     if (!g_timer.ready) {
@@ -590,6 +591,8 @@ isort_status isort_sample_sort(void* keys, void* vals, int64_t n, int key_bits, 
   char* b = static_cast<char*>(ws);
   SegArgs sa = seg_args(*c, G.seg, b, b + G.out_k, vals ? b + G.out_v : nullptr,
                         reinterpret_cast<const int64_t*>(b + G.offsets), buckets, n);
+  // inside a bucket of many the top byte takes one or two values
+  sa.agg_top = buckets >= 128;
   GvrArgs g;
   g.keys = keys;
   g.vals = vals;

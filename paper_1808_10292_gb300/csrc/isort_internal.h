@@ -112,6 +112,8 @@ struct SegArgs {
   int num_sms;
   KernelTimer* timer;
   uint32_t check_mode;   // test hook of the ordered keys-only rounds (0: normal)
+  int agg_top;           // the ranges are narrow in key value (a sample sort's buckets):
+                         // the top pass reserves slots per digit value in tiles with few digits
 };
 
 // Host side: configuration of one (key, payload) family and its launcher.

@@ -448,8 +448,21 @@ struct OrderedShape {
 // and gathered by the staged input indices at the write-out. Per key the fast
 // path makes three digit-indexed shared accesses (count add, slot add, key
 // store; with payloads also the index store and the payload gather).
+//
+// A slot add that returns the old value is served one lane at a time for the
+// lanes of a warp instruction that hit the same counter, so a row whose keys
+// share one or two digits takes up to ~30 times longer than a row of random
+// digits. With AGG, a tile with at most kAggDigits distinct digits (the top
+// digit inside the buckets of a sample sort, for instance) ranks without slot
+// adds: the owners list the tile's digit values, and each warp keeps one
+// running count per value in registers, taking a row's ranks from a ballot per
+// value (lane order within the row, rows in order: the same ranks the slot
+// adds give, so the check is unchanged). The warp's counters are then set as
+// the slot adds would have left them, for the fallback.
+constexpr int kAggDigits = 3;
+
 template <typename K, typename V, int BITS, int THREADS, int KPT, bool FULL,
-          typename DS = RadixDigit>
+          typename DS = RadixDigit, bool AGG = false>
 __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint32_t tile,
                                                       bool first, int64_t tile_base, int tile_n,
                                                       const K* __restrict__ kin,
@@ -477,6 +490,8 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
   uint32_t* my = s_wcnt + warp * R;
   // the fallback re-reads the tile's input address from here (fewer live registers)
   if (tid == 0) *reinterpret_cast<const K**>(s_misc + 48) = kin + tile_base;
+  if constexpr (AGG)
+    if (tid == 0) s_misc[40] = 0;  // AGG: the number of listed digit values
 
   K key[KPT];
   NoVal nv[1];
@@ -557,7 +572,42 @@ __device__ __forceinline__ void onesweep_tile_ordered(const PassParams& p, uint3
     dig.keep(pos, d);
     if constexpr (HV) s_src[pos] = (uint16_t)(wofs + i * 32);
   };
-  if (p.check_mode != kCheckPerturb) {
+  bool few = false;  // AGG: at most kAggDigits distinct digits in the tile
+  if constexpr (AGG && DPT == 1) {
+    const bool used = owner && dcnt[0] > 0;
+    if (used) {
+      const uint32_t k = atomicAdd(&s_misc[40], 1u);
+      if (k < (uint32_t)kAggDigits) s_misc[41 + k] = (uint32_t)tid;
+    }
+    few = __syncthreads_count(used) <= kAggDigits;
+  }
+  if (p.check_mode != kCheckPerturb && few) {
+    const uint32_t lt = lanemask_lt();
+    const uint32_t nv = s_misc[40];
+    uint32_t v[kAggDigits], c[kAggDigits];
+#pragma unroll
+    for (int j = 0; j < kAggDigits; ++j) {
+      v[j] = (uint32_t)j < nv ? s_misc[41 + j] : 0xffffffffu;  // no digit equals ~0
+      c[j] = (uint32_t)j < nv ? my[v[j]] : 0u;  // this warp's first slot of the value
+    }
+#pragma unroll
+    for (int i = 0; i < KPT; ++i) {
+      const bool valid = FULL || wofs + i * 32 < tile_n;
+      const uint32_t d = valid ? dig.of(key[i], i) : 0xffffffffu;
+      uint32_t pos = 0;
+#pragma unroll
+      for (int j = 0; j < kAggDigits; ++j) {
+        const uint32_t m = __ballot_sync(kFullMask, d == v[j]);
+        if (d == v[j]) pos = c[j] + __popc(m & lt);
+        c[j] += __popc(m);
+      }
+      if (valid) place(i, pos, d);
+    }
+    if (lane == 0)
+#pragma unroll
+      for (int j = 0; j < kAggDigits; ++j)
+        if ((uint32_t)j < nv) my[v[j]] = c[j];
+  } else if (p.check_mode != kCheckPerturb) {
 #pragma unroll
     for (int i = 0; i < KPT; ++i)
       if (FULL || wofs + i * 32 < tile_n) {

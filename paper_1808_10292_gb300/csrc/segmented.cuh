@@ -364,7 +364,11 @@ struct SegPassParams {
 
 // One round over the tiles of every radix range: the ordered form, or with
 // FIRST (keys only, pass 0) the order-free first round of onesweep_tile_first.
-template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB, bool FIRST = false>
+// AGG: the ordered form that reserves slots per digit value in tiles with few
+// distinct digits (onesweep_tile_ordered), for passes whose digit is nearly
+// constant inside each range.
+template <typename K, typename V, int BITS, int THREADS, int KPT, int MINB, bool FIRST = false,
+          bool AGG = false>
 __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp) {
   static_assert(!FIRST || !HasVal<V>::value, "the order-free round is keys-only");
   using S = OnesweepShape<K, V, BITS, THREADS, KPT>;
@@ -417,13 +421,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp
                                                         claim);
   } else {
     if (tile_n == TILE)
-      onesweep_tile_ordered<K, V, BITS, THREADS, KPT, true>(p, tile, lt == 0, tile_base, tile_n,
-                                                            kin, kout, vin, vout, base,
-                                                            (uint32_t)len, smem, dig);
+      onesweep_tile_ordered<K, V, BITS, THREADS, KPT, true, RadixDigit, AGG>(
+          p, tile, lt == 0, tile_base, tile_n, kin, kout, vin, vout, base, (uint32_t)len, smem,
+          dig);
     else
-      onesweep_tile_ordered<K, V, BITS, THREADS, KPT, false>(p, tile, lt == 0, tile_base,
-                                                             tile_n, kin, kout, vin, vout, base,
-                                                             (uint32_t)len, smem, dig);
+      onesweep_tile_ordered<K, V, BITS, THREADS, KPT, false, RadixDigit, AGG>(
+          p, tile, lt == 0, tile_base, tile_n, kin, kout, vin, vout, base, (uint32_t)len, smem,
+          dig);
   }
   if (prefetch) {
     cp_async_wait_all();
@@ -511,10 +515,15 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
   timer_end(a.timer, st);
 
   auto kern = k_seg_onesweep<K, V, 8, THREADS, KPT, MINB>;
+  auto kern_agg = k_seg_onesweep<K, V, 8, THREADS, KPT, MINB, false, true>;
   constexpr size_t SEG_SMEM = OrderedShape<K, V, 8, THREADS, KPT>::SMEM;
   if (SEG_SMEM > 48 * 1024) {
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)SEG_SMEM)))
+      return e;
+    if (a.agg_top && (e = cudaFuncSetAttribute(kern_agg,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)SEG_SMEM)))
       return e;
   }
   using FC = FirstCfg<K, THREADS, KPT, MINB>;  // the order-free first round's CTA shape
@@ -570,7 +579,10 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
       }
     }
     timer_begin(a.timer, "k_seg_onesweep", st);
-    kern<<<(unsigned)a.max_tiles, THREADS, SEG_SMEM, st>>>(sp);
+    if (a.agg_top && q == P - 1)  // the top digit, nearly constant inside each range
+      kern_agg<<<(unsigned)a.max_tiles, THREADS, SEG_SMEM, st>>>(sp);
+    else
+      kern<<<(unsigned)a.max_tiles, THREADS, SEG_SMEM, st>>>(sp);
     timer_end(a.timer, st);
   }
   timer_begin(a.timer, "k_seg_copy_back", st);

@@ -107,3 +107,27 @@ def test_check_mode_argument():
     assert lib.isort_debug_set(_lib.DEBUG_CHECK_MODE, 3) == _lib.EINVAL
     assert lib.isort_debug_set(_lib.DEBUG_CHECK_MODE, -1) == _lib.EINVAL
     assert lib.isort_debug_set(_lib.DEBUG_CHECK_MODE, 0) == _lib.OK
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("key_bits,val_bits", [(32, 0), (32, 32), (64, 0)])
+@pytest.mark.parametrize("dist", ["uniform", "and4", "sorted"])
+def test_sample_sort_buckets_every_check_mode(check_mode, mode, key_bits, val_bits, dist):
+    """With 256 buckets the top digit takes one or two values inside a bucket,
+    and the buckets' top pass ranks such tiles by one ballot per digit value
+    instead of slot adds; those ranks, the forced fallback after them and the
+    perturbed ranks must all give the oracle's result."""
+    n = 3_000_017  # buckets of about 1.4 tiles: whole and ragged tiles
+    k = inputs.keys(n, key_bits, dist, seed=16)
+    v = inputs.iota(n, val_bits) if val_bits else None
+    check_mode(mode)
+    dk = torch.from_numpy(k).cuda()
+    dv = None if v is None else torch.from_numpy(v).cuda()
+    isort.sample_sort(dk, dv, buckets=256, oversample=16, seed=5)
+    assert isort.stream_status() == _lib.OK
+    if val_bits:
+        ok, ov, _, _ = oracle.gvr_sort(k, v, buckets=256, oversample=16, seed=5)
+        assert np.array_equal(dv.cpu().numpy(), ov)
+    else:
+        ok, _, _ = oracle.gvr_sort(k, buckets=256, oversample=16, seed=5)
+    assert np.array_equal(dk.cpu().numpy(), ok)
