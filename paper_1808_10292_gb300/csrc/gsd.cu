@@ -29,12 +29,14 @@ constexpr int kSampleItems = 16;  // r*p*p <= 4096 sampled keys
 constexpr int kMergeThreads = 256;
 
 // Output keys per merge CTA: ITEMS per thread, odd so that a warp's merge
-// reads and writes (stride ITEMS) spread over all 32 banks, and as many as the
-// staged tile (keys and payloads) allows within 48 KB of static shared memory.
+// reads and writes (stride ITEMS) spread over all 32 banks. 4-byte keys alone
+// take 31 (each thread's merge-path search shared by more outputs; 15, 23 and
+// 47 measured slower); wider items 15 or 11, as many as the staged tile
+// (keys and payloads) allows within 48 KB of static shared memory.
 template <typename K, typename V>
 struct MergeShape {
   static constexpr int BYTES = (int)sizeof(K) + (HasVal<V>::value ? (int)sizeof(V) : 0);
-  static constexpr int ITEMS = BYTES <= 12 ? 15 : 11;
+  static constexpr int ITEMS = BYTES <= 4 ? 31 : BYTES <= 12 ? 15 : 11;
   static constexpr int TILE = kMergeThreads * ITEMS;
   static_assert(ITEMS % 2 == 1, "odd items per thread");
   static_assert((size_t)TILE * BYTES <= 48 * 1024, "static shared memory");
@@ -274,13 +276,38 @@ __global__ void __launch_bounds__(kMergeThreads)
     int ia = (int)merge_split<K>([&](int64_t i) { return s_k[i]; },
                                  [&](int64_t i) { return s_k[na + i]; }, na, nb, dd);
     int ib = dd - ia;
+    if constexpr (kMergeItems >= 23) {
+      // long per-thread merges: the two runs' heads stay in registers, one
+      // shared load per output (the consumed run's next key)
+      K ka = ia < na ? s_k[ia] : K(0), kb = ib < nb ? s_k[na + ib] : K(0);
 #pragma unroll
-    for (int o = 0; o < kMergeItems; ++o) {
-      if (dd + o < nt) {
-        const bool take_a = ib >= nb || (ia < na && s_k[ia] <= s_k[na + ib]);
-        const int src = take_a ? ia++ : na + ib++;
-        ok[o] = s_k[src];
-        if constexpr (HV) ov[o] = s_v[src];
+      for (int o = 0; o < kMergeItems; ++o) {
+        if (dd + o < nt) {
+          const bool take_a = ib >= nb || (ia < na && ka <= kb);
+          ok[o] = take_a ? ka : kb;
+          if constexpr (HV) ov[o] = s_v[take_a ? ia : na + ib];
+          if (take_a)
+            ++ia;
+          else
+            ++ib;
+          const bool more = take_a ? ia < na : ib < nb;
+          const K next = more ? s_k[take_a ? ia : na + ib] : K(0);
+          if (take_a)
+            ka = next;
+          else
+            kb = next;
+        }
+      }
+    } else {
+      // short ones: both heads re-read each step (measured faster at 15 items)
+#pragma unroll
+      for (int o = 0; o < kMergeItems; ++o) {
+        if (dd + o < nt) {
+          const bool take_a = ib >= nb || (ia < na && s_k[ia] <= s_k[na + ib]);
+          const int src = take_a ? ia++ : na + ib++;
+          ok[o] = s_k[src];
+          if constexpr (HV) ov[o] = s_v[src];
+        }
       }
     }
   }
