@@ -274,14 +274,17 @@ __host__ __device__ constexpr uint32_t radix8_byte_sel(int shift) {
 
 // Keep DRAM busy while tiles are ranking: one thread of the CTA asks the copy
 // engine to bring the input of a tile about one wave ahead into L2, so that
-// tile's loads hit L2. Skipped when the range is not 16-byte aligned.
+// tile's loads hit L2. The bulk prefetch takes 16-byte aligned addresses and
+// sizes, so a range that does not start or end on 16 bytes (a segment or a
+// bucket inside the keys) is prefetched without its partial 16-byte ends,
+// which stay inside the range.
 template <typename T>
 __device__ __forceinline__ void prefetch_tile(const T* base, int64_t first, int64_t count) {
-  const char* a = reinterpret_cast<const char*>(base + first);
-  const uintptr_t mis = reinterpret_cast<uintptr_t>(a) & 15;
-  if (count <= 0 || mis) return;
-  const uint32_t bytes = (uint32_t)((count * (int64_t)sizeof(T)) & ~int64_t(15));
-  if (bytes) prefetch_l2(a, bytes);
+  if (count <= 0) return;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(base + first);
+  const uintptr_t lo = (a + 15) & ~uintptr_t(15);
+  const uintptr_t hi = (a + (uintptr_t)count * sizeof(T)) & ~uintptr_t(15);
+  if (hi > lo) prefetch_l2(reinterpret_cast<const void*>(lo), (uint32_t)(hi - lo));
 }
 
 template <typename K, typename V, int BITS, int THREADS, int KPT>
