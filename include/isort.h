@@ -106,7 +106,9 @@ isort_status isort_pairs_host(const void *keys_in, const void *vals_in, void *ke
  * segments of a class in the same launch.
  *  - total_keys: the key count (= offsets[num_segments]) given on the host, so
  *    that the call can size its workspace without reading the device-resident
- *    offsets (which keeps the call asynchronous and graph-capturable).
+ *    offsets (which keeps the call asynchronous and graph-capturable); below
+ *    2^40 (ISORT_EINVAL otherwise: the radix tiles record their first key in
+ *    40 bits).
  *  - radix_bits: 0 or 8 (the segmented rounds are radix-256 rounds only; 11
  *    and 16 return ISORT_EUNSUPPORTED).
  * Offsets are read on the device only: a segment that breaks these rules is

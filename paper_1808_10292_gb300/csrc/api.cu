@@ -207,6 +207,9 @@ bool aligned(const void* p, int bytes) { return (reinterpret_cast<uintptr_t>(p) 
 
 // ---- segmented sort workspace ----
 std::map<std::pair<int, int>, int64_t> g_seg_btn_max;  // (key_bits, val_bits) -> threshold
+// Keys per segmented batch, exclusive: each radix tile records its first key
+// in 40 bits.
+constexpr int64_t kSegMaxKeys = int64_t(1) << 40;
 std::map<std::pair<int, int>, int> g_seg_network;      // (key_bits, val_bits) -> ISORT_NET_*
 
 // Longest range that takes the BTN path: the tuned threshold, capped by the
@@ -705,6 +708,7 @@ isort_status isort_segmented(void* keys, void* vals, const int64_t* offsets, int
   if (radix_bits != 0 && radix_bits != 8)
     return (radix_bits > 0 && radix_bits <= 24) ? ISORT_EUNSUPPORTED : ISORT_EINVAL;
   if (num_segments < 0 || total_keys < 0 || num_segments > INT32_MAX) return ISORT_EINVAL;
+  if (total_keys >= kSegMaxKeys) return ISORT_EINVAL;
   if (num_segments == 0 || total_keys == 0) return ISORT_OK;
   if (!offsets || !keys || !aligned(keys, key_bits / 8) ||
       (vals && !aligned(vals, val_bits / 8)) || !aligned(offsets, 8))
@@ -748,7 +752,8 @@ isort_status isort_tune_segmented_network(int key_bits, int val_bits, int networ
 
 isort_status isort_segmented_workspace_size(int64_t num_segments, int64_t total_keys, int key_bits,
                                             int val_bits, size_t* bytes) {
-  if (!bytes || num_segments < 0 || total_keys < 0) return ISORT_EINVAL;
+  if (!bytes || num_segments < 0 || total_keys < 0 || total_keys >= kSegMaxKeys)
+    return ISORT_EINVAL;
   isort_status s = check_widths(key_bits, val_bits, val_bits != 0);
   if (s != ISORT_OK) return s;
   const SegConfig* c = key_bits == 32 ? seg_config_k32(val_bits) : seg_config_k64(val_bits);

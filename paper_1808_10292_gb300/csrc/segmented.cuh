@@ -38,6 +38,14 @@ constexpr uint32_t kErrOffsets = 4u;  // error bit: offsets not a valid partitio
 // Classes of ranges.
 enum { kSegWarp = 0, kSegMid = 1, kSegCta = 2, kSegRadix = 3, kSegClasses = 4 };
 
+// Per radix tile, one 64-bit word (tile_info): the tile's first key (an index
+// into the whole batch, 40 bits), its number of keys (14 bits) and the
+// range's skipped passes (bit 56 + q: pass q is skipped).
+constexpr int kTileKeysShift = 40, kTileSkipShift = 56;
+constexpr uint64_t kTileStartMask = (uint64_t(1) << kTileKeysShift) - 1;
+constexpr uint64_t kTileKeysMask = 0x3fff;
+constexpr int64_t kSegMaxTotal = int64_t(1) << kTileKeysShift;  // keys per batch, exclusive
+
 __device__ __forceinline__ void seg_range(const int64_t* off, int64_t s, int64_t total,
                                           int64_t& start, int64_t& len) {
   int64_t a = off[s], b = off[s + 1];
@@ -276,7 +284,7 @@ __global__ void __launch_bounds__(1 << BITS) k_seg_scan(const uint32_t* __restri
                                                        const int32_t* __restrict__ list,
                                                        const uint32_t* __restrict__ slot_first,
                                                        uint64_t* __restrict__ tile_info) {
-  static_assert(PASSES <= 8 && TILE < 16384, "tile_info packs keys, parity and skip bits");
+  static_assert(PASSES <= 8 && TILE < 16384, "tile_info packs the start, keys and skip bits");
   constexpr int R = 1 << BITS;
   __shared__ uint32_t s_warp[R / 32];
   const uint32_t slot = blockIdx.x;
@@ -292,20 +300,14 @@ __global__ void __launch_bounds__(1 << BITS) k_seg_scan(const uint32_t* __restri
     if (threadIdx.x == 0) seg_skip[(size_t)slot * PASSES + p] = trivial;
     skips |= (uint32_t)trivial << p;
   }
-  uint32_t parity = 0, src = 0;  // bit p: the buffer holding the range's keys before pass p
-  for (int p = 0; p < PASSES; ++p) {
-    parity |= src << p;
-    src ^= ((skips >> p) & 1u) ^ 1u;
-  }
   int64_t start, len;
   seg_range(off, list[(size_t)kSegRadix * nseg + slot], total, start, len);
   const int64_t tiles = (len + TILE - 1) / TILE, first = slot_first[slot];
   for (int64_t lt = threadIdx.x; lt < tiles; lt += R) {
-    const int64_t at = start + lt * TILE;
-    // past 2^34 keys the word cannot hold the start: 0 keys, no prefetch
-    const int64_t n = at < (int64_t(1) << 34) ? min((int64_t)TILE, len - lt * TILE) : 0;
-    tile_info[first + lt] = (uint64_t)(n ? at : 0) | ((uint64_t)n << 34) |
-                            ((uint64_t)parity << 48) | ((uint64_t)skips << 56);
+    const int64_t at = start + lt * TILE;  // below 2^40: the host refuses larger batches
+    const int64_t n = min((int64_t)TILE, len - lt * TILE);
+    tile_info[first + lt] =
+        (uint64_t)at | ((uint64_t)n << kTileKeysShift) | ((uint64_t)skips << kTileSkipShift);
   }
 }
 
@@ -315,6 +317,11 @@ __device__ __forceinline__ int seg_src(const uint32_t* skip_row, int pass) {
   int src = 0;
   for (int q = 0; q < pass; ++q) src ^= (skip_row[q] == 0);
   return src;
+}
+
+// The same from a tile_info word's skip bits (bit q: pass q is skipped).
+__device__ __forceinline__ int tile_src(uint32_t skips, int pass) {
+  return __popc(~skips & ((1u << pass) - 1u)) & 1;
 }
 
 // After the last pass: the ranges that executed an odd number of passes end in
@@ -358,7 +365,7 @@ struct SegPassParams {
   const uint32_t* seg_base;
   const uint32_t* seg_skip;  // [slots][passes] 1 = the pass is the identity on the range
   uint32_t* seg_claim;       // [slots][R] keys only: the first round's output cursors
-  const uint64_t* tile_info;  // [tiles] first key | keys << 34 | parity << 48 | skip << 56
+  const uint64_t* tile_info;  // [tiles] first key | keys << 40 | skipped passes << 56
   int passes;
 };
 
@@ -378,16 +385,21 @@ __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp
   uint32_t* s_wcnt = reinterpret_cast<uint32_t*>(smem);
   uint32_t* s_misc = FIRST ? s_wcnt + 2 * R : s_wcnt + WARPS * R + R;
   const int tid = threadIdx.x;
+  const uint32_t ntiles = sp.cnt[kCntTiles];  // read now, off the tile's chain of loads
   if (p.status_next)
     for (int d = tid; d < R; d += THREADS) p.status_next[(size_t)blockIdx.x * R + d] = 0;
   if (tid == 0) s_misc[0] = atomicAdd(p.counter, 1u);
   zero_words<THREADS>(s_wcnt, FIRST ? R : WARPS * R);
   __syncthreads();
   const uint32_t tile = s_misc[0];
-  if (tile >= sp.cnt[kCntTiles]) return;  // more CTAs than tiles: nothing left
+  if (tile >= ntiles) return;  // more CTAs than tiles: nothing left
+  // One word gives the tile's first key, its length and the range's skipped
+  // passes, so the key loads wait on one load; the range (slot, start, length,
+  // bases) is looked up while they are in flight.
+  const uint64_t info = sp.tile_info[tile];
+  const uint32_t skips = (uint32_t)(info >> kTileSkipShift);
+  if ((skips >> p.pass) & 1u) return;  // the digit is constant on this range
   const int32_t slot = sp.tile_slot[tile];
-  const uint32_t* skip_row = sp.seg_skip + (size_t)slot * sp.passes;
-  if (skip_row[p.pass]) return;  // the digit is constant on this range
   // The tile one wave ahead: thread 0 copies its tile_info word to shared
   // memory now (cp.async: no register, no wait) and prefetches its keys into
   // L2 when this tile is done.
@@ -398,9 +410,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp
   int64_t start, len;
   seg_range(sp.off, sp.list[(size_t)kSegRadix * sp.nseg + slot], sp.total, start, len);
   const int64_t lt = (int64_t)tile - sp.slot_first[slot];  // tile index within the range
-  const int64_t tile_base = start + lt * TILE;
-  const int tile_n = (int)min((int64_t)TILE, len - lt * TILE);
-  const int src = seg_src(skip_row, p.pass);
+  const int64_t tile_base = (int64_t)(info & kTileStartMask);
+  const int tile_n = (int)((info >> kTileKeysShift) & kTileKeysMask);
+  const int src = tile_src(skips, p.pass);
   const K* kin = static_cast<const K*>(src ? p.keys[1] : p.keys[0]);
   K* kout = static_cast<K*>(src ? p.keys[0] : p.keys[1]) + start;
   const V* vin = static_cast<const V*>(src ? p.vals[1] : p.vals[0]);
@@ -432,10 +444,11 @@ __global__ void __launch_bounds__(THREADS, MINB) k_seg_onesweep(SegPassParams sp
   if (prefetch) {
     cp_async_wait_all();
     const uint64_t w = *s_pf;
-    const int64_t at = (int64_t)(w & ((uint64_t(1) << 34) - 1));
-    const int64_t n = (int64_t)((w >> 34) & 0x3fff);
-    if (!((w >> (56 + p.pass)) & 1) && n && at + n <= sp.total) {
-      const int s = (int)((w >> (48 + p.pass)) & 1);  // the buffer holding that tile now
+    const int64_t at = (int64_t)(w & kTileStartMask);
+    const int64_t n = (int64_t)((w >> kTileKeysShift) & kTileKeysMask);
+    const uint32_t sk = (uint32_t)(w >> kTileSkipShift);
+    if (!((sk >> p.pass) & 1u) && n && at + n <= sp.total) {
+      const int s = tile_src(sk, p.pass);  // the buffer holding that tile now
       prefetch_tile(static_cast<const K*>(s ? p.keys[1] : p.keys[0]), at, n);
       if constexpr (HasVal<V>::value)
         prefetch_tile(static_cast<const V*>(s ? p.vals[1] : p.vals[0]), at, n);
@@ -451,6 +464,7 @@ cudaError_t seg_launch(const SegArgs& a, cudaStream_t st) {
   constexpr int R = L::R, P = L::PASSES, TILE = OS::TILE;
   cudaError_t e;
   const int64_t nslots = a.nseg;
+  if (a.total >= kSegMaxTotal) return cudaErrorInvalidValue;  // tile_info holds 40-bit starts
   if ((e = cudaMemsetAsync(a.cnt, 0, sizeof(uint32_t) * kCntWords, st))) return e;
   if ((e = cudaMemsetAsync(a.seg_hist, 0, sizeof(uint32_t) * nslots * P * R, st))) return e;
   // status[0] serves pass 0 only with payloads (keys only, pass 0 takes cursors)

@@ -74,6 +74,11 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.isort_tune_segmented_network(16, 0, _lib.NET_OET) == _lib.EINVAL
     assert lib.isort_tune_segmented_network(32, 0, _lib.NET_BTN) == _lib.OK
     assert lib.isort_strerror(_lib.ETIMEOUT) == b"bounded device wait gave up"
+    # segmented batches: each radix tile records its first key in 40 bits
+    assert lib.isort_segmented(dummy, None, dummy, 1, 1 << 40, 32, 0, 8, None) == _lib.EINVAL
+    assert lib.isort_segmented(dummy, None, dummy, 1, -1, 32, 0, 8, None) == _lib.EINVAL
+    size = ctypes.c_size_t(0)
+    assert lib.isort_segmented_workspace_size(1, 1 << 40, 32, 0, ctypes.byref(size)) == _lib.EINVAL
 
 
 def test_workspace_size_and_tuning_tables(lib):
