@@ -104,8 +104,8 @@ struct SegArgs {
   uint32_t* seg_base;    // [nseg][P][R]
   uint32_t* seg_skip;    // [nseg][P] trivial passes of each radix range
   uint32_t* seg_claim;   // [nseg][R] keys only: the first round's output cursors per range
-  uint64_t* tile_info;   // [max_tiles] per radix tile: first key (34 bits) | keys << 34 |
-                         // input parity of each pass << 48 | skip of each pass << 56
+  uint64_t* tile_info;   // [max_tiles] per radix tile: first key (40 bits) | keys << 40 |
+                         // skip of each pass << 56
   uint32_t* status[2];   // [max_tiles][R]
   uint32_t* err;
   uint32_t spin_limit;

@@ -271,8 +271,8 @@ __global__ void __launch_bounds__(1024) k_seg_hist(const K* __restrict__ keys,
 // is the identity on that range and is skipped for it). Also zeroes the
 // range's first-round output cursors (seg_claim, keys only; null otherwise)
 // and writes, for each of its tiles, where the tile's keys start, how many
-// there are, and in each pass which buffer holds them and whether the pass is
-// skipped (tile_info, read by the rounds to prefetch a tile one wave ahead).
+// there are and which passes the range skips (tile_info: the rounds take their
+// tile from it, and prefetch the tile one wave ahead with it).
 template <int BITS, int PASSES, int TILE>
 __global__ void __launch_bounds__(1 << BITS) k_seg_scan(const uint32_t* __restrict__ cnt,
                                                        const uint32_t* __restrict__ seg_hist,

@@ -386,8 +386,9 @@ __global__ void __launch_bounds__(THREADS, MINB)
 
 // Step B of round 0 of a keys-only sort (order-free, as step A there): the
 // tiles of bucket h take their digits' ranges from the cursors claim[h*256 +
-// l] (zeroed by k_scan_wide) instead of looking back; CTA shape of the
-// order-free round (THREADS x KPT, the same tile as the ordered step).
+// l] (zeroed by k_scan_buckets, or k_scan_wide at radix 2048) instead of
+// looking back; CTA shape of the order-free round (THREADS x KPT, the same
+// tile as the ordered step).
 template <typename K, int THREADS, int KPT, int MINB, int NB, typename DS>
 __global__ void __launch_bounds__(THREADS, MINB)
     k_bucket_first(PassParams p, const uint32_t* __restrict__ base,
